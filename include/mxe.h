@@ -1,0 +1,225 @@
+/*
+ * mxe.h -- C ABI of the GB300 MXE hot path.
+ *
+ * The library evaluates the mean-field, phase-averaged EAM free energy of a
+ * lattice of Gaussian-smeared sites and its gradients (App. A, App. B.2,
+ * Sec. 2.1 of Mendez & Ponga, "MXE: A package for simulating long-term
+ * diffusive mass transport phenomena in nanoscale systems"), relaxes the mean
+ * positions and widths at fixed composition (Sec. 4, dynamic relaxation; here
+ * FIRE), and advances the molar fractions by one forward-Euler step of the
+ * master equation (Sec. 3.1, Eq. MassTransport).
+ *
+ * Conventions shared by every call:
+ *  - Units: Angstrom, eV, K, s.  kB = 8.617333262e-5 eV/K.
+ *  - Sites i = 0..n-1; non-vacancy species k = 0..S-1 (S <= MXE_MAXS); the
+ *    vacancy fraction x_iv = 1 - sum_k x_ik is implicit.
+ *  - sigma_i is the per-Cartesian-component standard deviation of site i's
+ *    Gaussian, sigma = (beta m)^(-1/2) / omega with the paper's omega.
+ *  - Arrays are structure-of-arrays, contiguous, FP64 unless stated:
+ *    q [3][n] (all x, then all y, then all z), sigma [n], x [S][n], T [n].
+ *  - Every state, input and output array is a CALLER-OWNED DEVICE pointer.
+ *    The context owns its own scratch (cell grid, neighbour and bond lists,
+ *    per-site embedding terms, reduction buffers, FIRE state).
+ *  - Every call is enqueued on the context's CUDA stream.  Calls that return
+ *    host values (counts, iteration numbers, statuses found on the device)
+ *    synchronise that stream before returning.
+ *  - No exception crosses the ABI.  Every call returns an mxe_status.  On any
+ *    error other than MXE_ERR_NO_CONVERGE, in-out arrays are left as they were.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef MXE_H
+#define MXE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MXE_MAXS 4
+
+typedef enum {
+    MXE_OK = 0,
+    MXE_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, unsupported option) */
+    MXE_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    MXE_ERR_OOM = 3,            /* device allocation failed */
+    MXE_ERR_BOX_TOO_SMALL = 4,  /* a box length is below 2 r_list */
+    MXE_ERR_NBR_OVERFLOW = 5,   /* neighbour count exceeds the list's int32 range */
+    MXE_ERR_GEOMETRY = 6,       /* a quadrature node closer than 0.5 A, or a static density <= 1e-12 */
+    MXE_ERR_NONFINITE = 7,      /* NaN or Inf in the free energy or a gradient */
+    MXE_ERR_X_RANGE = 8,        /* Euler step would give x_ik < -1e-12 or sum_k x_ik > 1 + 1e-12 */
+    MXE_ERR_NO_CONVERGE = 9,    /* relaxation reached max_iter; the last iterate is returned */
+    MXE_ERR_STATE = 10          /* call order violated (e.g. no neighbour list built yet) */
+} mxe_status;
+
+typedef enum {
+    MXE_FP64 = 0,        /* every step in FP64 */
+    MXE_FP32_MIXED = 1,  /* node arithmetic (distance, switch, exp, derivatives) in FP32;
+                            each pair's 13-node partial sums added into FP64 per-site sums;
+                            FP64 for per-site results, totals, mu differences, x, FIRE */
+    MXE_FP32_FF = 2      /* as MXE_FP32_MIXED, but the per-site sums are carried as
+                            unevaluated float pairs (float-float, >= 44-bit significand)
+                            and rounded to FP64 once per site */
+} mxe_precision;
+
+/* Periodic orthorhombic box.  A free surface is a periodic axis longer than
+ * the slab by more than r_list (a vacuum gap), so no pair spans the gap.    */
+typedef struct {
+    double L[3];
+} mxe_box;
+
+/* Analytic EAM tables (App. B.2 with pair-resolved species):
+ *   phi_kl(r) = phi_A[k][l] exp(-phi_p[k][l] (r / phi_r0[k][l] - 1)) S(r)
+ *   f_kl(r)   = f_xi[k][l]  exp(-f_q[k][l]  (r / f_r0[k][l]  - 1)) S(r)
+ *               (electron density at a k-site from an l-neighbour)
+ *   F_k(rho)  = -E[k] sqrt(rho)
+ *   S(r)      = 1 - 10 t^3 + 15 t^4 - 6 t^5, t = (r - r_switch)/(r_cut - r_switch)
+ *               clipped to [0, 1].
+ * cross_geomean != 0: phi_kl for k != l is sqrt(phi_kk phi_ll) pointwise and
+ * the off-diagonal phi entries are ignored.  Otherwise phi must be symmetric
+ * (phi_kl = phi_lk), else mxe_create returns MXE_ERR_ARG.  A = 0 or xi = 0
+ * switches a term off.                                                       */
+typedef struct {
+    int32_t n_species;
+    int32_t cross_geomean;
+    double phi_A[MXE_MAXS][MXE_MAXS], phi_p[MXE_MAXS][MXE_MAXS], phi_r0[MXE_MAXS][MXE_MAXS];
+    double f_xi[MXE_MAXS][MXE_MAXS], f_q[MXE_MAXS][MXE_MAXS], f_r0[MXE_MAXS][MXE_MAXS];
+    double E[MXE_MAXS];
+    double r_switch, r_cut;
+} mxe_potential;
+
+/* Per-site state (device pointers, caller-owned).  q and sigma are in-out for
+ * mxe_relax, x is in-out for mxe_diffuse_step.  sublattice may be NULL (all
+ * sites on sublattice 0); bit s of mobile_mask marks sublattice s as carrying
+ * mass flux (bonds only join two sites of the same mobile sublattice).      */
+typedef struct {
+    int64_t n;
+    double *q;                 /* [3][n] */
+    double *sigma;             /* [n] */
+    double *x;                 /* [S][n] */
+    const double *T;           /* [n] */
+    const uint8_t *sublattice; /* [n] or NULL */
+    uint32_t mobile_mask;
+    uint32_t pad;
+} mxe_state;
+
+/* FIRE constants (Bitzek et al., PRL 97, 170201, 2006), unit masses. */
+typedef struct {
+    double dt0, dt_max, f_inc, f_dec, alpha0, f_alpha;
+    int32_t n_min;
+    int32_t check_every;  /* iterations enqueued between host checks (<= 0: 16) */
+} mxe_fire_params;
+
+typedef struct mxe_ctx mxe_ctx;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *mxe_status_string(mxe_status s);
+
+/* Create a context for n sites on one box with one potential, evaluating in
+ * the given precision, enqueuing on cuda_stream (a cudaStream_t; NULL = the
+ * legacy default stream).  Allocates the n-sized scratch on the current
+ * device.  *out is NULL on error.                                            */
+mxe_status mxe_create(mxe_ctx **out, const mxe_box *box, const mxe_potential *pot, int64_t n,
+                      mxe_precision precision, void *cuda_stream);
+
+/* Release every device allocation of the context.  NULL is accepted. */
+mxe_status mxe_destroy(mxe_ctx *ctx);
+
+/* Neighbour and bond sets (Sec. 4, Algorithm 1: neighbour-list step; Sec. 3:
+ * the transport sum runs over nearest neighbours).
+ *   r_list = r_cut + sqrt(6) max_i sigma_i + skin  (a pair farther apart than
+ *   r_cut + sqrt(6) max sigma has every quadrature node beyond r_cut).
+ * Neighbours: every j != i with |d_ij| < r_list, d_ij the minimum image of
+ * q_j - q_i; d and |d|^2 are formed in FP64 without FMA as
+ *   d_a = (q_ja - q_ia) - L_a rint((q_ja - q_ia) (1/L_a)),
+ *   |d|^2 = (d_x d_x + d_y d_y) + d_z d_z,
+ * so the set is bit-reproducible.  Bonds: neighbours with |d| < r_bond on the
+ * same sublattice, that sublattice mobile.  Rows are sorted by j.
+ * Requires L_a >= 2 r_list on every axis (else MXE_ERR_BOX_TOO_SMALL).
+ * The list stays valid while 2 max|q - q_build| + sqrt(6)(max sigma - max
+ * sigma_build) <= skin; mxe_relax rebuilds it on its own when that fails.
+ * Outputs (host, optional): total neighbour entries, r_list used.  Syncs.  */
+mxe_status mxe_build_neighbors(mxe_ctx *ctx, const mxe_state *state, double skin, double r_bond,
+                               int64_t *n_pairs_out, double *r_list_out);
+
+/* Copy the current neighbour CSR (offsets_dev [n+1], idx_dev [n_pairs], int32
+ * device arrays, caller-owned) -- for tests; bit-identical to a brute-force
+ * evaluation of the rule above.  Either pointer may be NULL.                 */
+mxe_status mxe_export_neighbors(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev);
+
+/* Same for the bond CSR; *n_bonds_out (host) receives the entry count.     */
+mxe_status mxe_export_bonds(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev, int64_t *n_bonds_out);
+
+/* Free energy and its three gradients (App. A third-degree rule with 12 nodes
+ * per pair at +-sqrt(6) sigma along each axis for each of the two sites;
+ * App. B.2 Taylor-linearised embedding; Sec. 2.1 mean-field free energy):
+ *   rho_bar_i^k = sum_j sum_l x_jl f_kl(|d_ij|),  <rho_i^k> = sum_j sum_l x_jl <f_kl>_ij
+ *   e_i^k = F_k(rho_bar) + F_k'(rho_bar)(<rho> - rho_bar)
+ *   E_V   = sum_i [1/2 sum_j sum_kl x_ik x_jl <phi_kl>_ij + sum_k x_ik e_i^k]
+ *   F_vib = -3 kB sum_i T_i ln(sigma_i / 1 A)
+ *   F_mix = kB sum_i T_i (sum_k x_ik ln x_ik + x_iv ln x_iv),  0 ln 0 = 0
+ *   F     = E_V + F_vib + F_mix
+ * Outputs (device, caller-owned; any may be NULL except F4_dev):
+ *   F4_dev [4]       = E_V, F_vib, F_mix, F (FP64, deterministic order)
+ *   dFdq_dev [3][n]  = dF/dq (the force is its negative)
+ *   dFdsigma_dev [n] = dF/dsigma
+ *   mu_ex_dev [S][n] = dE_V/dx_ik with x_iv dependent (excess chemical potential)
+ *   mu_dev [S][n]    = dF/dx_ik = mu_ex + kB T_i (ln x_ik - ln x_iv), ln arguments
+ *                      floored at 1e-300
+ * Requires a neighbour list built for this state.  Syncs and returns
+ * MXE_ERR_GEOMETRY / MXE_ERR_NONFINITE if found.                              */
+mxe_status mxe_free_energy_grad(mxe_ctx *ctx, const mxe_state *state, double *F4_dev,
+                                double *dFdq_dev, double *dFdsigma_dev, double *mu_ex_dev,
+                                double *mu_dev);
+
+/* As mxe_free_energy_grad, but only enqueues the work: device-found errors
+ * are kept in the context and returned by the next mxe_sync_status.        */
+mxe_status mxe_free_energy_grad_async(mxe_ctx *ctx, const mxe_state *state, double *F4_dev,
+                                      double *dFdq_dev, double *dFdsigma_dev, double *mu_ex_dev,
+                                      double *mu_dev);
+
+/* Synchronise the context's stream and return (then clear) the first error
+ * recorded on the device since the last call.                               */
+mxe_status mxe_sync_status(mxe_ctx *ctx);
+
+/* Relax (q, sigma) at fixed x (Sec. 4: the equilibrium step of the staggered
+ * scheme) with FIRE:  y = (q, sigma), f = -(dF/dq, dF/dsigma), v = 0,
+ * dt = dt0, alpha = alpha0.  Iteration it = 0, 1, ...:
+ *   1. f(y); fmax = max_i max(|dF/dq_i|_2, |dF/dsigma_i|); stop (MXE_OK) if fmax <= ftol
+ *   2. stop with MXE_ERR_NO_CONVERGE if it == max_iter
+ *   3. if it > 0: P = f.v; P > 0: n_pos += 1 and, if n_pos > n_min,
+ *      dt = min(f_inc dt, dt_max), alpha *= f_alpha;  P <= 0: n_pos = 0,
+ *      dt *= f_dec, alpha = alpha0, v = 0
+ *   4. v += dt f;  v = (1 - alpha) v + alpha |v| f / |f|   (global norms)
+ *   5. y += dt v;  sigma = max(sigma, 1e-3 A)
+ * Neighbour lists are rebuilt whenever the skin criterion fails.
+ * fire may be NULL (defaults dt0 0.02, dt_max 0.1, f_inc 1.1, f_dec 0.5,
+ * alpha0 0.1, f_alpha 0.99, n_min 5).  iters_out = number of FIRE updates,
+ * fmax_out = fmax at the last evaluation (host, optional).  Syncs.
+ * On GEOMETRY / NONFINITE the input (q, sigma) is restored.                 */
+mxe_status mxe_relax(mxe_ctx *ctx, mxe_state *state, double ftol, int32_t max_iter,
+                     const mxe_fire_params *fire, int32_t *iters_out, double *fmax_out);
+
+/* One forward-Euler step of the master equation (Sec. 3.1, Eq. MassTransport
+ * with tau_r = 0, Eq. attempt_freq_mass), per species k and bond (i, j):
+ *   J_{i->j} = nu0 exp(-beta_i Qm) x_ik x_jv exp(beta_i (mu_ik - mu_jk))
+ *   x_ik' = x_ik + dt sum_{j in bonds(i)} (J_{j->i} - J_{i->j})
+ * with mu the excess chemical potential dE_V/dx.  Each bond's net exchange
+ * is formed identically from both ends, so the updates of i and j cancel
+ * exactly and total mass is conserved up to the rounding of the two sums.
+ * mu_ex_dev may be NULL: it is then computed first (one free-energy pass).
+ * x is updated only if every x_ik' >= -1e-12 and sum_k x_ik' <= 1 + 1e-12,
+ * else MXE_ERR_X_RANGE and x is unchanged.  Requires a bond list.  Syncs.   */
+mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
+                            double dt, double nu0, double Qm);
+
+/* As mxe_diffuse_step but enqueue-only; the range status is kept for the
+ * next mxe_sync_status.  The conditional commit of x happens on the device. */
+mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
+                                  double dt, double nu0, double Qm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MXE_H */
