@@ -38,6 +38,12 @@ extern "C" {
 
 #define MXE_MAXS 4
 
+#if defined(__GNUC__)
+#define MXE_API __attribute__((visibility("default")))
+#else
+#define MXE_API
+#endif
+
 typedef enum {
     MXE_OK = 0,
     MXE_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, unsupported option) */
@@ -103,9 +109,14 @@ typedef struct {
     uint32_t pad;
 } mxe_state;
 
-/* FIRE constants (Bitzek et al., PRL 97, 170201, 2006), unit masses. */
+/* FIRE constants (Bitzek et al., PRL 97, 170201, 2006), unit masses.
+ * sigma_max > 0 bounds every width from above (<= 0: no bound).  The paper's
+ * free energy gives each site -3 kB T ln sigma whatever its occupancy, so the
+ * width of a site with zero occupied fraction has nothing opposing it and
+ * grows without bound; a finite sigma_max keeps such sites in a box.        */
 typedef struct {
     double dt0, dt_max, f_inc, f_dec, alpha0, f_alpha;
+    double sigma_max;
     int32_t n_min;
     int32_t check_every;  /* iterations enqueued between host checks (<= 0: 16) */
 } mxe_fire_params;
@@ -113,17 +124,17 @@ typedef struct {
 typedef struct mxe_ctx mxe_ctx;
 
 /* Human-readable name of a status code (static string, never NULL). */
-const char *mxe_status_string(mxe_status s);
+MXE_API const char *mxe_status_string(mxe_status s);
 
 /* Create a context for n sites on one box with one potential, evaluating in
  * the given precision, enqueuing on cuda_stream (a cudaStream_t; NULL = the
  * legacy default stream).  Allocates the n-sized scratch on the current
  * device.  *out is NULL on error.                                            */
-mxe_status mxe_create(mxe_ctx **out, const mxe_box *box, const mxe_potential *pot, int64_t n,
+MXE_API mxe_status mxe_create(mxe_ctx **out, const mxe_box *box, const mxe_potential *pot, int64_t n,
                       mxe_precision precision, void *cuda_stream);
 
 /* Release every device allocation of the context.  NULL is accepted. */
-mxe_status mxe_destroy(mxe_ctx *ctx);
+MXE_API mxe_status mxe_destroy(mxe_ctx *ctx);
 
 /* Neighbour and bond sets (Sec. 4, Algorithm 1: neighbour-list step; Sec. 3:
  * the transport sum runs over nearest neighbours).
@@ -139,16 +150,16 @@ mxe_status mxe_destroy(mxe_ctx *ctx);
  * The list stays valid while 2 max|q - q_build| + sqrt(6)(max sigma - max
  * sigma_build) <= skin; mxe_relax rebuilds it on its own when that fails.
  * Outputs (host, optional): total neighbour entries, r_list used.  Syncs.  */
-mxe_status mxe_build_neighbors(mxe_ctx *ctx, const mxe_state *state, double skin, double r_bond,
+MXE_API mxe_status mxe_build_neighbors(mxe_ctx *ctx, const mxe_state *state, double skin, double r_bond,
                                int64_t *n_pairs_out, double *r_list_out);
 
 /* Copy the current neighbour CSR (offsets_dev [n+1], idx_dev [n_pairs], int32
  * device arrays, caller-owned) -- for tests; bit-identical to a brute-force
  * evaluation of the rule above.  Either pointer may be NULL.                 */
-mxe_status mxe_export_neighbors(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev);
+MXE_API mxe_status mxe_export_neighbors(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev);
 
 /* Same for the bond CSR; *n_bonds_out (host) receives the entry count.     */
-mxe_status mxe_export_bonds(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev, int64_t *n_bonds_out);
+MXE_API mxe_status mxe_export_bonds(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev, int64_t *n_bonds_out);
 
 /* Free energy and its three gradients (App. A third-degree rule with 12 nodes
  * per pair at +-sqrt(6) sigma along each axis for each of the two sites;
@@ -168,19 +179,19 @@ mxe_status mxe_export_bonds(mxe_ctx *ctx, int32_t *offsets_dev, int32_t *idx_dev
  *                      floored at 1e-300
  * Requires a neighbour list built for this state.  Syncs and returns
  * MXE_ERR_GEOMETRY / MXE_ERR_NONFINITE if found.                              */
-mxe_status mxe_free_energy_grad(mxe_ctx *ctx, const mxe_state *state, double *F4_dev,
+MXE_API mxe_status mxe_free_energy_grad(mxe_ctx *ctx, const mxe_state *state, double *F4_dev,
                                 double *dFdq_dev, double *dFdsigma_dev, double *mu_ex_dev,
                                 double *mu_dev);
 
 /* As mxe_free_energy_grad, but only enqueues the work: device-found errors
  * are kept in the context and returned by the next mxe_sync_status.        */
-mxe_status mxe_free_energy_grad_async(mxe_ctx *ctx, const mxe_state *state, double *F4_dev,
+MXE_API mxe_status mxe_free_energy_grad_async(mxe_ctx *ctx, const mxe_state *state, double *F4_dev,
                                       double *dFdq_dev, double *dFdsigma_dev, double *mu_ex_dev,
                                       double *mu_dev);
 
 /* Synchronise the context's stream and return (then clear) the first error
  * recorded on the device since the last call.                               */
-mxe_status mxe_sync_status(mxe_ctx *ctx);
+MXE_API mxe_status mxe_sync_status(mxe_ctx *ctx);
 
 /* Relax (q, sigma) at fixed x (Sec. 4: the equilibrium step of the staggered
  * scheme) with FIRE:  y = (q, sigma), f = -(dF/dq, dF/dsigma), v = 0,
@@ -191,13 +202,16 @@ mxe_status mxe_sync_status(mxe_ctx *ctx);
  *      dt = min(f_inc dt, dt_max), alpha *= f_alpha;  P <= 0: n_pos = 0,
  *      dt *= f_dec, alpha = alpha0, v = 0
  *   4. v += dt f;  v = (1 - alpha) v + alpha |v| f / |f|   (global norms)
- *   5. y += dt v;  sigma = max(sigma, 1e-3 A)
+ *   5. y += dt v; a sigma leaving [1e-3 A, sigma_max] is set to the bound
+ *      and its velocity to zero
+ * The sigma force is projected on that box (zero where a bound blocks it) in
+ * fmax, P, |f| and the update.
  * Neighbour lists are rebuilt whenever the skin criterion fails.
  * fire may be NULL (defaults dt0 0.02, dt_max 0.1, f_inc 1.1, f_dec 0.5,
- * alpha0 0.1, f_alpha 0.99, n_min 5).  iters_out = number of FIRE updates,
+ * alpha0 0.1, f_alpha 0.99, n_min 5, no sigma_max).  iters_out = number of FIRE updates,
  * fmax_out = fmax at the last evaluation (host, optional).  Syncs.
  * On GEOMETRY / NONFINITE the input (q, sigma) is restored.                 */
-mxe_status mxe_relax(mxe_ctx *ctx, mxe_state *state, double ftol, int32_t max_iter,
+MXE_API mxe_status mxe_relax(mxe_ctx *ctx, mxe_state *state, double ftol, int32_t max_iter,
                      const mxe_fire_params *fire, int32_t *iters_out, double *fmax_out);
 
 /* One forward-Euler step of the master equation (Sec. 3.1, Eq. MassTransport
@@ -210,12 +224,12 @@ mxe_status mxe_relax(mxe_ctx *ctx, mxe_state *state, double ftol, int32_t max_it
  * mu_ex_dev may be NULL: it is then computed first (one free-energy pass).
  * x is updated only if every x_ik' >= -1e-12 and sum_k x_ik' <= 1 + 1e-12,
  * else MXE_ERR_X_RANGE and x is unchanged.  Requires a bond list.  Syncs.   */
-mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
+MXE_API mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
                             double dt, double nu0, double Qm);
 
 /* As mxe_diffuse_step but enqueue-only; the range status is kept for the
  * next mxe_sync_status.  The conditional commit of x happens on the device. */
-mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
+MXE_API mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
                                   double dt, double nu0, double Qm);
 
 #ifdef __cplusplus

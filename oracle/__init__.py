@@ -65,7 +65,7 @@ class _Sys(C.Structure):
 class _Fire(C.Structure):
     _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("f_inc", C.c_double),
                 ("f_dec", C.c_double), ("alpha0", C.c_double), ("f_alpha", C.c_double),
-                ("n_min", C.c_int32), ("pad", C.c_int32)]
+                ("sigma_max", C.c_double), ("n_min", C.c_int32), ("pad", C.c_int32)]
 
 
 @dataclasses.dataclass
@@ -79,6 +79,7 @@ class FireParams:
     alpha0: float = 0.1
     f_alpha: float = 0.99
     n_min: int = 5
+    sigma_max: float = 0.0    # <= 0: no upper bound on sigma
 
 
 def lib():
@@ -265,7 +266,8 @@ def relax(sys, ftol, max_iter, fire: FireParams | None = None, skin=0.2, q=None,
     qq = ref.q.copy()
     ss = ref.sigma.copy()
     P = make_potential(sys.pot)
-    fp = _Fire(fire.dt0, fire.dt_max, fire.f_inc, fire.f_dec, fire.alpha0, fire.f_alpha, fire.n_min, 0)
+    fp = _Fire(fire.dt0, fire.dt_max, fire.f_inc, fire.f_dec, fire.alpha0, fire.f_alpha, fire.sigma_max,
+               fire.n_min, 0)
     it = C.c_int(0)
     fm = C.c_double(0.0)
     rl = sys.pot.r_cut + skin

@@ -69,9 +69,19 @@ typedef struct {
 
 typedef struct {
     double dt0, dt_max, f_inc, f_dec, alpha0, f_alpha;
+    double sigma_max;   /* upper bound of sigma (A); <= 0 or inf: none */
     int32_t n_min;
     int32_t pad;
 } orc_fire;
+
+/* Force on sigma projected on the box [lo, hi]: zero where a bound blocks it. */
+static double proj_fsig(double gs, double sigma, double lo, double hi)
+{
+    double f = -gs;
+    if (sigma >= hi && f > 0.0) return 0.0;
+    if (sigma <= lo && f < 0.0) return 0.0;
+    return f;
+}
 
 /* ------------------------------------------------------------------ */
 /* Pairwise summation (deterministic, accurate totals).                */
@@ -674,8 +684,13 @@ int orc_diffuse_step(int64_t n, int S, double *x, const double *T, const double 
  *        dt = min(f_inc dt, dt_max), alpha = f_alpha alpha;
  *        P <= 0: n_pos = 0, dt = f_dec dt, alpha = alpha0, v = 0
  *     4. v = v + dt f;  v = (1 - alpha) v + alpha |v| f / |f|  (global norms)
- *     5. y = y + dt v;  sigma = max(sigma, sigma_min)
- *   Global dot products and norms are pairwise sums over sites.
+ *     5. y = y + dt v;  sigma is kept in [sigma_min, sigma_max]: a sigma that
+ *        leaves the box is set to the bound and its velocity to zero
+ *   The sigma force is projected on the box (zero where a bound blocks it)
+ *   in fmax, P, |f| and the update.  sigma_max (default: none) bounds the
+ *   width of a site whose occupied fraction is zero: the literal free energy
+ *   gives such a site -3 kB T ln sigma and nothing else, so its width would
+ *   grow without bound.  Global dot products and norms are pairwise sums.
  * On GEOMETRY / NONFINITE the input state is restored.                   */
 /* ------------------------------------------------------------------ */
 int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential *P,
@@ -701,6 +716,9 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
     int64_t cap = 64 * n + 64, npairs = 0;
     int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * cap);
     double dt = fp->dt0, alpha = fp->alpha0, F4[4];
+    const double s_lo = ORC_SIGMA_MIN;
+    const double s_hi = (fp->sigma_max > 0.0) ? fp->sigma_max : INFINITY;
+    double *fs = (double *)malloc(sizeof(double) * n);
     int n_pos = 0, status = ORC_OK, it = 0;
     double fmx = 0.0;
     for (it = 0;; ++it) {
@@ -720,14 +738,15 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
         if (status != ORC_OK) break;
         fmx = 0.0;
         for (int64_t i = 0; i < n; ++i) {
+            fs[i] = proj_fsig(gs[i], sigma[i], s_lo, s_hi);
             double gqi = sqrt(gq[i] * gq[i] + gq[n + i] * gq[n + i] + gq[2 * n + i] * gq[2 * n + i]);
-            fmx = fmax(fmx, fmax(gqi, fabs(gs[i])));
+            fmx = fmax(fmx, fmax(gqi, fabs(fs[i])));
         }
         if (fmx <= ftol) break;
         if (it == max_iter) { status = ORC_ERR_NO_CONVERGE; break; }
         if (it > 0) {
             for (int64_t i = 0; i < n; ++i)
-                tmp[i] = -(gq[i] * vq[i] + gq[n + i] * vq[n + i] + gq[2 * n + i] * vq[2 * n + i]) - gs[i] * vs[i];
+                tmp[i] = -(gq[i] * vq[i] + gq[n + i] * vq[n + i] + gq[2 * n + i] * vq[2 * n + i]) + fs[i] * vs[i];
             double Pw = pairwise_sum(tmp, n);
             if (Pw > 0.0) {
                 n_pos += 1;
@@ -745,23 +764,28 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
         }
         for (int64_t i = 0; i < n; ++i) {
             for (int c = 0; c < 3; ++c) vq[c * n + i] += dt * (-gq[c * n + i]);
-            vs[i] += dt * (-gs[i]);
+            vs[i] += dt * fs[i];
         }
         for (int64_t i = 0; i < n; ++i)
             tmp[i] = vq[i] * vq[i] + vq[n + i] * vq[n + i] + vq[2 * n + i] * vq[2 * n + i] + vs[i] * vs[i];
         double vnorm = sqrt(pairwise_sum(tmp, n));
         for (int64_t i = 0; i < n; ++i)
-            tmp[i] = gq[i] * gq[i] + gq[n + i] * gq[n + i] + gq[2 * n + i] * gq[2 * n + i] + gs[i] * gs[i];
+            tmp[i] = gq[i] * gq[i] + gq[n + i] * gq[n + i] + gq[2 * n + i] * gq[2 * n + i] + fs[i] * fs[i];
         double fnorm = sqrt(pairwise_sum(tmp, n));
         double mix = fnorm > 0.0 ? alpha * vnorm / fnorm : 0.0;
         for (int64_t i = 0; i < n; ++i) {
             for (int c = 0; c < 3; ++c)
                 vq[c * n + i] = (1.0 - alpha) * vq[c * n + i] + mix * (-gq[c * n + i]);
-            vs[i] = (1.0 - alpha) * vs[i] + mix * (-gs[i]);
+            vs[i] = (1.0 - alpha) * vs[i] + mix * fs[i];
         }
         for (int64_t i = 0; i < n; ++i) {
             for (int c = 0; c < 3; ++c) q[c * n + i] += dt * vq[c * n + i];
-            sigma[i] = fmax(sigma[i] + dt * vs[i], ORC_SIGMA_MIN);
+            double sn = sigma[i] + dt * vs[i];
+            if (sn < s_lo || sn > s_hi) {
+                sn = sn < s_lo ? s_lo : s_hi;
+                vs[i] = 0.0;
+            }
+            sigma[i] = sn;
         }
     }
     if (status != ORC_OK && status != ORC_ERR_NO_CONVERGE) {
@@ -770,7 +794,7 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
     }
     *iters_out = it;
     *fmax_out = fmx;
-    free(q0); free(s0); free(vq); free(vs); free(gq); free(gs); free(mu_ex); free(tmp);
+    free(q0); free(s0); free(vq); free(vs); free(gq); free(gs); free(mu_ex); free(tmp); free(fs);
     free(off); free(idx);
     return status;
 }

@@ -1,0 +1,754 @@
+// api.cu -- the C ABI declared in include/mxe.h: context, workspace ownership,
+// call ordering and status mapping.  Every compute step is a kernel launched
+// on the context's stream; this file holds host logic only.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "mxe_internal.cuh"
+
+using namespace mxe;
+
+struct mxe_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0;
+  int S = 1;
+  int precision = 0;
+  int nl = 8;
+  mxe_box box{};
+  mxe_potential pot{};
+  DevPot dp{};
+  DevGrid grid{};
+
+  // cell grid
+  int* cell_of = nullptr;
+  int* cell_slot = nullptr;
+  int* abs_cell = nullptr;  // [3][n]
+  int* cell_count = nullptr;
+  int* cell_start = nullptr;
+  int* cell_sites = nullptr;
+  float4* qf = nullptr;  // FP32 copies of the positions for the neighbour prefilter
+  int64_t ncell_cap = 0;
+
+  // neighbour / bond CSR
+  int* nb_cnt = nullptr;
+  int* bd_cnt = nullptr;
+  int* nb_off = nullptr;
+  int* bd_off = nullptr;
+  uint32_t* nb_ent = nullptr;
+  int* bd_idx = nullptr;
+  int64_t nb_cap = 0, bd_cap = 0;
+  long long* scan_tmp = nullptr;
+  int64_t scan_len = 0;
+  long long* totals = nullptr;  // [4]: cells, neighbours, bonds, spare
+  int* max_row = nullptr;
+  unsigned long long* smax_bits = nullptr;
+  int64_t n_pairs = 0, n_bonds = 0;
+  int max_row_h = 0;
+  bool have_list = false;
+  double r_list = 0, skin = 0.2, r_bond = 0, sigma_max_build = 0;
+  double* q_build = nullptr;
+
+  // per-site work arrays
+  double *rho_bar = nullptr, *rho_avg = nullptr, *a = nullptr, *b = nullptr, *e = nullptr;
+  float4 *pos32 = nullptr, *x32 = nullptr, *ab32 = nullptr;
+  double *gq = nullptr, *gs = nullptr, *mu_ex = nullptr;
+  double* site_E = nullptr;
+  double* partials = nullptr;
+  double* F4_tmp = nullptr;
+  double *vq = nullptr, *vs = nullptr, *q0 = nullptr, *s0 = nullptr;
+  double* x_new = nullptr;
+  double* flux_tmp = nullptr;  // per-site factors of the Euler step
+  int* flags = nullptr;
+  int* step_flags = nullptr;
+  Ctrl* ctrl = nullptr;
+
+  // pinned host mirrors
+  Ctrl* ctrl_h = nullptr;
+  long long* totals_h = nullptr;
+  int* ints_h = nullptr;
+  unsigned long long* bits_h = nullptr;
+};
+
+namespace {
+
+struct Guard {  // keep the caller's current device, switch to the context's
+  int prev = 0;
+  bool ok = false;
+  explicit Guard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~Guard() {
+    if (ok) cudaSetDevice(prev);
+  }
+};
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t _e = (call);                      \
+    if (_e != cudaSuccess) return map_cuda(_e);   \
+  } while (0)
+
+mxe_status map_cuda(cudaError_t e) {
+  cudaGetLastError();  // clear a non-sticky error so it does not surface in the caller's next CUDA call
+  return e == cudaErrorMemoryAllocation ? MXE_ERR_OOM : MXE_ERR_CUDA;
+}
+
+// cudaMemcpyAsync / cudaMemsetAsync that accept an empty range with null pointers
+cudaError_t copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+mxe_status map_flags(int f) {
+  if (f & kFlagGeometry) return MXE_ERR_GEOMETRY;
+  if (f & kFlagNonfinite) return MXE_ERR_NONFINITE;
+  if (f & kFlagXRange) return MXE_ERR_X_RANGE;
+  if (f & kFlagBoxTooSmall) return MXE_ERR_BOX_TOO_SMALL;
+  if (f & kFlagOverflow) return MXE_ERR_NBR_OVERFLOW;
+  return MXE_OK;
+}
+
+// Distinct radial terms of the potential (dedupe identical (A, kappa, lambda)).
+int add_fn(RadialFn* tab, int& count, int cap, double A, double kappa, double lambda) {
+  if (A == 0.0) return -1;
+  for (int u = 0; u < count; ++u)
+    if (tab[u].A == A && tab[u].kappa == kappa && tab[u].lambda == lambda) return u;
+  if (count >= cap) return -2;
+  RadialFn& F = tab[count];
+  F.A = A;
+  F.kappa = kappa;
+  F.lambda = lambda;
+  const double log2e = 1.4426950408889634;
+  F.c0 = (float)(std::log2(A) + kappa * log2e);
+  F.c1 = (float)(lambda * log2e);
+  F.lam_f = (float)lambda;
+  F.on = 1;
+  return count++;
+}
+
+mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
+  std::memset(&d, 0, sizeof(d));
+  const int S = p.n_species;
+  if (S < 1 || S > 2) return MXE_ERR_ARG;  // kernels are instantiated for S = 1, 2
+  if (!(p.r_cut > p.r_switch) || !(p.r_switch >= 0.0)) return MXE_ERR_ARG;
+  d.S = S;
+  for (int k = 0; k < kMaxS; ++k)
+    for (int l = 0; l < kMaxS; ++l) d.phi_of[k][l] = d.f_of[k][l] = -1;
+  for (int k = 0; k < S; ++k) {
+    if (!(p.E[k] >= 0.0)) return MXE_ERR_ARG;
+    d.E[k] = p.E[k];
+    for (int l = 0; l < S; ++l) {
+      if (!(p.phi_r0[k][l] > 0.0) || !(p.f_r0[k][l] > 0.0)) return MXE_ERR_ARG;
+      if (p.phi_A[k][l] < 0.0 || p.f_xi[k][l] < 0.0) return MXE_ERR_ARG;
+    }
+  }
+  for (int k = 0; k < S; ++k)
+    for (int l = k; l < S; ++l) {
+      double A, kap, lam;
+      if (p.cross_geomean && k != l) {
+        // sqrt(phi_kk phi_ll) = sqrt(A_k A_l) exp((p_k + p_l)/2 - (p_k/r0_k + p_l/r0_l)/2 r) S(r)
+        A = std::sqrt(p.phi_A[k][k] * p.phi_A[l][l]);
+        kap = 0.5 * (p.phi_p[k][k] + p.phi_p[l][l]);
+        lam = 0.5 * (p.phi_p[k][k] / p.phi_r0[k][k] + p.phi_p[l][l] / p.phi_r0[l][l]);
+      } else {
+        if (p.phi_A[k][l] != p.phi_A[l][k] || p.phi_p[k][l] != p.phi_p[l][k] || p.phi_r0[k][l] != p.phi_r0[l][k])
+          return MXE_ERR_ARG;
+        A = p.phi_A[k][l];
+        kap = p.phi_p[k][l];
+        lam = p.phi_p[k][l] / p.phi_r0[k][l];
+      }
+      int u = add_fn(d.phi, d.n_phi, kMaxPhiFn, A, kap, lam);
+      if (u == -2) return MXE_ERR_ARG;
+      d.phi_of[k][l] = d.phi_of[l][k] = (int8_t)u;
+    }
+  for (int k = 0; k < S; ++k)
+    for (int l = 0; l < S; ++l) {
+      int v = add_fn(d.f, d.n_f, kMaxFFn, p.f_xi[k][l], p.f_q[k][l], p.f_q[k][l] / p.f_r0[k][l]);
+      if (v == -2) return MXE_ERR_ARG;
+      d.f_of[k][l] = (int8_t)v;
+    }
+  d.rs = p.r_switch;
+  d.rc = p.r_cut;
+  d.inv_w = 1.0 / (p.r_cut - p.r_switch);
+  d.rs_f = (float)p.r_switch;
+  d.rc_f = (float)p.r_cut;
+  d.inv_w_f = (float)d.inv_w;
+  d.dS_scale_f = (float)(-30.0 * d.inv_w);
+  return MXE_OK;
+}
+
+bool state_ok(const mxe_ctx* c, const mxe_state* s) {
+  return s && s->n == c->n && (c->n == 0 || (s->q && s->sigma && s->x && s->T));
+}
+
+void fill_pass(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
+  std::memset(&A, 0, sizeof(A));
+  A.q = s->q;
+  A.sigma = s->sigma;
+  A.x = s->x;
+  A.T = s->T;
+  A.pos32 = c->pos32;
+  A.x32 = c->x32;
+  A.nb_off = c->nb_off;
+  A.nb_ent = c->nb_ent;
+  A.n = c->n;
+  A.rho_bar = c->rho_bar;
+  A.rho_avg = c->rho_avg;
+  A.a = c->a;
+  A.b = c->b;
+  A.e = c->e;
+  A.ab32 = c->ab32;
+  A.gq = c->gq;
+  A.gs = c->gs;
+  A.mu_ex = c->mu_ex;
+  A.mu = nullptr;
+  A.site_E = c->site_E;
+  A.ctrl = nullptr;
+  A.flags = c->flags;
+  A.check_skin = 0;
+}
+
+mxe_status ensure_cells(mxe_ctx* c, int64_t ncell) {
+  if (ncell <= c->ncell_cap) return MXE_OK;
+  dfree(c->cell_count);
+  dfree(c->cell_start);
+  int64_t cap = ncell + ncell / 4 + 16;
+  CK(dalloc(&c->cell_count, cap));
+  CK(dalloc(&c->cell_start, cap + 1));
+  c->ncell_cap = cap;
+  int64_t need = std::max<int64_t>(c->n, cap) + 1;
+  if (c->scan_len < scan_tmp_len(need)) {
+    dfree(c->scan_tmp);
+    c->scan_len = scan_tmp_len(need);
+    CK(dalloc(&c->scan_tmp, c->scan_len));
+  }
+  return MXE_OK;
+}
+
+mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bond) {
+  const int64_t n = c->n;
+  cudaStream_t st = c->stream;
+  c->have_list = false;
+  // max sigma -> r_list; max |q| -> error band of the FP32 prefilter
+  CK(cudaMemsetAsync(c->smax_bits, 0, 2 * sizeof(unsigned long long), st));
+  CK(launch_site_max(s->sigma, s->q, n, c->smax_bits, st));
+  CK(cudaMemcpyAsync(c->bits_h, c->smax_bits, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double smax, qmax;
+  std::memcpy(&smax, c->bits_h, sizeof(double));
+  std::memcpy(&qmax, c->bits_h + 1, sizeof(double));
+  const double r_list = (c->pot.r_cut + kSqrt6 * smax) + skin;
+  if (!std::isfinite(r_list)) return MXE_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!(c->box.L[a] >= 2.0 * r_list)) return MXE_ERR_BOX_TOO_SMALL;
+  DevGrid& g = c->grid;
+  // cells no smaller than r_list; a sparse box gets coarser cells so the grid
+  // never holds many more cells than sites
+  double cell_min = r_list * (1.0 + 1e-9);
+  int64_t ncell = 1;
+  for (int pass = 0; pass < 64; ++pass) {
+    ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      int nc = (int)std::floor(c->box.L[a] / cell_min);
+      if (nc < 3) nc = 1;
+      g.nc[a] = nc;
+      ncell *= nc;
+    }
+    if (ncell <= 8 * n + 4096) break;
+    cell_min *= 1.25;
+  }
+  double Lmax = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    g.L[a] = c->box.L[a];
+    g.invL[a] = 1.0 / c->box.L[a];
+    g.h[a] = c->box.L[a] / g.nc[a];
+    g.h_f[a] = (float)g.h[a];
+    g.L_f[a] = (float)g.L[a];
+    g.invL_f[a] = (float)g.invL[a];
+    Lmax = std::max(Lmax, g.L[a]);
+  }
+  // Error band of the FP32 |d|^2 (u = 2^-24): each component of d carries at
+  // most delta = 6 u Qmax (rounded positions and their difference) + u Lmax
+  // (rounded box length times the image count) + u r_list (last rounding),
+  // doubled for a differing image choice near half a box; then
+  // | |d|^2_f32 - |d|^2 | <= 2 sqrt3 r delta + 3 delta^2 + 3 u r^2, plus u r^2
+  // for the rounded cutoff; the band is twice that.
+  const double u = std::ldexp(1.0, -24);
+  const double delta = 2.0 * (6.0 * u * qmax + u * Lmax + u * r_list);
+  const double band_d = 2.0 * (2.0 * std::sqrt(3.0) * r_list * delta + 3.0 * delta * delta + 4.0 * u * r_list * r_list);
+  const float band = (float)(band_d * (1.0 + 1e-6));
+  mxe_status ms = ensure_cells(c, ncell);
+  if (ms != MXE_OK) return ms;
+  // cell lists
+  CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int) * ncell, st));
+  CK(launch_cell_assign(s->q, n, g, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st));
+  CK(launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st));
+  CK(launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st));
+  // counts
+  const double rl2 = r_list * r_list, rb2 = r_bond * r_bond;
+  CK(cudaMemsetAsync(c->max_row, 0, sizeof(int), st));
+  CK(launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
+                      rl2, rb2, band, c->nb_cnt, c->bd_cnt, c->max_row, st));
+  CK(launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st));
+  CK(launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st));
+  CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->ints_h, c->max_row, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const long long npairs = c->totals_h[1], nbonds = c->totals_h[2];
+  if (npairs > 2147483647LL || nbonds > 2147483647LL) return MXE_ERR_NBR_OVERFLOW;
+  if (npairs > c->nb_cap) {
+    dfree(c->nb_ent);
+    int64_t cap = npairs + npairs / 8 + 64;
+    CK(dalloc(&c->nb_ent, cap));
+    c->nb_cap = cap;
+  }
+  if (nbonds > c->bd_cap) {
+    dfree(c->bd_idx);
+    int64_t cap = nbonds + nbonds / 8 + 64;
+    CK(dalloc(&c->bd_idx, cap));
+    c->bd_cap = cap;
+  }
+  const int max_row = c->ints_h[0];
+  if ((int64_t)max_row * 5 > 200 * 1024) return MXE_ERR_NBR_OVERFLOW;
+  CK(launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
+                     c->abs_cell, rl2, rb2, band, c->nb_off, c->nb_ent, c->bd_off, c->bd_idx, max_row, st));
+  CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
+  c->n_pairs = npairs;
+  c->n_bonds = nbonds;
+  c->max_row_h = max_row;
+  c->r_list = r_list;
+  c->skin = skin;
+  c->r_bond = r_bond;
+  c->sigma_max_build = smax;
+  c->have_list = true;
+  return MXE_OK;
+}
+
+// Free energy and gradients.  want_mu: the chemical potentials are requested.
+// The FP32 paths evaluate mu (and then the energies) with the FP64 density and
+// chemical-potential passes: the flux step takes differences of neighbouring
+// mu, so their absolute error must stay far below kB T * 1e-7; the forces and
+// the relaxation use the FP32 passes.
+mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want_mu) {
+  cudaStream_t st = c->stream;
+  const bool fp32 = c->precision != MXE_FP64;
+  if (!fp32) {
+    CK(launch_density(0, c->nl, c->dp, c->grid, A, st));
+    CK(launch_gradient(0, want_mu ? kGradAll : kGradForce, c->nl, c->dp, c->grid, A, st));
+    return MXE_OK;
+  }
+  CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->pos32, c->x32, st));
+  if (!want_mu) {
+    CK(launch_density(c->precision, c->nl, c->dp, c->grid, A, st));
+    CK(launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st));
+    return MXE_OK;
+  }
+  CK(launch_density(0, c->nl, c->dp, c->grid, A, st));
+  CK(launch_gradient(0, kGradMu, c->nl, c->dp, c->grid, A, st));
+  CK(launch_pack_ab(c->a, c->b, c->n, c->S, c->ab32, st));
+  if (A.gq != nullptr || A.gs != nullptr) {
+    PassArgs F = A;
+    F.site_E = nullptr;  // energies already come from the FP64 pass
+    CK(launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, F, st));
+  }
+  return MXE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mxe_status_string(mxe_status s) {
+  switch (s) {
+    case MXE_OK: return "ok";
+    case MXE_ERR_ARG: return "invalid argument";
+    case MXE_ERR_CUDA: return "CUDA runtime error";
+    case MXE_ERR_OOM: return "device out of memory";
+    case MXE_ERR_BOX_TOO_SMALL: return "box length below 2 r_list";
+    case MXE_ERR_NBR_OVERFLOW: return "neighbour list too large";
+    case MXE_ERR_GEOMETRY: return "quadrature node closer than 0.5 A or static density <= 1e-12";
+    case MXE_ERR_NONFINITE: return "non-finite free energy or gradient";
+    case MXE_ERR_X_RANGE: return "Euler step leaves molar fractions outside [0, 1]";
+    case MXE_ERR_NO_CONVERGE: return "relaxation reached max_iter";
+    case MXE_ERR_STATE: return "call order violated (no neighbour list)";
+  }
+  return "unknown status";
+}
+
+mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* pot, int64_t n,
+                      mxe_precision precision, void* cuda_stream) {
+  if (!out) return MXE_ERR_ARG;
+  *out = nullptr;
+  if (!box || !pot || n < 0 || n >= (int64_t)kIdxMask) return MXE_ERR_ARG;
+  if (precision != MXE_FP64 && precision != MXE_FP32_MIXED && precision != MXE_FP32_FF) return MXE_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!(box->L[a] > 0.0) || !std::isfinite(box->L[a])) return MXE_ERR_ARG;
+  mxe_ctx* c = new (std::nothrow) mxe_ctx();
+  if (!c) return MXE_ERR_OOM;
+  mxe_status ms = make_devpot(*pot, c->dp);
+  if (ms != MXE_OK) {
+    delete c;
+    return ms;
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return MXE_ERR_CUDA;
+  }
+  c->stream = (cudaStream_t)cuda_stream;
+  c->n = n;
+  c->S = pot->n_species;
+  c->precision = precision;
+  c->box = *box;
+  c->pot = *pot;
+  if (const char* env = std::getenv("MXE_LANES_PER_SITE")) {
+    int v = std::atoi(env);
+    if (v == 1 || v == 4 || v == 8 || v == 16) c->nl = v;
+  }
+  const int64_t S = c->S;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  A(dalloc(&c->cell_of, n));
+  A(dalloc(&c->cell_slot, n));
+  A(dalloc(&c->abs_cell, 3 * n));
+  A(dalloc(&c->cell_sites, n));
+  A(dalloc(&c->nb_cnt, n));
+  A(dalloc(&c->bd_cnt, n));
+  A(dalloc(&c->nb_off, n + 1));
+  A(dalloc(&c->bd_off, n + 1));
+  A(dalloc(&c->totals, 4));
+  A(dalloc(&c->max_row, 1));
+  A(dalloc(&c->smax_bits, 2));
+  A(dalloc(&c->qf, n));
+  A(dalloc(&c->q_build, 3 * n));
+  A(dalloc(&c->rho_bar, S * n));
+  A(dalloc(&c->rho_avg, S * n));
+  A(dalloc(&c->a, S * n));
+  A(dalloc(&c->b, S * n));
+  A(dalloc(&c->e, S * n));
+  if (precision != MXE_FP64) {
+    A(dalloc(&c->pos32, n));
+    A(dalloc(&c->x32, n));
+    A(dalloc(&c->ab32, 2 * n));
+  }
+  A(dalloc(&c->gq, 3 * n));
+  A(dalloc(&c->gs, n));
+  A(dalloc(&c->mu_ex, S * n));
+  A(dalloc(&c->site_E, 3 * n));
+  A(dalloc(&c->partials, 3 * ((n + kReduceGroup - 1) / kReduceGroup + 1)));
+  A(dalloc(&c->F4_tmp, 4));
+  A(dalloc(&c->vq, 3 * n));
+  A(dalloc(&c->vs, n));
+  A(dalloc(&c->q0, 3 * n));
+  A(dalloc(&c->s0, n));
+  A(dalloc(&c->x_new, S * n));
+  A(dalloc(&c->flux_tmp, flux_scratch_len(n, (int)S)));
+  A(dalloc(&c->flags, 1));
+  A(dalloc(&c->step_flags, 1));
+  A(dalloc(&c->ctrl, 1));
+  A(cudaMallocHost((void**)&c->ctrl_h, sizeof(Ctrl)));
+  A(cudaMallocHost((void**)&c->totals_h, sizeof(long long) * 4));
+  A(cudaMallocHost((void**)&c->ints_h, sizeof(int) * 4));
+  A(cudaMallocHost((void**)&c->bits_h, sizeof(unsigned long long) * 2));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    mxe_destroy(c);
+    return map_cuda(e);
+  }
+  *out = c;
+  return MXE_OK;
+}
+
+mxe_status mxe_destroy(mxe_ctx* c) {
+  if (!c) return MXE_OK;
+  Guard gd(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dfree(c->cell_of);
+  dfree(c->cell_slot);
+  dfree(c->abs_cell);
+  dfree(c->cell_count);
+  dfree(c->cell_start);
+  dfree(c->cell_sites);
+  dfree(c->nb_cnt);
+  dfree(c->bd_cnt);
+  dfree(c->nb_off);
+  dfree(c->bd_off);
+  dfree(c->nb_ent);
+  dfree(c->bd_idx);
+  dfree(c->scan_tmp);
+  dfree(c->totals);
+  dfree(c->max_row);
+  dfree(c->smax_bits);
+  dfree(c->qf);
+  dfree(c->q_build);
+  dfree(c->rho_bar);
+  dfree(c->rho_avg);
+  dfree(c->a);
+  dfree(c->b);
+  dfree(c->e);
+  dfree(c->pos32);
+  dfree(c->x32);
+  dfree(c->ab32);
+  dfree(c->gq);
+  dfree(c->gs);
+  dfree(c->mu_ex);
+  dfree(c->site_E);
+  dfree(c->partials);
+  dfree(c->F4_tmp);
+  dfree(c->vq);
+  dfree(c->vs);
+  dfree(c->q0);
+  dfree(c->s0);
+  dfree(c->x_new);
+  dfree(c->flux_tmp);
+  dfree(c->flags);
+  dfree(c->step_flags);
+  dfree(c->ctrl);
+  if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
+  if (c->totals_h) cudaFreeHost(c->totals_h);
+  if (c->ints_h) cudaFreeHost(c->ints_h);
+  if (c->bits_h) cudaFreeHost(c->bits_h);
+  delete c;
+  return MXE_OK;
+}
+
+mxe_status mxe_build_neighbors(mxe_ctx* c, const mxe_state* s, double skin, double r_bond, int64_t* n_pairs_out,
+                               double* r_list_out) {
+  if (!c || !state_ok(c, s) || !(skin >= 0.0) || !(r_bond >= 0.0)) return MXE_ERR_ARG;
+  Guard gd(c->device);
+  mxe_status ms = build_lists(c, s, skin, r_bond);
+  if (ms != MXE_OK) return ms;
+  if (n_pairs_out) *n_pairs_out = c->n_pairs;
+  if (r_list_out) *r_list_out = c->r_list;
+  return MXE_OK;
+}
+
+mxe_status mxe_export_neighbors(mxe_ctx* c, int32_t* offsets_dev, int32_t* idx_dev) {
+  if (!c) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  if (offsets_dev) CK(copy_d2d(offsets_dev, c->nb_off, sizeof(int32_t) * (c->n + 1), c->stream));
+  if (idx_dev) CK(launch_strip_codes(c->nb_ent, idx_dev, c->n_pairs, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MXE_OK;
+}
+
+mxe_status mxe_export_bonds(mxe_ctx* c, int32_t* offsets_dev, int32_t* idx_dev, int64_t* n_bonds_out) {
+  if (!c) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  if (offsets_dev) CK(copy_d2d(offsets_dev, c->bd_off, sizeof(int32_t) * (c->n + 1), c->stream));
+  if (idx_dev) CK(copy_d2d(idx_dev, c->bd_idx, sizeof(int32_t) * c->n_bonds, c->stream));
+  if (n_bonds_out) *n_bonds_out = c->n_bonds;
+  CK(cudaStreamSynchronize(c->stream));
+  return MXE_OK;
+}
+
+mxe_status mxe_sync_status(mxe_ctx* c) {
+  if (!c) return MXE_ERR_ARG;
+  Guard gd(c->device);
+  CK(cudaMemcpyAsync(c->ints_h, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int f = c->ints_h[0];
+  if (f) {
+    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return map_flags(f);
+}
+
+mxe_status mxe_free_energy_grad_async(mxe_ctx* c, const mxe_state* s, double* F4_dev, double* dFdq_dev,
+                                      double* dFdsigma_dev, double* mu_ex_dev, double* mu_dev) {
+  if (!c || !state_ok(c, s) || !F4_dev) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  PassArgs A;
+  fill_pass(c, s, A);
+  if (dFdq_dev) A.gq = dFdq_dev;
+  if (dFdsigma_dev) A.gs = dFdsigma_dev;
+  if (mu_ex_dev) A.mu_ex = mu_ex_dev;
+  A.mu = mu_dev;
+  if (!dFdq_dev) A.gq = nullptr;
+  if (!dFdsigma_dev) A.gs = nullptr;
+  const bool want_mu = mu_ex_dev != nullptr || mu_dev != nullptr;
+  if (!want_mu) A.mu_ex = nullptr;
+  mxe_status ms = enqueue_passes(c, s, A, want_mu);
+  if (ms != MXE_OK) return ms;
+  CK(launch_energy_reduce(c->site_E, c->n, c->partials, F4_dev, c->stream));
+  return MXE_OK;
+}
+
+mxe_status mxe_free_energy_grad(mxe_ctx* c, const mxe_state* s, double* F4_dev, double* dFdq_dev,
+                                double* dFdsigma_dev, double* mu_ex_dev, double* mu_dev) {
+  mxe_status ms = mxe_free_energy_grad_async(c, s, F4_dev, dFdq_dev, dFdsigma_dev, mu_ex_dev, mu_dev);
+  if (ms != MXE_OK) return ms;
+  return mxe_sync_status(c);
+}
+
+mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, const mxe_fire_params* fire,
+                     int32_t* iters_out, double* fmax_out) {
+  if (!c || !state_ok(c, s) || !(ftol >= 0.0) || max_iter < 0) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  mxe_fire_params fp = {0.02, 0.1, 1.1, 0.5, 0.1, 0.99, 0.0, 5, 16};
+  if (fire) fp = *fire;
+  const int chunk = fp.check_every > 0 ? fp.check_every : 16;
+  const int64_t n = c->n;
+  cudaStream_t st = c->stream;
+  // clear stale device errors from earlier asynchronous calls into this call's result
+  mxe_status pre = mxe_sync_status(c);
+  if (pre != MXE_OK) return pre;
+  CK(copy_d2d(c->q0, s->q, sizeof(double) * 3 * n, st));
+  CK(copy_d2d(c->s0, s->sigma, sizeof(double) * n, st));
+  if (n > 0) {
+    CK(cudaMemsetAsync(c->vq, 0, sizeof(double) * 3 * n, st));
+    CK(cudaMemsetAsync(c->vs, 0, sizeof(double) * n, st));
+  }
+  Ctrl& H = *c->ctrl_h;
+  std::memset(&H, 0, sizeof(Ctrl));
+  H.max_iter = max_iter;
+  H.dt = fp.dt0;
+  H.alpha = fp.alpha0;
+  H.ftol = ftol;
+  H.skin = c->skin;
+  H.sigma_max_build = c->sigma_max_build;
+  H.dt_max = fp.dt_max;
+  H.f_inc = fp.f_inc;
+  H.f_dec = fp.f_dec;
+  H.alpha0 = fp.alpha0;
+  H.f_alpha = fp.f_alpha;
+  H.n_min = fp.n_min;
+  H.sigma_lo = kSigmaMin;
+  H.sigma_hi = fp.sigma_max > 0.0 ? fp.sigma_max : INFINITY;
+  CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  if (c->precision != MXE_FP64)
+    CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, st));
+  PassArgs A;
+  fill_pass(c, s, A);
+  A.ctrl = c->ctrl;
+  A.check_skin = 1;
+  A.site_E = nullptr;
+  mxe_status result = MXE_OK;
+  int last_iter = -1, rebuilds = 0;
+  for (;;) {
+    for (int it = 0; it < chunk; ++it) {
+      CK(launch_density(c->precision, c->nl, c->dp, c->grid, A, st));
+      CK(launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st));
+      CK(launch_fire_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->partials, c->ctrl, c->flags, st));
+      CK(launch_fire_logic(c->partials, n, c->ctrl, c->flags, st));
+      CK(launch_fire_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n, c->grid,
+                            c->precision != MXE_FP64 ? c->pos32 : nullptr, c->ctrl, st));
+    }
+    CK(cudaMemcpyAsync(&H, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (H.reason == kReasonNone) {
+      if (H.iter == last_iter) {  // no progress over a whole chunk: never expected
+        result = MXE_ERR_STATE;
+        break;
+      }
+      last_iter = H.iter;
+      continue;
+    }
+    last_iter = H.iter;
+    if (H.reason == kReasonConverged) {
+      result = MXE_OK;
+      break;
+    }
+    if (H.reason == kReasonMaxIter) {
+      result = MXE_ERR_NO_CONVERGE;
+      break;
+    }
+    if (H.reason == kReasonError) {
+      result = mxe_sync_status(c);
+      if (result == MXE_OK) result = MXE_ERR_NONFINITE;
+      break;
+    }
+    // rebuild: the skin criterion failed before the next evaluation
+    if (++rebuilds > max_iter + 16) {
+      result = MXE_ERR_STATE;
+      break;
+    }
+    mxe_status ms = build_lists(c, s, c->skin, c->r_bond);
+    if (ms != MXE_OK) {
+      result = ms;
+      break;
+    }
+    H.halted = 0;
+    H.reason = kReasonNone;
+    H.disp2_bits = 0ull;
+    H.smax_bits = 0ull;
+    H.sigma_max_build = c->sigma_max_build;
+    CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    if (c->precision != MXE_FP64)
+      CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, st));
+    // the rebuild may have reallocated the lists: take the current pointers
+    fill_pass(c, s, A);
+    A.ctrl = c->ctrl;
+    A.check_skin = 1;
+    A.site_E = nullptr;
+  }
+  if (iters_out) *iters_out = H.iter;
+  if (fmax_out) *fmax_out = H.fmax;
+  if (result != MXE_OK && result != MXE_ERR_NO_CONVERGE) {
+    CK(copy_d2d(s->q, c->q0, sizeof(double) * 3 * n, st));
+    CK(copy_d2d(s->sigma, c->s0, sizeof(double) * n, st));
+    CK(cudaStreamSynchronize(st));
+    // the list was built for the discarded iterate; rebuild it for the restored state
+    if (result != MXE_ERR_BOX_TOO_SMALL && result != MXE_ERR_NBR_OVERFLOW) build_lists(c, s, c->skin, c->r_bond);
+    else c->have_list = false;
+  }
+  return result;
+}
+
+mxe_status mxe_diffuse_step_async(mxe_ctx* c, mxe_state* s, const double* mu_ex_dev, double dt, double nu0,
+                                  double Qm) {
+  if (!c || !state_ok(c, s) || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm)) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  cudaStream_t st = c->stream;
+  const double* mu = mu_ex_dev;
+  if (!mu) {
+    PassArgs A;
+    fill_pass(c, s, A);
+    A.site_E = nullptr;
+    A.gq = nullptr;
+    A.gs = nullptr;
+    mxe_status ms = enqueue_passes(c, s, A, true);
+    if (ms != MXE_OK) return ms;
+    mu = c->mu_ex;
+  }
+  CK(cudaMemsetAsync(c->step_flags, 0, sizeof(int), st));
+  CK(launch_flux(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, c->flux_tmp, c->x_new,
+                 c->step_flags, st));
+  CK(launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, st));
+  return MXE_OK;
+}
+
+mxe_status mxe_diffuse_step(mxe_ctx* c, mxe_state* s, const double* mu_ex_dev, double dt, double nu0, double Qm) {
+  mxe_status ms = mxe_diffuse_step_async(c, s, mu_ex_dev, dt, nu0, Qm);
+  if (ms != MXE_OK) return ms;
+  return mxe_sync_status(c);
+}
+
+}  // extern "C"

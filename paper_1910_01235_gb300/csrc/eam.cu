@@ -1,0 +1,745 @@
+// eam.cu -- K7 pack, K2 density/embedding pass, K3 gradient pass, K6 energy reduction.
+//
+// Thermalized EAM (App. B.2) averaged with the third-degree rule of App. A:
+// for a pair (i, j) the 12 nodes move one of the two sites by +-sqrt(6) sigma
+// along one axis, each with weight 1/12; the static point is the mean
+// separation.  Embedding: Taylor-linearised about the static density
+// (Eq. F_taylor_mxe), so pass 1 needs rho_bar and <rho> of every site and pass
+// 2 needs the per-site coefficients a = x F''(rho_bar)(<rho> - rho_bar) and
+// b = x F'(rho_bar) of every neighbour.
+//
+// Work split: a team of NL consecutive lanes owns one site and strides over
+// its neighbour row; each lane evaluates the 13 points of a pair unrolled in
+// registers; the team reduces its per-site sums with warp shuffles.  The
+// neighbour rows are contiguous (CSR), so a team's index loads coalesce, and
+// the neighbours' packed float4 records are L1/L2-resident gathers.
+//
+// Precision variants (template PREC):
+//   0  FP64 everywhere.
+//   1  node arithmetic in FP32 from cell-relative FP32 positions (the pair
+//      separation is rebuilt from the image code, never from absolute FP32
+//      coordinates); each pair's 13-node partial sums are added into FP64
+//      per-site accumulators.
+//   2  as 1, with the per-site sums carried as float-float pairs (TwoSum).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mxe_internal.cuh"
+
+namespace mxe {
+namespace {
+
+// ---------------------------------------------------------------- accumulators
+struct AccD {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(float x) { v += (double)x; }
+  __device__ __forceinline__ double get() const { return v; }
+  __device__ __forceinline__ void team_reduce(int nl) {
+    for (int o = nl >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+};
+
+// Unevaluated sum hi + lo of floats; TwoSum (Knuth) keeps the rounding error
+// of every addition, so the pair carries about twice the float significand.
+struct AccFF {
+  float hi, lo;
+  __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    float s = hi + x;
+    float bp = s - hi;
+    float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ void team_reduce(int nl) {
+    for (int o = nl >> 1; o > 0; o >>= 1) {
+      float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+      float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      add(oh);
+      lo += ol;
+    }
+  }
+};
+
+template <int PREC>
+struct Traits;
+template <>
+struct Traits<0> {
+  using R = double;
+  using Acc = AccD;
+};
+template <>
+struct Traits<1> {
+  using R = float;
+  using Acc = AccD;
+};
+template <>
+struct Traits<2> {
+  using R = float;
+  using Acc = AccFF;
+};
+
+// ---------------------------------------------------------------- math
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 1/r and r from r^2
+__device__ __forceinline__ void r_from_r2(float r2, float& r, float& rinv) {
+  rinv = rsqrt_approx(r2);
+  r = r2 * rinv;
+}
+__device__ __forceinline__ void r_from_r2(double r2, double& r, double& rinv) {
+  r = sqrt(r2);
+  rinv = 1.0 / r;
+}
+
+// quintic switch S(r) and dS/dr
+__device__ __forceinline__ void sw(const DevPot& P, float r, float& S, float& dS) {
+  float t = fminf(fmaxf((r - P.rs_f) * P.inv_w_f, 0.f), 1.f);
+  float t2 = t * t;
+  float u = 1.f - t;
+  S = fmaf(t2 * t, fmaf(t, fmaf(-6.f, t, 15.f), -10.f), 1.f);
+  dS = (t2 * (u * u)) * P.dS_scale_f;
+}
+__device__ __forceinline__ void sw(const DevPot& P, double r, double& S, double& dS) {
+  double t = fmin(fmax((r - P.rs) * P.inv_w, 0.0), 1.0);
+  double t2 = t * t;
+  double u = 1.0 - t;
+  S = fma(t2 * t, fma(t, fma(-6.0, t, 15.0), -10.0), 1.0);
+  dS = (t2 * (u * u)) * (-30.0 * P.inv_w);
+}
+
+// raw exponential part of a radial term
+__device__ __forceinline__ float rad_raw(const RadialFn& F, float r) { return ex2_approx(fmaf(-F.c1, r, F.c0)); }
+__device__ __forceinline__ double rad_raw(const RadialFn& F, double r) { return F.A * exp(F.kappa - F.lambda * r); }
+__device__ __forceinline__ float rad_lam(const RadialFn& F, float) { return F.lam_f; }
+__device__ __forceinline__ double rad_lam(const RadialFn& F, double) { return F.lambda; }
+
+template <typename T>
+__device__ __forceinline__ T sqrt6();
+template <>
+__device__ __forceinline__ float sqrt6<float>() { return 2.44948974f; }
+template <>
+__device__ __forceinline__ double sqrt6<double>() { return kSqrt6; }
+
+// ---------------------------------------------------------------- site data
+template <int PREC, int S>
+struct SiteData {
+  using R = typename Traits<PREC>::R;
+  R p[3];     // FP64: absolute position; FP32: cell-relative position
+  R sig;
+  R x[S];
+};
+
+template <int S>
+__device__ __forceinline__ void load_site(const PassArgs& A, int64_t j, SiteData<0, S>& d) {
+  const int64_t n = A.n;
+  d.p[0] = A.q[j];
+  d.p[1] = A.q[n + j];
+  d.p[2] = A.q[2 * n + j];
+  d.sig = A.sigma[j];
+#pragma unroll
+  for (int k = 0; k < S; ++k) d.x[k] = A.x[k * n + j];
+}
+template <int PREC, int S>
+__device__ __forceinline__ void load_site(const PassArgs& A, int64_t j, SiteData<PREC, S>& d) {
+  float4 P = __ldg(&A.pos32[j]);
+  d.p[0] = P.x;
+  d.p[1] = P.y;
+  d.p[2] = P.z;
+  d.sig = P.w;
+  float4 X = __ldg(&A.x32[j]);
+  float xs[4] = {X.x, X.y, X.z, X.w};
+#pragma unroll
+  for (int k = 0; k < S; ++k) d.x[k] = xs[k];
+}
+
+// separation d = q_j - q_i
+template <int S>
+__device__ __forceinline__ void separation(const DevGrid& g, const SiteData<0, S>& si, const SiteData<0, S>& sj,
+                                           uint32_t, double d[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double da = sj.p[a] - si.p[a];
+    d[a] = da - g.L[a] * rint(da * g.invL[a]);
+  }
+}
+template <int PREC, int S>
+__device__ __forceinline__ void separation(const DevGrid& g, const SiteData<PREC, S>& si,
+                                           const SiteData<PREC, S>& sj, uint32_t code, float d[3]) {
+  int c = (int)(code);
+  int s[3] = {c / 9 - 1, (c / 3) % 3 - 1, c % 3 - 1};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = (sj.p[a] - si.p[a]) + (float)s[a] * g.h_f[a];
+}
+
+// neighbours' embedding coefficients for pass 2
+template <int S>
+__device__ __forceinline__ void load_ab(const PassArgs& A, int64_t j, double a[S], double b[S],
+                                        SiteData<0, S>*) {
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    a[k] = A.a[k * A.n + j];
+    b[k] = A.b[k * A.n + j];
+  }
+}
+template <int PREC, int S>
+__device__ __forceinline__ void load_ab(const PassArgs& A, int64_t j, float a[S], float b[S],
+                                        SiteData<PREC, S>*) {
+  float4 v0 = __ldg(&A.ab32[2 * j]);
+  a[0] = v0.x;
+  b[0] = v0.y;
+  if (S > 1) {
+    a[1 < S ? 1 : 0] = v0.z;
+    b[1 < S ? 1 : 0] = v0.w;
+  }
+  if (S > 2) {
+    float4 v1 = __ldg(&A.ab32[2 * j + 1]);
+    a[2 < S ? 2 : 0] = v1.x;
+    b[2 < S ? 2 : 0] = v1.y;
+    if (S > 3) {
+      a[3 < S ? 3 : 0] = v1.z;
+      b[3 < S ? 3 : 0] = v1.w;
+    }
+  }
+}
+
+__device__ __forceinline__ bool skin_violated(const Ctrl* c) {
+  double disp = sqrt(__longlong_as_double((long long)c->disp2_bits));
+  double smax = __longlong_as_double((long long)c->smax_bits);
+  return 2.0 * disp + kSqrt6 * (smax - c->sigma_max_build) > c->skin;
+}
+
+// Uniform early exit of the relaxation chunk.  Returns true if the kernel must stop.
+__device__ __forceinline__ bool chunk_halted(const PassArgs& A) {
+  if (A.ctrl == nullptr) return false;
+  if (A.ctrl->halted) return true;
+  if (A.check_skin && skin_violated(A.ctrl)) {
+    if (threadIdx.x == 0) {
+      A.ctrl->reason = kReasonRebuild;
+      A.ctrl->halted = 1;
+    }
+    return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- K2: density pass
+template <int PREC, int S, int NL>
+__global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A) {
+  using R = typename Traits<PREC>::R;
+  using Acc = typename Traits<PREC>::Acc;
+  constexpr int NF = S * S;
+  if (chunk_halted(A)) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  Acc rb[S], ra[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    rb[k].zero();
+    ra[k].zero();
+  }
+  int bad = 0;
+  if (active) {
+    SiteData<PREC, S> si;
+    load_site(A, i, si);
+    const R s_i = sqrt6<R>() * si.sig;
+    const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+    for (int t = beg + lane; t < end; t += NL) {
+      const uint32_t ent = __ldg(&A.nb_ent[t]);
+      const int64_t j = ent & kIdxMask;
+      SiteData<PREC, S> sj;
+      load_site(A, j, sj);
+      R d[3];
+      separation(g, si, sj, ent >> kCodeShift, d);
+      const R s_j = sqrt6<R>() * sj.sig;
+      const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      R fst[NF], fav[NF];
+      // static point
+      {
+        R r, rinv, Sw, dS;
+        r_from_r2(D2, r, rinv);
+        bad |= D2 < (R)(kRMin * kRMin);
+        sw(P, r, Sw, dS);
+#pragma unroll
+        for (int v = 0; v < NF; ++v) {
+          fst[v] = (v < P.n_f) ? rad_raw(P.f[v], r) * Sw : (R)0;
+          fav[v] = (R)0;
+        }
+      }
+      // 12 nodes: site i moved (base_i), site j moved (base_j), each +-s along each axis
+#pragma unroll
+      for (int site = 0; site < 2; ++site) {
+        const R s = site == 0 ? s_i : s_j;
+        const R base = D2 + s * s;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R tw = (R)2 * s * d[a];
+#pragma unroll
+          for (int pm = 0; pm < 2; ++pm) {
+            const R r2 = pm == 0 ? base + tw : base - tw;
+            R r, rinv, Sw, dS;
+            r_from_r2(r2, r, rinv);
+            bad |= r2 < (R)(kRMin * kRMin);
+            sw(P, r, Sw, dS);
+#pragma unroll
+            for (int v = 0; v < NF; ++v)
+              if (v < P.n_f) fav[v] += rad_raw(P.f[v], r) * Sw;
+          }
+        }
+      }
+      // rho_i^k += sum_l x_jl f_kl
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        R sb = 0, sa = 0;
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+          for (int v = 0; v < NF; ++v)
+            if (P.f_of[k][l] == v) {
+              sb += sj.x[l] * fst[v];
+              sa += sj.x[l] * fav[v];
+            }
+        rb[k].add(sb);
+        ra[k].add(sa);
+      }
+    }
+  }
+  if (NL > 1) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      rb[k].team_reduce(NL);
+      ra[k].team_reduce(NL);
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+  }
+  if (!active || lane != 0) {
+    if (bad && active) atomicOr(A.flags, kFlagGeometry);
+    return;
+  }
+  const int64_t n = A.n;
+  int flag = bad ? kFlagGeometry : 0;
+  float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const double rbar = rb[k].get();
+    const double ravg = ra[k].get() * (1.0 / 12.0);
+    const double xk = A.x[k * n + i];
+    double e = 0.0, ak = 0.0, bk = 0.0;
+    if (rbar > kRhoMin) {
+      const double sq = sqrt(rbar);
+      const double F = -P.E[k] * sq;
+      const double dF = -P.E[k] / (2.0 * sq);
+      const double d2F = P.E[k] / (4.0 * rbar * sq);
+      e = F + dF * (ravg - rbar);
+      ak = xk * d2F * (ravg - rbar);
+      bk = xk * dF;
+    } else {
+      flag |= kFlagGeometry;
+    }
+    A.rho_bar[k * n + i] = rbar;
+    A.rho_avg[k * n + i] = ravg;
+    A.e[k * n + i] = e;
+    A.a[k * n + i] = ak;
+    A.b[k * n + i] = bk;
+    ab[2 * k] = (float)ak;
+    ab[2 * k + 1] = (float)bk;
+  }
+  if (PREC != 0) {
+    A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
+    if (S > 2) A.ab32[2 * i + 1] = make_float4(ab[4], ab[5], ab[6], ab[7]);
+  }
+  if (flag) atomicOr(A.flags, flag);
+}
+
+// ---------------------------------------------------------------- K3: gradient pass
+// MODE kGradAll: dF/dq, dF/dsigma, mu, energies; kGradForce: dF/dq, dF/dsigma,
+// energies (no mu); kGradMu: mu and energies only (no derivatives).
+template <int PREC, int S, int NL, int MODE>
+__global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs A) {
+  constexpr bool DER = MODE != kGradMu;
+  constexpr bool MU = MODE != kGradForce;
+  using R = typename Traits<PREC>::R;
+  using Acc = typename Traits<PREC>::Acc;
+  constexpr int NF = S * S;
+  constexpr int NP = S * (S + 1) / 2;
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  Acc gacc[3], gsig, mu[S], epair;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gacc[c].zero();
+  gsig.zero();
+  epair.zero();
+#pragma unroll
+  for (int k = 0; k < S; ++k) mu[k].zero();
+  if (active) {
+    SiteData<PREC, S> si;
+    load_site(A, i, si);
+    R ai[S], bi[S];
+    load_ab(A, i, ai, bi, (SiteData<PREC, S>*)nullptr);
+    const R s_i = sqrt6<R>() * si.sig;
+    const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+    for (int t = beg + lane; t < end; t += NL) {
+      const uint32_t ent = __ldg(&A.nb_ent[t]);
+      const int64_t j = ent & kIdxMask;
+      SiteData<PREC, S> sj;
+      load_site(A, j, sj);
+      R aj[S], bj[S];
+      load_ab(A, j, aj, bj, (SiteData<PREC, S>*)nullptr);
+      R d[3];
+      separation(g, si, sj, ent >> kCodeShift, d);
+      const R s_j = sqrt6<R>() * sj.sig;
+      const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      // pair weights of the distinct radial terms
+      R cphi[NP], cfa[NF], cfs[NF];
+#pragma unroll
+      for (int u = 0; u < NP; ++u) cphi[u] = 0;
+#pragma unroll
+      for (int v = 0; v < NF; ++v) {
+        cfa[v] = 0;
+        cfs[v] = 0;
+      }
+#pragma unroll
+      for (int k = 0; k < S; ++k)
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+#pragma unroll
+          for (int u = 0; u < NP; ++u)
+            if (P.phi_of[k][l] == u) cphi[u] += si.x[k] * sj.x[l];
+#pragma unroll
+          for (int v = 0; v < NF; ++v)
+            if (P.f_of[k][l] == v) {
+              cfa[v] += bi[k] * sj.x[l] + bj[k] * si.x[l];
+              cfs[v] += ai[k] * sj.x[l] + aj[k] * si.x[l];
+            }
+        }
+      // static point: density terms only
+      R fst[NF], Gs;
+      {
+        R r, rinv, Sw, dS;
+        r_from_r2(D2, r, rinv);
+        sw(P, r, Sw, dS);
+        Gs = 0;
+#pragma unroll
+        for (int v = 0; v < NF; ++v) {
+          fst[v] = 0;
+          if (v < P.n_f) {
+            const R e = rad_raw(P.f[v], r);
+            fst[v] = e * Sw;
+            Gs += cfs[v] * (e * (dS - rad_lam(P.f[v], r) * Sw));
+          }
+        }
+        Gs *= rinv;
+      }
+      // 12 nodes
+      R aphi[NP], af[NF];
+#pragma unroll
+      for (int u = 0; u < NP; ++u) aphi[u] = 0;
+#pragma unroll
+      for (int v = 0; v < NF; ++v) af[v] = 0;
+      R T = 0, U[3] = {0, 0, 0}, Vs = 0;
+#pragma unroll
+      for (int site = 0; site < 2; ++site) {
+        const R s = site == 0 ? s_i : s_j;
+        const R base = D2 + s * s;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R tw = (R)2 * s * d[a];
+          R w2[2];
+#pragma unroll
+          for (int pm = 0; pm < 2; ++pm) {
+            const R r2 = pm == 0 ? base + tw : base - tw;
+            R r, rinv, Sw, dS;
+            r_from_r2(r2, r, rinv);
+            sw(P, r, Sw, dS);
+            R G = 0;
+#pragma unroll
+            for (int u = 0; u < NP; ++u)
+              if (u < P.n_phi) {
+                const R e = rad_raw(P.phi[u], r);
+                aphi[u] += e * Sw;
+                if (DER) G += cphi[u] * (e * (dS - rad_lam(P.phi[u], r) * Sw));
+              }
+#pragma unroll
+            for (int v = 0; v < NF; ++v)
+              if (v < P.n_f) {
+                const R e = rad_raw(P.f[v], r);
+                if (MU) af[v] += e * Sw;
+                if (DER) G += cfa[v] * (e * (dS - rad_lam(P.f[v], r) * Sw));
+              }
+            w2[pm] = G * rinv;
+          }
+          T += w2[0] + w2[1];
+          U[a] += s * (w2[0] - w2[1]);
+          if (site == 0) Vs += sqrt6<R>() * ((d[a] + s) * w2[0] - (d[a] - s) * w2[1]);
+        }
+      }
+      const R inv12 = (R)(1.0 / 12.0);
+      if (DER) {
+        const R Tt = T * inv12 + Gs;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gacc[c].add(-(d[c] * Tt + U[c] * inv12));
+        gsig.add(Vs * inv12);
+      }
+      R ep = 0;
+#pragma unroll
+      for (int u = 0; u < NP; ++u) ep += cphi[u] * aphi[u];
+      epair.add((R)0.5 * inv12 * ep);
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        if (!MU) break;
+        R m = 0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+#pragma unroll
+          for (int u = 0; u < NP; ++u)
+            if (P.phi_of[k][l] == u) m += sj.x[l] * aphi[u] * inv12;
+          // density at j of species l from this site holding species k: f_lk
+#pragma unroll
+          for (int v = 0; v < NF; ++v)
+            if (P.f_of[l][k] == v) m += aj[l] * fst[v] + bj[l] * af[v] * inv12;
+        }
+        mu[k].add(m);
+      }
+    }
+  }
+  if (NL > 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gacc[c].team_reduce(NL);
+    gsig.team_reduce(NL);
+    epair.team_reduce(NL);
+#pragma unroll
+    for (int k = 0; k < S; ++k) mu[k].team_reduce(NL);
+  }
+  if (!active || lane != 0) return;
+  const int64_t n = A.n;
+  const double kT = kKB * A.T[i];
+  const double sg = A.sigma[i];
+  int flag = 0;
+  double g0 = gacc[0].get(), g1 = gacc[1].get(), g2 = gacc[2].get();
+  double gs = gsig.get() - 3.0 * kT / sg;
+  if (DER && A.gq) {
+    A.gq[i] = g0;
+    A.gq[n + i] = g1;
+    A.gq[2 * n + i] = g2;
+  }
+  if (DER && A.gs) A.gs[i] = gs;
+  double xv = 1.0, mix = 0.0, emb = 0.0;
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const double xk = A.x[k * n + i];
+    xv -= xk;
+    if (xk > 0.0) mix += xk * log(xk);
+    emb += xk * A.e[k * n + i];
+  }
+  if (xv > 0.0) mix += xv * log(xv);
+  bool finite = !DER || (isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs));
+  if (MU) {
+    const double lv = log(fmax(xv, kLogFloor));
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const double m = mu[k].get() + A.e[k * n + i];
+      finite = finite && isfinite(m);
+      if (A.mu_ex) A.mu_ex[k * n + i] = m;
+      if (A.mu) A.mu[k * n + i] = m + kT * (log(fmax(A.x[k * n + i], kLogFloor)) - lv);
+    }
+  }
+  const double EV = epair.get() + emb;
+  const double Fv = -3.0 * kT * log(sg);
+  const double Fm = kT * mix;
+  if (A.site_E) {
+    A.site_E[i] = EV;
+    A.site_E[n + i] = Fv;
+    A.site_E[2 * n + i] = Fm;
+  }
+  if (!(finite && isfinite(EV) && isfinite(Fv) && isfinite(Fm))) flag |= kFlagNonfinite;
+  if (flag) atomicOr(A.flags, flag);
+}
+
+// ---------------------------------------------------------------- K7: pack
+__global__ void k_pack(const double* __restrict__ q, const double* __restrict__ sigma, const double* __restrict__ x,
+                       const int* __restrict__ abs_cell, int64_t n, int S, DevGrid g, float4* __restrict__ pos32,
+                       float4* __restrict__ x32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float p[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) p[a] = (float)(q[a * n + i] - (double)abs_cell[a * n + i] * g.h[a]);
+  pos32[i] = make_float4(p[0], p[1], p[2], (float)sigma[i]);
+  float xs[4] = {0, 0, 0, 0};
+  for (int k = 0; k < S && k < 4; ++k) xs[k] = (float)x[k * n + i];
+  x32[i] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+}
+
+// FP64 embedding coefficients -> the packed FP32 records the FP32 gradient pass gathers
+__global__ void k_pack_ab(const double* __restrict__ a, const double* __restrict__ b, int64_t n, int S,
+                          float4* __restrict__ ab32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < S && k < 4; ++k) {
+    v[2 * k] = (float)a[k * n + i];
+    v[2 * k + 1] = (float)b[k * n + i];
+  }
+  ab32[2 * i] = make_float4(v[0], v[1], v[2], v[3]);
+  if (S > 2) ab32[2 * i + 1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// ---------------------------------------------------------------- K6: energy totals
+// Fixed grouping (kReduceGroup sites per partial, fixed tree inside a group,
+// groups summed in order by one block), so the totals do not depend on any
+// launch shape.
+__global__ void k_energy_partials(const double* __restrict__ site_E, int64_t n, int64_t ngroups,
+                                  double* __restrict__ partials) {
+  __shared__ double sh[3][kReduceGroup / 4];
+  const int64_t grp = blockIdx.x;
+  const int tid = threadIdx.x;  // blockDim = kReduceGroup / 4
+  for (int c = 0; c < 3; ++c) {
+    double v = 0.0;
+    for (int r = 0; r < 4; ++r) {
+      int64_t i = grp * kReduceGroup + r * (kReduceGroup / 4) + tid;
+      if (i < n) v += site_E[c * n + i];
+    }
+    sh[c][tid] = v;
+  }
+  __syncthreads();
+  for (int w = kReduceGroup / 8; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int c = 0; c < 3; ++c) partials[c * ngroups + grp] = sh[c][0];
+}
+
+__global__ void k_energy_final(const double* __restrict__ partials, int64_t ngroups, double* __restrict__ F4) {
+  __shared__ double sh[3][256];
+  const int tid = threadIdx.x;
+  for (int c = 0; c < 3; ++c) {
+    double v = 0.0;
+    for (int64_t gi = tid; gi < ngroups; gi += 256) v += partials[c * ngroups + gi];
+    sh[c][tid] = v;
+  }
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    F4[0] = sh[0][0];
+    F4[1] = sh[1][0];
+    F4[2] = sh[2][0];
+    F4[3] = (sh[0][0] + sh[1][0]) + sh[2][0];
+  }
+}
+
+template <int PREC, int S, int NL>
+cudaError_t launch_density_t(const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t work = a.n * NL;
+  k_density<PREC, S, NL><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(P, g, a);
+  return cudaGetLastError();
+}
+template <int PREC, int S, int NL>
+cudaError_t launch_gradient_t(int mode, const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t work = a.n * NL;
+  const unsigned blocks = (unsigned)((work + threads - 1) / threads);
+  if (mode == kGradForce) {
+    k_gradient<PREC, S, NL, kGradForce><<<blocks, threads, 0, s>>>(P, g, a);
+  } else if (PREC == 0) {
+    // the FP64 instantiations also serve the accurate chemical potentials of the FP32 paths
+    if (mode == kGradAll)
+      k_gradient<0, S, NL, kGradAll><<<blocks, threads, 0, s>>>(P, g, a);
+    else
+      k_gradient<0, S, NL, kGradMu><<<blocks, threads, 0, s>>>(P, g, a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// mode < 0: density pass; otherwise the gradient pass in that mode
+template <int PREC, int S>
+cudaError_t dispatch_nl(int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
+  switch (nl) {
+    case 1: return mode >= 0 ? launch_gradient_t<PREC, S, 1>(mode, P, g, a, s) : launch_density_t<PREC, S, 1>(P, g, a, s);
+    case 4: return mode >= 0 ? launch_gradient_t<PREC, S, 4>(mode, P, g, a, s) : launch_density_t<PREC, S, 4>(P, g, a, s);
+    case 8: return mode >= 0 ? launch_gradient_t<PREC, S, 8>(mode, P, g, a, s) : launch_density_t<PREC, S, 8>(P, g, a, s);
+    case 16:
+      return mode >= 0 ? launch_gradient_t<PREC, S, 16>(mode, P, g, a, s) : launch_density_t<PREC, S, 16>(P, g, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int PREC>
+cudaError_t dispatch_s(int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
+  switch (P.S) {
+    case 1: return dispatch_nl<PREC, 1>(mode, nl, P, g, a, s);
+    case 2: return dispatch_nl<PREC, 2>(mode, nl, P, g, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch(int mode, int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
+                     cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  switch (precision) {
+    case 0: return dispatch_s<0>(mode, nl, P, g, a, s);
+    case 1: return dispatch_s<1>(mode, nl, P, g, a, s);
+    case 2: return dispatch_s<2>(mode, nl, P, g, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const double* q, const double* sigma, const double* x, const int* abs_cell, int64_t n,
+                        int S, const DevGrid& g, float4* pos32, float4* x32, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, sigma, x, abs_cell, n, S, g, pos32, x32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
+                           cudaStream_t s) {
+  return dispatch(-1, precision, nl, P, g, a, s);
+}
+
+cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
+                            cudaStream_t s) {
+  return dispatch(mode, precision, nl, P, g, a, s);
+}
+
+cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_pack_ab<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n, S, ab32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s) {
+  int64_t ng = (n + kReduceGroup - 1) / kReduceGroup;
+  if (ng < 1) ng = 1;
+  k_energy_partials<<<(unsigned)ng, kReduceGroup / 4, 0, s>>>(site_E, n, ng, partials);
+  k_energy_final<<<1, 256, 0, s>>>(partials, ng, F4);
+  return cudaGetLastError();
+}
+
+}  // namespace mxe

@@ -1,0 +1,166 @@
+// mxe_internal.cuh -- types and launchers shared by the CUDA translation units
+// of the MXE library (never included by the oracle, never exported).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mxe.h"
+
+namespace mxe {
+
+constexpr int kMaxS = MXE_MAXS;
+constexpr int kMaxPhiFn = MXE_MAXS * (MXE_MAXS + 1) / 2;  // distinct symmetric pair terms
+constexpr int kMaxFFn = MXE_MAXS * MXE_MAXS;              // distinct density terms
+constexpr int kCodeShift = 27;                            // neighbour entry: j | image code << 27
+constexpr uint32_t kIdxMask = (1u << kCodeShift) - 1u;
+constexpr int kReduceGroup = 1024;                        // sites per fixed-order partial sum
+constexpr double kKB = 8.617333262e-5;                    // eV/K
+constexpr double kSqrt6 = 2.449489742783178098197284;     // node offset / sigma (App. A, r^2 = 3)
+constexpr double kRMin = 0.5;                             // smallest admissible node distance
+constexpr double kRhoMin = 1e-12;                         // smallest admissible static density
+constexpr double kXTol = 1e-12;                           // admissible excursion of x
+constexpr double kSigmaMin = 1e-3;                        // FIRE floor on sigma
+constexpr double kLogFloor = 1e-300;                      // ln-argument floor of the full mu
+
+// Device status bits (ORed by kernels, mapped to mxe_status by the host).
+enum : int {
+  kFlagGeometry = 1,
+  kFlagNonfinite = 2,
+  kFlagXRange = 4,
+  kFlagBoxTooSmall = 8,
+  kFlagOverflow = 16,
+};
+
+// One distinct radial term g(r) = A exp(kappa - lambda r) S(r).
+//  FP64: A, kappa, lambda.  FP32: g_raw = exp2(c0 - c1 r) with
+//  c0 = log2(A) + kappa log2(e), c1 = lambda log2(e).
+struct RadialFn {
+  double A, kappa, lambda;
+  float c0, c1, lam_f;
+  int on;
+};
+
+// Potential in the form the kernels read (passed by value).
+struct DevPot {
+  int S;
+  int n_phi, n_f;
+  RadialFn phi[kMaxPhiFn];
+  RadialFn f[kMaxFFn];
+  int8_t phi_of[kMaxS][kMaxS];   // species pair -> distinct phi term (-1: zero)
+  int8_t f_of[kMaxS][kMaxS];     // species pair -> distinct f term (-1: zero)
+  double E[kMaxS];
+  double rs, rc, inv_w;          // switch start, cutoff, 1/(rc - rs)
+  float rs_f, rc_f, inv_w_f, dS_scale_f;
+};
+
+// Box / cell grid for positions and image codes.
+struct DevGrid {
+  double L[3], invL[3], h[3];
+  float h_f[3], L_f[3], invL_f[3];
+  int nc[3];
+};
+
+// FIRE / relaxation control block living in device memory.
+struct Ctrl {
+  int flags;          // kFlag* bits
+  int halted;         // nonzero: remaining kernels of the chunk return at once
+  int reason;         // 1 converged, 2 max_iter, 3 rebuild needed, 4 error
+  int iter;           // FIRE updates done
+  int n_pos;
+  int max_iter;
+  double dt, alpha;
+  double ftol, skin;
+  double sigma_max_build;
+  double fmax;        // last max_i max(|g_q,i|, |g_sigma,i|)
+  unsigned long long fmax_bits;   // atomicMax of non-negative doubles
+  unsigned long long disp2_bits;  // max_i |q_i - q_build,i|^2 after the update
+  unsigned long long smax_bits;   // max_i sigma_i after the update
+  // scalars of the current update
+  double keep, mix, one_minus_alpha;
+  // FIRE constants
+  double dt_max, f_inc, f_dec, alpha0, f_alpha;
+  double sigma_lo, sigma_hi;      // box of the widths
+  int n_min;
+  int pad;
+};
+
+enum { kReasonNone = 0, kReasonConverged = 1, kReasonMaxIter = 2, kReasonRebuild = 3, kReasonError = 4 };
+
+// ---------------------------------------------------------------- launchers
+// neighbours.cu
+cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, int* cell_of, int* cell_slot,
+                               int* cell_count, int* abs_cell, float4* qf, cudaStream_t s);
+cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slot, const int* cell_start,
+                              int* cell_sites, cudaStream_t s);
+cudaError_t launch_nbr_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                             const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                             double rl2, double rb2, float band, int* nb_cnt, int* bd_cnt, int* max_row,
+                             cudaStream_t s);
+cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                            const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                            const int* abs_cell, double rl2, double rb2, float band, const int* nb_off,
+                            uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row, cudaStream_t s);
+// exclusive scan of n int32 counts into out[0..n] (out[n] = total, int64 total in *total64)
+cudaError_t launch_scan(const int* in, int* out, int64_t n, long long* total64, int* tmp, int64_t tmp_len,
+                        cudaStream_t s);
+int64_t scan_tmp_len(int64_t n);
+cudaError_t launch_strip_codes(const uint32_t* ent, int32_t* idx, int64_t m, cudaStream_t s);
+cudaError_t launch_site_max(const double* sigma, const double* q, int64_t n, unsigned long long* out_bits,
+                            cudaStream_t s);
+
+// eam.cu
+cudaError_t launch_pack(const double* q, const double* sigma, const double* x, const int* abs_cell, int64_t n,
+                        int S, const DevGrid& g, float4* pos32, float4* x32, cudaStream_t s);
+struct PassArgs {
+  const double* q;
+  const double* sigma;
+  const double* x;
+  const double* T;
+  const float4* pos32;
+  const float4* x32;
+  const int* nb_off;
+  const uint32_t* nb_ent;
+  int64_t n;
+  // pass-1 outputs / pass-2 inputs
+  double* rho_bar;
+  double* rho_avg;
+  double* a;
+  double* b;
+  double* e;
+  float4* ab32;     // [n][2] packed (a_k, b_k) for the mixed pass-2 gathers
+  // pass-2 outputs
+  double* gq;
+  double* gs;
+  double* mu_ex;
+  double* mu;
+  double* site_E;   // [3][n]: E_V, F_vib, F_mix per site
+  Ctrl* ctrl;       // optional: kernels return at once if ctrl->halted
+  int* flags;
+  int check_skin;   // pass 1 checks the rebuild criterion in ctrl first
+};
+cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
+                           cudaStream_t s);
+enum { kGradAll = 0, kGradForce = 1, kGradMu = 2 };
+cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
+                            cudaStream_t s);
+cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);
+cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s);
+
+// relax.cu
+cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
+                               const double* vs, int64_t n, double* partials, Ctrl* ctrl, int* flags, cudaStream_t s);
+cudaError_t launch_fire_logic(const double* partials, int64_t n, Ctrl* ctrl, int* flags, cudaStream_t s);
+cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
+                               const double* gs, const double* q_build, const int* abs_cell, int64_t n,
+                               const DevGrid& g, float4* pos32, Ctrl* ctrl, cudaStream_t s);
+
+// flux.cu
+int64_t flux_scratch_len(int64_t n, int S);
+cudaError_t launch_flux(const double* x, const double* T, const double* mu_ex, const int* bd_off, const int* bd_idx,
+                        int64_t n, int S, double dt, double nu0, double Qm, double* scratch, double* x_new,
+                        int* flags, cudaStream_t s);
+cudaError_t launch_commit_x(double* x, const double* x_new, int64_t count, const int* step_flags, int* flags,
+                            cudaStream_t s);
+
+}  // namespace mxe

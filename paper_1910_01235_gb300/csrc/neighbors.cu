@@ -1,0 +1,427 @@
+// neighbors.cu -- K1: cell-list neighbour and bond builder (Sec. 4, Algorithm 1,
+// neighbour-list step; Sec. 3: the transport sum runs over nearest neighbours).
+//
+// Membership is decided in FP64 with explicitly rounded operations (no FMA):
+//   d_a = (q_ja - q_ia) - L_a rint((q_ja - q_ia) * invL_a),  |d|^2 = (dx dx + dy dy) + dz dz
+// so the set is bit-reproducible against any IEEE evaluation of the same rule.
+// GB300 runs FP64 at 1/73 of the FP32 rate, so every candidate is first tested
+// in FP32 from rounded positions; only a candidate whose FP32 |d|^2 lies
+// inside a rigorous error band around the cutoff is decided by the FP64 rule
+// (the band bounds the position rounding, the image choice and the rounding
+// of |d|^2; outside it the FP32 and FP64 decisions agree).
+// One warp handles one site: lanes sweep the candidates of the distinct
+// neighbouring cells, accepted entries are compacted into shared memory with
+// ballots and placed in j order by rank counting.  Each entry stores j in the
+// low 27 bits and the periodic image code (cell offset in {-1,0,1}^3) above it,
+// which the FP32 kernels use to rebuild d from cell-relative positions.
+#include <cuda_runtime.h>
+
+#include "mxe_internal.cuh"
+
+namespace mxe {
+namespace {
+
+__global__ void k_cell_assign(const double* __restrict__ q, int64_t n, DevGrid g, int* __restrict__ cell_of,
+                              int* __restrict__ cell_slot, int* __restrict__ cell_count, int* __restrict__ abs_cell,
+                              float4* __restrict__ qf) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  qf[i] = make_float4((float)q[i], (float)q[n + i], (float)q[2 * n + i], 0.f);
+  int c3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double u = q[a * n + i] * g.invL[a];
+    double w = floor(u);
+    int c = (int)((u - w) * g.nc[a]);
+    c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+    c3[a] = c;
+    abs_cell[a * n + i] = (int)w * g.nc[a] + c;
+  }
+  int cell = (c3[0] * g.nc[1] + c3[1]) * g.nc[2] + c3[2];
+  cell_of[i] = cell;
+  cell_slot[i] = atomicAdd(&cell_count[cell], 1);
+}
+
+__global__ void k_cell_place(int64_t n, const int* __restrict__ cell_of, const int* __restrict__ cell_slot,
+                             const int* __restrict__ cell_start, int* __restrict__ cell_sites) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cell_sites[cell_start[cell_of[i]] + cell_slot[i]] = (int)i;
+}
+
+// The distinct cells of the 3x3x3 stencil around `cell` (duplicates removed
+// when an axis has fewer than 3 cells).
+struct Stencil {
+  int off[3][3];
+  int cnt[3];
+};
+
+__device__ __forceinline__ Stencil make_stencil(int cell, const DevGrid& g) {
+  Stencil st;
+  int c3[3] = {cell / (g.nc[1] * g.nc[2]), (cell / g.nc[2]) % g.nc[1], cell % g.nc[2]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    st.cnt[a] = 0;
+    for (int o = -1; o <= 1; ++o) {
+      int v = ((c3[a] + o) % g.nc[a] + g.nc[a]) % g.nc[a];
+      bool dup = false;
+      for (int t = 0; t < st.cnt[a]; ++t) dup |= st.off[a][t] == v;
+      if (!dup) st.off[a][st.cnt[a]++] = v;
+    }
+  }
+  return st;
+}
+
+struct PairTest {
+  double r2;
+  double k[3];
+};
+
+__device__ __forceinline__ PairTest pair_test(const double qi[3], const double* __restrict__ q, int64_t n, int j,
+                                              const DevGrid& g) {
+  PairTest t;
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double da = __dsub_rn(q[a * n + j], qi[a]);
+    double k = rint(__dmul_rn(da, g.invL[a]));
+    d[a] = __dsub_rn(da, __dmul_rn(g.L[a], k));
+    t.k[a] = k;
+  }
+  t.r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+  return t;
+}
+
+// FP32 estimate of the minimum-image |d|^2 and image counts
+struct PairTestF {
+  float r2;
+  float k[3];
+  bool near_half;  // a component near half a box length: take the FP64 image
+};
+
+__device__ __forceinline__ PairTestF pair_test_f(const float4& qi, const float4& qj, const DevGrid& g) {
+  PairTestF t;
+  const float dq[3] = {qj.x - qi.x, qj.y - qi.y, qj.z - qi.z};
+  float r2 = 0.f;
+  t.near_half = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float u = dq[a] * g.invL_f[a];
+    const float k = rintf(u);
+    const float d = fmaf(-g.L_f[a], k, dq[a]);
+    t.near_half |= fabsf(u - k) > 0.45f;
+    t.k[a] = k;
+    r2 = fmaf(d, d, r2);
+  }
+  t.r2 = r2;
+  return t;
+}
+
+// Decision for one cutoff: 1 inside, 0 outside, -1 undecided in FP32.
+__device__ __forceinline__ int decide_f(float r2f, float cut2f, float band) {
+  if (r2f < cut2f - band) return 1;
+  if (r2f > cut2f + band) return 0;
+  return -1;
+}
+
+__global__ void k_nbr_count(const double* __restrict__ q, const float4* __restrict__ qf,
+                            const uint8_t* __restrict__ sub, uint32_t mobile_mask, int64_t n, DevGrid g,
+                            const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                            const int* __restrict__ cell_sites, double rl2, double rb2, float band,
+                            int* __restrict__ nb_cnt, int* __restrict__ bd_cnt, int* __restrict__ max_row) {
+  const int lane = threadIdx.x & 31;
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;
+  double qi[3] = {q[i], q[n + i], q[2 * n + i]};
+  const float4 qfi = qf[i];
+  const float rl2f = (float)rl2, rb2f = (float)rb2;
+  int si = sub ? sub[i] : 0;
+  bool mob = (mobile_mask >> si) & 1u;
+  Stencil st = make_stencil(cell_of[i], g);
+  int cnt = 0, bcnt = 0;
+  for (int ax = 0; ax < st.cnt[0]; ++ax)
+    for (int ay = 0; ay < st.cnt[1]; ++ay)
+      for (int az = 0; az < st.cnt[2]; ++az) {
+        int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+        int beg = cell_start[c], end = cell_start[c + 1];
+        for (int t0 = beg; t0 < end; t0 += 32) {
+          int t = t0 + lane;
+          bool in = false, bond = false;
+          if (t < end) {
+            int j = cell_sites[t];
+            if (j != (int)i) {
+              const PairTestF pf = pair_test_f(qfi, __ldg(&qf[j]), g);
+              int din = decide_f(pf.r2, rl2f, band);
+              int dbo = decide_f(pf.r2, rb2f, band);
+              if (din < 0 || (din > 0 && dbo < 0)) {
+                const PairTest pt = pair_test(qi, q, n, j, g);
+                din = pt.r2 < rl2;
+                dbo = pt.r2 < rb2;
+              }
+              in = din > 0;
+              int sj = sub ? sub[j] : 0;
+              bond = in && mob && sj == si && dbo > 0;
+            }
+          }
+          cnt += __popc(__ballot_sync(0xffffffffu, in));
+          bcnt += __popc(__ballot_sync(0xffffffffu, bond));
+        }
+      }
+  if (lane == 0) {
+    nb_cnt[i] = cnt;
+    bd_cnt[i] = bcnt;
+    atomicMax(max_row, cnt);
+  }
+}
+
+__global__ void k_nbr_fill(const double* __restrict__ q, const float4* __restrict__ qf,
+                           const uint8_t* __restrict__ sub, uint32_t mobile_mask, int64_t n, DevGrid g,
+                           const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                           const int* __restrict__ cell_sites, const int* __restrict__ abs_cell, double rl2,
+                           double rb2, float band, const int* __restrict__ nb_off, uint32_t* __restrict__ nb_ent,
+                           const int* __restrict__ bd_off, int* __restrict__ bd_idx, int max_row) {
+  extern __shared__ unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  uint32_t* buf = reinterpret_cast<uint32_t*>(smem) + (size_t)warp * max_row;
+  uint8_t* isb = reinterpret_cast<uint8_t*>(reinterpret_cast<uint32_t*>(smem) + (size_t)(blockDim.x >> 5) * max_row) +
+                 (size_t)warp * max_row;
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;
+  double qi[3] = {q[i], q[n + i], q[2 * n + i]};
+  const float4 qfi = qf[i];
+  const float rl2f = (float)rl2, rb2f = (float)rb2;
+  int Ai[3] = {abs_cell[i], abs_cell[n + i], abs_cell[2 * n + i]};
+  int si = sub ? sub[i] : 0;
+  bool mob = (mobile_mask >> si) & 1u;
+  Stencil st = make_stencil(cell_of[i], g);
+  int m = 0;
+  for (int ax = 0; ax < st.cnt[0]; ++ax)
+    for (int ay = 0; ay < st.cnt[1]; ++ay)
+      for (int az = 0; az < st.cnt[2]; ++az) {
+        int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+        int beg = cell_start[c], end = cell_start[c + 1];
+        for (int t0 = beg; t0 < end; t0 += 32) {
+          int t = t0 + lane;
+          bool in = false, bond = false;
+          uint32_t ent = 0;
+          if (t < end) {
+            int j = cell_sites[t];
+            if (j != (int)i) {
+              const PairTestF pf = pair_test_f(qfi, __ldg(&qf[j]), g);
+              int din = decide_f(pf.r2, rl2f, band);
+              int dbo = decide_f(pf.r2, rb2f, band);
+              float kk[3] = {pf.k[0], pf.k[1], pf.k[2]};
+              if (din < 0 || (din > 0 && (dbo < 0 || pf.near_half))) {
+                const PairTest pt = pair_test(qi, q, n, j, g);
+                din = pt.r2 < rl2;
+                dbo = pt.r2 < rb2;
+                kk[0] = (float)pt.k[0];
+                kk[1] = (float)pt.k[1];
+                kk[2] = (float)pt.k[2];
+              }
+              in = din > 0;
+              if (in) {
+                int sj = sub ? sub[j] : 0;
+                bond = mob && sj == si && dbo > 0;
+                int code = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  int s = abs_cell[a * n + j] - Ai[a] - g.nc[a] * (int)kk[a];
+                  s = s < -1 ? -1 : (s > 1 ? 1 : s);
+                  code = code * 3 + (s + 1);
+                }
+                ent = (uint32_t)j | ((uint32_t)code << kCodeShift);
+              }
+            }
+          }
+          unsigned msk = __ballot_sync(0xffffffffu, in);
+          if (in) {
+            int pos = m + __popc(msk & ((1u << lane) - 1u));
+            if (pos < max_row) {
+              buf[pos] = ent;
+              isb[pos] = bond ? 1 : 0;
+            }
+          }
+          m += __popc(msk);
+        }
+      }
+  __syncwarp();
+  if (m > max_row) m = max_row;  // cannot happen: max_row is the counted maximum
+  const int off = nb_off[i];
+  const int boff = bd_off[i];
+  for (int e = lane; e < m; e += 32) {
+    uint32_t je = buf[e] & kIdxMask;
+    int rank = 0, brank = 0;
+    for (int f = 0; f < m; ++f) {
+      uint32_t jf = buf[f] & kIdxMask;
+      int less = jf < je;
+      rank += less;
+      brank += less & isb[f];
+    }
+    nb_ent[off + rank] = buf[e];
+    if (isb[e]) bd_idx[boff + brank] = (int)je;
+  }
+}
+
+// ---------------------------------------------------------------- scan
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+__global__ void k_scan_blocks(const int* __restrict__ in, int* __restrict__ out, int64_t n,
+                              long long* __restrict__ block_tot) {
+  __shared__ long long warp_tot[kScanThreads / 32];
+  int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x * kScanPer;
+  long long v[kScanPer];
+  long long run = 0;
+#pragma unroll
+  for (int t = 0; t < kScanPer; ++t) {
+    long long x = (base + t < n) ? in[base + t] : 0;
+    v[t] = run;
+    run += x;
+  }
+  // exclusive scan of per-thread totals across the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  long long wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
+  long long excl = wbase + incl - run;
+#pragma unroll
+  for (int t = 0; t < kScanPer; ++t)
+    if (base + t < n) out[base + t] = (int)(excl + v[t]);
+  if (threadIdx.x == kScanThreads - 1) block_tot[blockIdx.x] = excl + run;
+}
+
+__global__ void k_scan_tops(long long* __restrict__ block_tot, int64_t nblk, long long* __restrict__ total64) {
+  // single thread block: sequential exclusive scan over block totals (nblk is small)
+  if (threadIdx.x != 0) return;
+  long long run = 0;
+  for (int64_t b = 0; b < nblk; ++b) {
+    long long t = block_tot[b];
+    block_tot[b] = run;
+    run += t;
+  }
+  *total64 = run;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int64_t n, const long long* __restrict__ block_tot,
+                           const long long* __restrict__ total64) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int)((long long)out[i] + block_tot[i / kScanBlock]);
+  if (i == n) out[n] = (int)(*total64);
+}
+
+__global__ void k_strip(const uint32_t* __restrict__ ent, int32_t* __restrict__ idx, int64_t m) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m) idx[t] = (int32_t)(ent[t] & kIdxMask);
+}
+
+// out[0] = max sigma, out[1] = max |q| component (maxima of non-negative doubles =
+// maxima of their bit patterns; warp maximum, then one atomic per warp)
+__device__ __forceinline__ void warp_max_bits(unsigned long long* addr, double v) {
+  unsigned long long b = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+    b = y > b ? y : b;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(addr, b);
+}
+
+__global__ void k_site_max(const double* __restrict__ sigma, const double* __restrict__ q, int64_t n,
+                           unsigned long long* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double vs = 0.0, vq = 0.0;
+  if (i < n) {
+    vs = fmax(sigma[i], 0.0);
+    vq = fmax(fabs(q[i]), fmax(fabs(q[n + i]), fabs(q[2 * n + i])));
+    if (!(vq <= 1e300)) vq = 1e300;  // NaN / Inf positions
+  }
+  warp_max_bits(&out[0], vs);
+  warp_max_bits(&out[1], vq);
+}
+
+inline unsigned grid_for(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, int* cell_of, int* cell_slot,
+                               int* cell_count, int* abs_cell, float4* qf, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_cell_assign<<<grid_for(n, 256), 256, 0, s>>>(q, n, g, cell_of, cell_slot, cell_count, abs_cell, qf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slot, const int* cell_start,
+                              int* cell_sites, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_cell_place<<<grid_for(n, 256), 256, 0, s>>>(n, cell_of, cell_slot, cell_start, cell_sites);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nbr_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                             const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                             double rl2, double rb2, float band, int* nb_cnt, int* bd_cnt, int* max_row,
+                             cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_nbr_count<<<grid_for(n * 32, 256), 256, 0, s>>>(q, qf, sub, mobile_mask, n, g, cell_of, cell_start, cell_sites,
+                                                    rl2, rb2, band, nb_cnt, bd_cnt, max_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                            const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                            const int* abs_cell, double rl2, double rb2, float band, const int* nb_off,
+                            uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (max_row < 1) max_row = 1;
+  const size_t per_warp = (size_t)max_row * 5;
+  int warps = (int)((200 * 1024) / per_warp);
+  if (warps > 8) warps = 8;
+  if (warps < 1) return cudaErrorInvalidValue;
+  size_t shm = per_warp * warps + 16;
+  cudaError_t e = cudaFuncSetAttribute(k_nbr_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  int threads = warps * 32;
+  k_nbr_fill<<<grid_for(n * 32, threads), threads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_of, cell_start,
+                                                             cell_sites, abs_cell, rl2, rb2, band, nb_off, nb_ent,
+                                                             bd_off, bd_idx, max_row);
+  return cudaGetLastError();
+}
+
+int64_t scan_tmp_len(int64_t n) { return (n + kScanBlock) / kScanBlock + 2; }
+
+cudaError_t launch_scan(const int* in, int* out, int64_t n, long long* total64, int* tmp, int64_t tmp_len,
+                        cudaStream_t s) {
+  int64_t nblk = (n + kScanBlock - 1) / kScanBlock;
+  if (nblk < 1) nblk = 1;
+  if (nblk + 1 > tmp_len) return cudaErrorInvalidValue;
+  long long* bt = reinterpret_cast<long long*>(tmp);
+  k_scan_blocks<<<(unsigned)nblk, kScanThreads, 0, s>>>(in, out, n, bt);
+  k_scan_tops<<<1, 32, 0, s>>>(bt, nblk, total64);
+  k_scan_add<<<grid_for(n + 1, 256), 256, 0, s>>>(out, n, bt, total64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_strip_codes(const uint32_t* ent, int32_t* idx, int64_t m, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  k_strip<<<grid_for(m, 256), 256, 0, s>>>(ent, idx, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_site_max(const double* sigma, const double* q, int64_t n, unsigned long long* out_bits,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_site_max<<<grid_for(n, 256), 256, 0, s>>>(sigma, q, n, out_bits);
+  return cudaGetLastError();
+}
+
+}  // namespace mxe

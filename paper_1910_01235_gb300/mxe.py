@@ -1,0 +1,279 @@
+"""Thin Python binding of the MXE C ABI (include/mxe.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library `libmxe.so`; PyTorch supplies device memory and the stream.  The
+low-level functions carry the C names and return the C status code (plus the
+C out-parameters); `MxeSystem` wraps one context with device-resident state
+and raises `MxeError` on failure.  There is no CPU fallback: if the library
+cannot be built or loaded, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MAXS = 4
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_BOX_TOO_SMALL, ERR_NBR_OVERFLOW = 0, 1, 2, 3, 4, 5
+ERR_GEOMETRY, ERR_NONFINITE, ERR_X_RANGE, ERR_NO_CONVERGE, ERR_STATE = 6, 7, 8, 9, 10
+FP64, FP32_MIXED, FP32_FF = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "mixed": FP32_MIXED, "ff": FP32_FF}
+
+
+class MxeError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        super().__init__(f"{where}: {mxe_status_string(status)} (status {status})")
+
+
+class mxe_box(C.Structure):
+    _fields_ = [("L", C.c_double * 3)]
+
+
+class mxe_potential(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("cross_geomean", C.c_int32)] + [
+        (nm, (C.c_double * MAXS) * MAXS) for nm in ("phi_A", "phi_p", "phi_r0", "f_xi", "f_q", "f_r0")
+    ] + [("E", C.c_double * MAXS), ("r_switch", C.c_double), ("r_cut", C.c_double)]
+
+
+class mxe_state(C.Structure):
+    _fields_ = [("n", C.c_int64), ("q", C.c_void_p), ("sigma", C.c_void_p), ("x", C.c_void_p),
+                ("T", C.c_void_p), ("sublattice", C.c_void_p), ("mobile_mask", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
+class mxe_fire_params(C.Structure):
+    _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("f_inc", C.c_double),
+                ("f_dec", C.c_double), ("alpha0", C.c_double), ("f_alpha", C.c_double),
+                ("sigma_max", C.c_double), ("n_min", C.c_int32), ("check_every", C.c_int32)]
+
+
+EXPORTS = ["mxe_status_string", "mxe_create", "mxe_destroy", "mxe_build_neighbors", "mxe_export_neighbors",
+           "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async", "mxe_sync_status",
+           "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmxe.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            p, i64, d = C.c_void_p, C.c_int64, C.c_double
+            L.mxe_status_string.restype = C.c_char_p
+            L.mxe_status_string.argtypes = [C.c_int]
+            L.mxe_create.argtypes = [C.POINTER(C.c_void_p), p, p, i64, C.c_int, p]
+            L.mxe_destroy.argtypes = [p]
+            L.mxe_build_neighbors.argtypes = [p, p, d, d, C.POINTER(i64), C.POINTER(d)]
+            L.mxe_export_neighbors.argtypes = [p, p, p]
+            L.mxe_export_bonds.argtypes = [p, p, p, C.POINTER(i64)]
+            L.mxe_free_energy_grad.argtypes = [p, p, p, p, p, p, p]
+            L.mxe_free_energy_grad_async.argtypes = [p, p, p, p, p, p, p]
+            L.mxe_sync_status.argtypes = [p]
+            L.mxe_relax.argtypes = [p, p, d, C.c_int32, p, C.POINTER(C.c_int32), C.POINTER(d)]
+            L.mxe_diffuse_step.argtypes = [p, p, p, d, d, d]
+            L.mxe_diffuse_step_async.argtypes = [p, p, p, d, d, d]
+            for nm in EXPORTS:
+                if nm != "mxe_status_string":
+                    getattr(L, nm).restype = C.c_int
+            _lib = L
+        return _lib
+
+
+# ------------------------------------------------------------------ C names
+def mxe_status_string(status) -> str:
+    return lib().mxe_status_string(int(status)).decode()
+
+
+def mxe_create(box: mxe_box, pot: mxe_potential, n: int, precision: int, stream: int):
+    ctx = C.c_void_p()
+    st = lib().mxe_create(C.byref(ctx), C.byref(box), C.byref(pot), int(n), int(precision), C.c_void_p(stream))
+    return st, ctx
+
+
+def mxe_destroy(ctx):
+    return lib().mxe_destroy(ctx)
+
+
+def mxe_build_neighbors(ctx, state: mxe_state, skin: float, r_bond: float):
+    npairs = C.c_int64(0)
+    rl = C.c_double(0.0)
+    st = lib().mxe_build_neighbors(ctx, C.byref(state), float(skin), float(r_bond), C.byref(npairs), C.byref(rl))
+    return st, npairs.value, rl.value
+
+
+def mxe_export_neighbors(ctx, offsets_ptr: int, idx_ptr: int):
+    return lib().mxe_export_neighbors(ctx, C.c_void_p(offsets_ptr), C.c_void_p(idx_ptr))
+
+
+def mxe_export_bonds(ctx, offsets_ptr: int, idx_ptr: int):
+    nb = C.c_int64(0)
+    st = lib().mxe_export_bonds(ctx, C.c_void_p(offsets_ptr), C.c_void_p(idx_ptr), C.byref(nb))
+    return st, nb.value
+
+
+def mxe_free_energy_grad(ctx, state, F4, gq, gs, mu_ex, mu, asynchronous=False):
+    fn = lib().mxe_free_energy_grad_async if asynchronous else lib().mxe_free_energy_grad
+    return fn(ctx, C.byref(state), *[C.c_void_p(p) for p in (F4, gq, gs, mu_ex, mu)])
+
+
+def mxe_sync_status(ctx):
+    return lib().mxe_sync_status(ctx)
+
+
+def mxe_relax(ctx, state, ftol, max_iter, fire: mxe_fire_params | None = None):
+    it = C.c_int32(0)
+    fm = C.c_double(0.0)
+    st = lib().mxe_relax(ctx, C.byref(state), float(ftol), int(max_iter),
+                         C.byref(fire) if fire is not None else None, C.byref(it), C.byref(fm))
+    return st, it.value, fm.value
+
+
+def mxe_diffuse_step(ctx, state, mu_ex_ptr, dt, nu0, Qm, asynchronous=False):
+    fn = lib().mxe_diffuse_step_async if asynchronous else lib().mxe_diffuse_step
+    return fn(ctx, C.byref(state), C.c_void_p(mu_ex_ptr or 0), float(dt), float(nu0), float(Qm))
+
+
+# ------------------------------------------------------------------ helpers
+def make_potential(pot) -> mxe_potential:
+    P = mxe_potential()
+    S = pot.n_species
+    P.n_species = S
+    P.cross_geomean = 1 if pot.cross_geomean else 0
+    for nm in ("phi_A", "phi_p", "phi_r0", "f_xi", "f_q", "f_r0"):
+        tab, dst = getattr(pot, nm), getattr(P, nm)
+        for k in range(MAXS):
+            for l in range(MAXS):
+                dst[k][l] = float(tab[k, l]) if (k < S and l < S) else (1.0 if nm.endswith("r0") else 0.0)
+    for k in range(S):
+        P.E[k] = float(pot.E[k])
+    P.r_switch, P.r_cut = float(pot.r_switch), float(pot.r_cut)
+    return P
+
+
+def make_fire(dt0=0.02, dt_max=0.1, f_inc=1.1, f_dec=0.5, alpha0=0.1, f_alpha=0.99, n_min=5, check_every=16,
+              sigma_max=0.0):
+    return mxe_fire_params(dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, sigma_max, n_min, check_every)
+
+
+def _ptr(t):
+    return 0 if t is None else int(t.data_ptr())
+
+
+class MxeSystem:
+    """One context plus device-resident state (torch tensors on `device`)."""
+
+    def __init__(self, sys, precision="fp64", device="cuda:0", stream=None, skin=0.2, r_bond=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.sys = sys
+        self.n, self.S = sys.n, sys.S
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        dev = self.device
+        self.q = torch.as_tensor(np.ascontiguousarray(sys.q), dtype=torch.float64, device=dev).contiguous()
+        self.sigma = torch.as_tensor(np.ascontiguousarray(sys.sigma), dtype=torch.float64, device=dev).contiguous()
+        self.x = torch.as_tensor(np.ascontiguousarray(sys.x), dtype=torch.float64, device=dev).contiguous()
+        self.T = torch.as_tensor(np.ascontiguousarray(sys.T), dtype=torch.float64, device=dev).contiguous()
+        self.sub = torch.as_tensor(np.ascontiguousarray(sys.sublattice), dtype=torch.uint8, device=dev).contiguous()
+        self.F4 = torch.zeros(4, dtype=torch.float64, device=dev)
+        self.gq = torch.zeros((3, self.n), dtype=torch.float64, device=dev)
+        self.gs = torch.zeros(self.n, dtype=torch.float64, device=dev)
+        self.mu_ex = torch.zeros((self.S, self.n), dtype=torch.float64, device=dev)
+        self.mu = torch.zeros((self.S, self.n), dtype=torch.float64, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.box = mxe_box((C.c_double * 3)(*[float(v) for v in sys.L]))
+        self.pot = make_potential(sys.pot)
+        with torch.cuda.device(dev):
+            st, self.ctx = mxe_create(self.box, self.pot, self.n, self.precision, self.stream.cuda_stream)
+        if st != OK:
+            raise MxeError(st, "mxe_create")
+        self.skin = skin
+        # bonds: nearest neighbours of the FCC sublattice (a/sqrt2), cut halfway to the second shell (a)
+        self.r_bond = r_bond if r_bond is not None else 0.5 * (sys.a / np.sqrt(2.0) + sys.a)
+        self.state = mxe_state()
+        self._refresh_state()
+
+    def _refresh_state(self):
+        s = self.state
+        s.n = self.n
+        s.q, s.sigma, s.x, s.T = _ptr(self.q), _ptr(self.sigma), _ptr(self.x), _ptr(self.T)
+        s.sublattice = _ptr(self.sub)
+        s.mobile_mask = int(self.sys.mobile_mask)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mxe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, where, allow=()):
+        if st != OK and st not in allow:
+            raise MxeError(st, where)
+        return st
+
+    def build_neighbors(self):
+        st, npairs, rl = mxe_build_neighbors(self.ctx, self.state, self.skin, self.r_bond)
+        self._check(st, "mxe_build_neighbors")
+        self.n_pairs, self.r_list = npairs, rl
+        return npairs, rl
+
+    def export_neighbors(self):
+        t = self.torch
+        off = t.zeros(self.n + 1, dtype=t.int32, device=self.device)
+        idx = t.zeros(max(self.n_pairs, 1), dtype=t.int32, device=self.device)
+        self._check(mxe_export_neighbors(self.ctx, _ptr(off), _ptr(idx)), "mxe_export_neighbors")
+        return off, idx[: self.n_pairs]
+
+    def export_bonds(self):
+        t = self.torch
+        off = t.zeros(self.n + 1, dtype=t.int32, device=self.device)
+        st, nb = mxe_export_bonds(self.ctx, _ptr(off), 0)
+        self._check(st, "mxe_export_bonds")
+        idx = t.zeros(max(nb, 1), dtype=t.int32, device=self.device)
+        st, nb = mxe_export_bonds(self.ctx, _ptr(off), _ptr(idx))
+        self._check(st, "mxe_export_bonds")
+        return off, idx[:nb]
+
+    def free_energy_grad(self, with_mu=True, asynchronous=False):
+        st = mxe_free_energy_grad(self.ctx, self.state, _ptr(self.F4), _ptr(self.gq), _ptr(self.gs),
+                                  _ptr(self.mu_ex), _ptr(self.mu) if with_mu else 0, asynchronous)
+        return self._check(st, "mxe_free_energy_grad")
+
+    def sync_status(self, allow=()):
+        return self._check(mxe_sync_status(self.ctx), "mxe_sync_status", allow)
+
+    def relax(self, ftol, max_iter, fire=None, allow=(ERR_NO_CONVERGE,)):
+        st, it, fm = mxe_relax(self.ctx, self.state, ftol, max_iter, fire)
+        self._check(st, "mxe_relax", allow)
+        return st, it, fm
+
+    def diffuse_step(self, dt, mu_ex=None, nu0=None, Qm=None, asynchronous=False, allow=()):
+        st = mxe_diffuse_step(self.ctx, self.state, _ptr(mu_ex), dt,
+                              self.sys.nu0 if nu0 is None else nu0, self.sys.Qm if Qm is None else Qm,
+                              asynchronous)
+        return self._check(st, "mxe_diffuse_step", allow)
+
+    def staggered_step(self, dt, ftol, max_iter, fire=None):
+        """One step of the staggered scheme (Sec. 4): excess chemical potentials,
+        one Euler step of x, then relaxation of (q, sigma) at fixed x."""
+        self.free_energy_grad(with_mu=False)
+        self.diffuse_step(dt, mu_ex=self.mu_ex)
+        return self.relax(ftol, max_iter, fire)

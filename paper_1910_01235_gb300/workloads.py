@@ -94,6 +94,15 @@ def potential_binary() -> Potential:
     return Potential(S, pA, pp, pr0, fx, fq, fr0, np.array([1.0, 1.1]), 4.5, 5.0, True)
 
 
+def potential_binary_variant_s() -> Potential:
+    """The binary tables with the exponents swapped (p = 5, q = 3) for both
+    species: a stable alloy whose relaxation converges."""
+    P = potential_binary()
+    P.phi_p[:] = np.where(P.phi_p != 0, 5.0, 0.0)
+    P.f_q[:] = np.where(P.f_q != 0, 3.0, 0.0)
+    return P
+
+
 def potential_host_solute() -> Potential:
     """Species 0 = host, 1 = interstitial solute.  Host-host as the single
     species potential; host-solute pair and density with prefactor 0.5 and
