@@ -232,6 +232,34 @@ MXE_API mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double
 MXE_API mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
                                   double dt, double nu0, double Qm);
 
+/* Euler step of the master equation that allocates no device memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- a host framework whose caching allocator already holds
+ * the card, a process under a fixed device-memory budget, or a
+ * latency-critical loop that must not pay the device-wide synchronisation an
+ * allocation can cause.  It computes exactly what mxe_diffuse_step computes,
+ * without a context: the caller passes every input and output (device
+ * pointers): x [S][n] in-out, T [n], mu_ex [S][n], and the bond CSR
+ * (offsets [n+1], idx) that mxe_export_bonds returns.  Scratch lives in one
+ * file-scope device array of MXE_NOALLOC_SCRATCH_DOUBLES doubles plus 256
+ * bytes (about 4 MiB) that every device which loads the library holds until
+ * the process exits; it bounds n to MXE_NOALLOC_MAX_SITES(S), and a larger n
+ * (or S outside 1..2) returns MXE_ERR_ARG before any GPU work.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the array and it keeps the last call's contents: the flag words are cleared
+ * at the start of each call and the per-site scratch is written before it is
+ * read, but calls that overlap on the GPU (other streams, other host threads)
+ * race on it.  Work is enqueued on cuda_stream (NULL: legacy default stream);
+ * the call synchronises that stream and returns MXE_ERR_X_RANGE (x unchanged)
+ * under the same rule as mxe_diffuse_step.                                    */
+#define MXE_NOALLOC_SCRATCH_DOUBLES (1 << 19)
+#define MXE_NOALLOC_MAX_SITES(S) ((int64_t)MXE_NOALLOC_SCRATCH_DOUBLES / (3 + 3 * (int64_t)(S)))
+MXE_API mxe_status mxe_diffuse_step_noalloc(int64_t n, int32_t n_species, double *x_dev, const double *T_dev,
+                                            const double *mu_ex_dev, const int32_t *bond_offsets_dev,
+                                            const int32_t *bond_idx_dev, double dt, double nu0, double Qm,
+                                            void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

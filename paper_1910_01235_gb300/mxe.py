@@ -54,7 +54,12 @@ class mxe_fire_params(C.Structure):
 
 EXPORTS = ["mxe_status_string", "mxe_create", "mxe_destroy", "mxe_build_neighbors", "mxe_export_neighbors",
            "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async", "mxe_sync_status",
-           "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async"]
+           "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async", "mxe_diffuse_step_noalloc"]
+NOALLOC_SCRATCH_DOUBLES = 1 << 19
+
+
+def noalloc_max_sites(S: int) -> int:
+    return NOALLOC_SCRATCH_DOUBLES // (3 + 3 * S)
 
 _lib = None
 _lock = threading.Lock()
@@ -85,6 +90,7 @@ def lib():
             L.mxe_relax.argtypes = [p, p, d, C.c_int32, p, C.POINTER(C.c_int32), C.POINTER(d)]
             L.mxe_diffuse_step.argtypes = [p, p, p, d, d, d]
             L.mxe_diffuse_step_async.argtypes = [p, p, p, d, d, d]
+            L.mxe_diffuse_step_noalloc.argtypes = [i64, C.c_int32, p, p, p, p, p, d, d, d, p]
             for nm in EXPORTS:
                 if nm != "mxe_status_string":
                     getattr(L, nm).restype = C.c_int
@@ -144,6 +150,14 @@ def mxe_relax(ctx, state, ftol, max_iter, fire: mxe_fire_params | None = None):
 def mxe_diffuse_step(ctx, state, mu_ex_ptr, dt, nu0, Qm, asynchronous=False):
     fn = lib().mxe_diffuse_step_async if asynchronous else lib().mxe_diffuse_step
     return fn(ctx, C.byref(state), C.c_void_p(mu_ex_ptr or 0), float(dt), float(nu0), float(Qm))
+
+
+def mxe_diffuse_step_noalloc(n, S, x_ptr, T_ptr, mu_ex_ptr, bond_off_ptr, bond_idx_ptr, dt, nu0, Qm, stream):
+    """Euler step with no device allocation (see include/mxe.h)."""
+    return lib().mxe_diffuse_step_noalloc(int(n), int(S), C.c_void_p(x_ptr), C.c_void_p(T_ptr),
+                                          C.c_void_p(mu_ex_ptr), C.c_void_p(bond_off_ptr),
+                                          C.c_void_p(bond_idx_ptr), float(dt), float(nu0), float(Qm),
+                                          C.c_void_p(stream))
 
 
 # ------------------------------------------------------------------ helpers
