@@ -100,16 +100,30 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- algorithmic work
-def k3_fp32_ops_per_pair(n_phi, n_f):
-    """FP32-pipe operations the gradient pass spends on one (i, j) pair, counted
-    from the algorithm: 12 nodes x (distance 2, switch 11, 5 per radial term,
-    force/sigma accumulation 4.25) + the static point (distance 2, switch 11,
-    5 per density term) + per-pair set-up and combination (separation 9,
-    weights 3 n_phi + 4 n_f, sums 10 + 2 (n_phi + n_f))."""
-    node = 2 + 11 + 5 * (n_phi + n_f) + 4.25
-    static = 2 + 11 + 5 * n_f
-    pair = 9 + 3 * n_phi + 4 * n_f + 10 + 2 * (n_phi + n_f)
-    return 12 * node + static + pair
+# FP32-pipe operations per (i, j) pair of each pass, counted from the algorithm
+# as the kernels evaluate it (an FMA counts as one operation: one issue slot of
+# the FP32 pipe).  n_phi, n_f: distinct pair and density terms; S species.
+def ops_per_pair(kernel, n_phi, n_f, S):
+    if kernel.startswith("density_fp32"):
+        node = 2 + 7 + 2 * n_f                      # distance, switch, terms
+        return 13 * node + 20 + 2 * S * S + 12 * S  # 12 nodes + static point, set-up, sums
+    if kernel.startswith("gradient_fp32") and kernel.endswith("force_noe"):
+        node = 2 + 11 + 3 * (n_phi + n_f) + 3 + 4.25   # distance, switch, factored terms, G, force sums
+        static = 2 + 11 + 4 * n_f + 1
+        pair = 20 + S * S + 4 * S * S + (n_phi + n_f) + 9 + 24
+        return 12 * node + static + pair
+    # float-float passes: add 20, mul 7, exp 110 FP32 operations (see csrc/ff.cuh)
+    term = 7 + 20 + 110 + 7 + 20
+    if kernel.startswith("density_ff"):
+        return 13 * (55 + term * n_f) + 60
+    if kernel.startswith("gradient_ff"):
+        return 12 * (55 + term * (n_phi + n_f)) + (55 + term * n_f) + 80
+    return None
+
+
+def peak_fp32_ops(clock_mhz=2070.0):
+    """FP32 pipe: 152 SMs x 128 lanes x clock (one FMA or add or multiply per lane per cycle)."""
+    return 152 * 128 * clock_mhz * 1e6
 
 
 def measured_peaks():
@@ -171,24 +185,18 @@ def run_ours(args):
         g.sync_status()
         kern = None
         if kernel_events:
-            # average duration of the gradient pass (the dominant kernel), timed alone
-            g.build_neighbors()
-            g.free_energy_grad(with_mu=False)
-            reps = 20
-            A = M.lib()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            ms = []
-            for r in range(reps):
-                with torch.cuda.stream(stream):
-                    flush.fill_(float(r))
-                ev[0].record(stream)
-                M.mxe_free_energy_grad(g.ctx, g.state, M._ptr(g.F4), M._ptr(g.gq), M._ptr(g.gs),
-                                       M._ptr(g.mu_ex), 0, True)
-                ev[1].record(stream)
-                stream.synchronize()
-                ms.append(ev[0].elapsed_time(ev[1]))
-            kern = float(np.median(ms))
-            del A
+            # per-kernel-class device times of one more identical step, with
+            # every launch of the library bracketed by CUDA events on its stream
+            with torch.cuda.stream(stream):
+                g.q.copy_(q0)
+                g.sigma.copy_(s0)
+                g.x.copy_(x0)
+                flush.fill_(-1.0)
+            stream.synchronize()
+            M.mxe_timing_enable(g.ctx, True)
+            one_step()
+            st, kern = M.mxe_timing_read(g.ctx)
+            M.mxe_timing_enable(g.ctx, False)
         npairs = g.n_pairs
         g.close()
         return total_ms, kern, npairs
@@ -203,14 +211,14 @@ def run_ours(args):
         sampler = ClockSampler(local) if p == main_prec else None
         if sampler:
             sampler.start()
-        ms, _, npairs = timed_arm(p, steps, warm)
+        ms, kern, npairs = timed_arm(p, steps, warm, kernel_events=True)
         if sampler:
             clocks = sampler.stop()
         t = torch.tensor([ms / steps], dtype=torch.float64)
         if world > 1:
             t = t.to(dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        results[p] = (float(t.item()), steps, warm, npairs)
+        results[p] = (float(t.item()), steps, warm, npairs, kern)
 
     # e2e through the public API with host buffers
     def e2e(prec, steps):
@@ -259,9 +267,6 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_ms = float(t.item())
 
-    # dominant kernel alone (roofline)
-    _, kern_ms, npairs = timed_arm(main_prec, 1, 1, kernel_events=True)
-
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -270,19 +275,24 @@ def run_ours(args):
         return
 
     evals_per_step = n * (K + 2)
-    ms, steps, warm, npairs = results[main_prec]
+    ms, steps, warm, npairs, kern = results[main_prec]
     value = world * evals_per_step / (ms / 1e3)
-    dfn = M  # noqa: F841
     dp = sys0.pot
     n_phi = 3 if dp.cross_geomean else 2
     n_f = 2
-    ops_launch = npairs * k3_fp32_ops_per_pair(n_phi, n_f)
-    peak_ops = 152 * 128 * 2.07e9
-    # the evaluation timed alone contains density + gradient + energy passes; the
-    # gradient pass share of it comes from the ncu launch list (profiles/)
-    k3_share = float(os.environ.get("MXE_K3_SHARE", "0.62"))
-    k3_ms = kern_ms * k3_share if kern_ms else None
-    achieved = ops_launch / (k3_ms / 1e3) / 1e12 if k3_ms else None
+    # dominant kernel of the step: largest share of the per-class device time
+    shares = {}
+    tot_k = sum(v[1] for v in kern.values()) if kern else 0.0
+    for k_, (cnt, tms) in (kern or {}).items():
+        shares[k_] = {"launches": cnt, "total_ms": tms, "avg_ms": tms / cnt, "share": tms / tot_k if tot_k else None}
+    dom = max(shares, key=lambda k_: shares[k_]["total_ms"]) if shares else None
+    opp = ops_per_pair(dom, n_phi, n_f, sys0.S) if dom else None
+    peak_ops = peak_fp32_ops()
+    if dom and opp:
+        ops_launch = npairs * opp
+        achieved = ops_launch / (shares[dom]["avg_ms"] / 1e3) / 1e12
+    else:
+        ops_launch, achieved = None, None
     line = {
         "metric": METRIC,
         "value": value,
@@ -294,7 +304,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "f32+f64acc", "ff": "f32+ff-acc"}[main_prec],
+        "dtype": {"fp64": "f64", "mixed": "f32 (f64 sums, f64 mu)", "ff": "f32 (float-float sums and mu)"}[main_prec],
         "data": "synthetic (seeded FCC binary alloy, random-init composition)",
         "config": {"workload": WORKLOAD, "sites": n, "species": 2, "fire_iters_per_step": K,
                    "evals_per_step": K + 2, "neighbor_pairs": npairs, "parallelism": f"replicas{world}",
@@ -302,18 +312,19 @@ def run_ours(args):
         "diffusion_steps_per_s": world * 1e3 / ms,
         "precisions": {p: {"ms_per_step": r[0], "site_evals_per_s": world * evals_per_step / (r[0] / 1e3),
                            "steps": r[1]} for p, r in results.items()},
+        "kernels": shares,
         "e2e": {"value": world * evals_per_step / (e2e_ms / 1e3), "unit": "site-evals/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "kernel": "k_gradient", "achieved": achieved, "peak": peak_ops / 1e12,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 pipe)", "frac": (achieved / (peak_ops / 1e12)) if achieved else None,
-                     "traffic": None, "kernel_ms": k3_ms, "ops_per_launch": ops_launch,
+                     "traffic": None, "kernel_avg_ms": shares[dom]["avg_ms"] if dom else None,
+                     "ops_per_launch": ops_launch,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"},
         "clocks": clocks,
         "gpu_launches": None,
     }
-    # kernels per step: build 14, free energy 4 (+1 pack), diffuse 2, relax 1 + 5 (K + 1)
-    pack = 0 if main_prec == "fp64" else 1
-    line["gpu_launches"] = steps * (14 + 4 + pack + 2 + pack + 5 * (K + 1))
+    # kernels per step, counted by the library's launch timing
+    line["gpu_launches"] = steps * sum(v["launches"] for v in shares.values())
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sys0)
     print(json.dumps(line), flush=True)
@@ -376,7 +387,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "ff"])
+    ap.add_argument("--precision", default="ff", choices=["fp64", "mixed", "ff"])
     ap.add_argument("--fire-iters", type=int, default=FIRE_ITERS)
     ap.add_argument("--quick", action="store_true", help="main precision only")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -232,6 +232,20 @@ MXE_API mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double
 MXE_API mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
                                   double dt, double nu0, double Qm);
 
+/* Event timing of the context's kernels, for profiling.  While enabled, every
+ * kernel launch of the context is bracketed by CUDA events on the context's
+ * stream and filed under its kernel class.  mxe_timing_read synchronises the
+ * stream and returns, per class, the number of launches and their total
+ * device time in ms; names receives the class names as consecutive
+ * NUL-terminated strings of MXE_TIMING_NAME_LEN bytes each (caller-owned
+ * host arrays of max_entries entries; *n_entries receives the count).
+ * Reading clears the record.  Enabling allocates a small host-side pool of
+ * CUDA events.                                                               */
+#define MXE_TIMING_NAME_LEN 48
+MXE_API mxe_status mxe_timing_enable(mxe_ctx *ctx, int32_t enable);
+MXE_API mxe_status mxe_timing_read(mxe_ctx *ctx, int32_t max_entries, char *names, int64_t *counts,
+                                   double *total_ms, int32_t *n_entries);
+
 /* Euler step of the master equation that allocates no device memory.  The
  * paper has no counterpart: this entry point exists for callers that cannot
  * call cudaMalloc -- a host framework whose caching allocator already holds

@@ -3,10 +3,14 @@
 // on the context's stream; this file holds host logic only.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "mxe_internal.cuh"
 
@@ -56,6 +60,7 @@ struct mxe_ctx {
   // per-site work arrays
   double *rho_bar = nullptr, *rho_avg = nullptr, *a = nullptr, *b = nullptr, *e = nullptr;
   float4 *pos32 = nullptr, *x32 = nullptr, *ab32 = nullptr;
+  float4 *pos32lo = nullptr, *x32lo = nullptr, *ab32lo = nullptr;  // float-float remainders (FF mode)
   double *gq = nullptr, *gs = nullptr, *mu_ex = nullptr;
   double* site_E = nullptr;
   double* partials = nullptr;
@@ -66,6 +71,15 @@ struct mxe_ctx {
   int* flags = nullptr;
   int* step_flags = nullptr;
   Ctrl* ctrl = nullptr;
+
+  // event timing (profiling): launches bracketed by events, filed by class
+  bool timing = false;
+  struct TimedLaunch {
+    std::string cls;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
 
   // pinned host mirrors
   Ctrl* ctrl_h = nullptr;
@@ -97,6 +111,43 @@ mxe_status map_cuda(cudaError_t e) {
   cudaGetLastError();  // clear a non-sticky error so it does not surface in the caller's next CUDA call
   return e == cudaErrorMemoryAllocation ? MXE_ERR_OOM : MXE_ERR_CUDA;
 }
+
+cudaEvent_t take_event(mxe_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch `fn` (returning cudaError_t); with timing on, bracket it with events.
+template <typename Fn>
+cudaError_t timed(mxe_ctx* c, const std::string& cls, Fn&& fn) {
+  if (!c->timing) return fn();
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  cudaEventRecord(e0, c->stream);
+  cudaError_t e = fn();
+  cudaEventRecord(e1, c->stream);
+  c->timed.push_back({cls, e0, e1});
+  return e;
+}
+
+const char* prec_name(int p) {
+  static const char* names[] = {"fp64", "fp32_mixed", "fp32_ff", "ff"};
+  return (p >= 0 && p < 4) ? names[p] : "?";
+}
+
+std::string cls_name(const char* pass, int prec, int mode = -1) {
+  static const char* modes[] = {"all", "force", "mu", "force_noe"};
+  std::string s = std::string(pass) + "_" + prec_name(prec);
+  if (mode >= 0 && mode < 4) s += std::string("_") + modes[mode];
+  return s;
+}
+
+#define TIMED(cls, call) timed(c, (cls), [&]() { return (call); })
 
 // cudaMemcpyAsync / cudaMemsetAsync that accept an empty range with null pointers
 cudaError_t copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
@@ -141,6 +192,8 @@ int add_fn(RadialFn* tab, int& count, int cap, double A, double kappa, double la
   F.c1 = (float)(lambda * log2e);
   F.lam_f = (float)lambda;
   F.on = 1;
+  F.lnA_kappa_ff = ff(std::log(A) + kappa);
+  F.lambda_ff = ff(lambda);
   return count++;
 }
 
@@ -192,6 +245,9 @@ mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
   d.rc_f = (float)p.r_cut;
   d.inv_w_f = (float)d.inv_w;
   d.dS_scale_f = (float)(-30.0 * d.inv_w);
+  d.rs_ff = ff(d.rs);
+  d.inv_w_ff = ff(d.inv_w);
+  d.dS_scale_ff = ff(-30.0 * d.inv_w);
   return MXE_OK;
 }
 
@@ -207,6 +263,8 @@ void fill_pass(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
   A.T = s->T;
   A.pos32 = c->pos32;
   A.x32 = c->x32;
+  A.pos32lo = c->pos32lo;
+  A.x32lo = c->x32lo;
   A.nb_off = c->nb_off;
   A.nb_ent = c->nb_ent;
   A.n = c->n;
@@ -216,6 +274,7 @@ void fill_pass(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
   A.b = c->b;
   A.e = c->e;
   A.ab32 = c->ab32;
+  A.ab32lo = c->ab32lo;
   A.gq = c->gq;
   A.gs = c->gs;
   A.mu_ex = c->mu_ex;
@@ -249,7 +308,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   c->have_list = false;
   // max sigma -> r_list; max |q| -> error band of the FP32 prefilter
   CK(cudaMemsetAsync(c->smax_bits, 0, 2 * sizeof(unsigned long long), st));
-  CK(launch_site_max(s->sigma, s->q, n, c->smax_bits, st));
+  CK(TIMED("build_misc", launch_site_max(s->sigma, s->q, n, c->smax_bits, st)));
   CK(cudaMemcpyAsync(c->bits_h, c->smax_bits, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   double smax, qmax;
@@ -281,6 +340,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     g.invL[a] = 1.0 / c->box.L[a];
     g.h[a] = c->box.L[a] / g.nc[a];
     g.h_f[a] = (float)g.h[a];
+    g.h_lo[a] = (float)(g.h[a] - (double)g.h_f[a]);
     g.L_f[a] = (float)g.L[a];
     g.invL_f[a] = (float)g.invL[a];
     Lmax = std::max(Lmax, g.L[a]);
@@ -299,16 +359,16 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   if (ms != MXE_OK) return ms;
   // cell lists
   CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int) * ncell, st));
-  CK(launch_cell_assign(s->q, n, g, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st));
-  CK(launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st));
-  CK(launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st));
+  CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
+  CK(TIMED("build_misc", launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st)));
+  CK(TIMED("build_misc", launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st)));
   // counts
   const double rl2 = r_list * r_list, rb2 = r_bond * r_bond;
   CK(cudaMemsetAsync(c->max_row, 0, sizeof(int), st));
-  CK(launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
-                      rl2, rb2, band, c->nb_cnt, c->bd_cnt, c->max_row, st));
-  CK(launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st));
-  CK(launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st));
+  CK(TIMED("build_count", launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
+                      rl2, rb2, band, c->nb_cnt, c->bd_cnt, c->max_row, st)));
+  CK(TIMED("build_misc", launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st)));
+  CK(TIMED("build_misc", launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st)));
   CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(c->ints_h, c->max_row, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -328,8 +388,8 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   }
   const int max_row = c->ints_h[0];
   if ((int64_t)max_row * 5 > 200 * 1024) return MXE_ERR_NBR_OVERFLOW;
-  CK(launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
-                     c->abs_cell, rl2, rb2, band, c->nb_off, c->nb_ent, c->bd_off, c->bd_idx, max_row, st));
+  CK(TIMED("build_fill", launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
+                     c->abs_cell, rl2, rb2, band, c->nb_off, c->nb_ent, c->bd_off, c->bd_idx, max_row, st)));
   CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
   c->n_pairs = npairs;
   c->n_bonds = nbonds;
@@ -343,31 +403,35 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
 }
 
 // Free energy and gradients.  want_mu: the chemical potentials are requested.
-// The FP32 paths evaluate mu (and then the energies) with the FP64 density and
-// chemical-potential passes: the flux step takes differences of neighbouring
-// mu, so their absolute error must stay far below kB T * 1e-7; the forces and
-// the relaxation use the FP32 passes.
+// The FP32 modes evaluate mu (and then the energies) with more accurate
+// density and chemical-potential passes -- FP64 in MXE_FP32_MIXED, float-float
+// in MXE_FP32_FF: the flux step takes differences of neighbouring mu, so their
+// absolute error must stay far below kB T * 1e-7.  Forces and the relaxation
+// use the FP32 passes.
 mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want_mu) {
   cudaStream_t st = c->stream;
   const bool fp32 = c->precision != MXE_FP64;
   if (!fp32) {
-    CK(launch_density(0, c->nl, c->dp, c->grid, A, st));
-    CK(launch_gradient(0, want_mu ? kGradAll : kGradForce, c->nl, c->dp, c->grid, A, st));
+    CK(TIMED(cls_name("density", 0), launch_density(0, c->nl, c->dp, c->grid, A, st)));
+    CK(TIMED(cls_name("gradient", 0, want_mu ? kGradAll : kGradForce), launch_gradient(0, want_mu ? kGradAll : kGradForce, c->nl, c->dp, c->grid, A, st)));
     return MXE_OK;
   }
-  CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->pos32, c->x32, st));
+  const bool ffm = c->precision == MXE_FP32_FF;
+  CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->pos32, c->x32,
+                 ffm && want_mu ? c->pos32lo : nullptr, ffm && want_mu ? c->x32lo : nullptr, st)));
   if (!want_mu) {
-    CK(launch_density(c->precision, c->nl, c->dp, c->grid, A, st));
-    CK(launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st));
+    CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
+    CK(TIMED(cls_name("gradient", c->precision, kGradForce), launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st)));
     return MXE_OK;
   }
-  CK(launch_density(0, c->nl, c->dp, c->grid, A, st));
-  CK(launch_gradient(0, kGradMu, c->nl, c->dp, c->grid, A, st));
-  CK(launch_pack_ab(c->a, c->b, c->n, c->S, c->ab32, st));
+  const int acc = ffm ? 3 : 0;  // precision of the chemical-potential passes
+  CK(TIMED(cls_name("density", acc), launch_density(acc, c->nl, c->dp, c->grid, A, st)));
+  CK(TIMED(cls_name("gradient", acc, kGradMu), launch_gradient(acc, kGradMu, c->nl, c->dp, c->grid, A, st)));
+  if (!ffm) CK(TIMED("pack_ab", launch_pack_ab(c->a, c->b, c->n, c->S, c->ab32, st)));  // the float-float pass packs them itself
   if (A.gq != nullptr || A.gs != nullptr) {
     PassArgs F = A;
-    F.site_E = nullptr;  // energies already come from the FP64 pass
-    CK(launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, F, st));
+    F.site_E = nullptr;  // energies already come from the accurate pass
+    CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, F, st)));
   }
   return MXE_OK;
 }
@@ -420,7 +484,7 @@ mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* po
   c->pot = *pot;
   if (const char* env = std::getenv("MXE_LANES_PER_SITE")) {
     int v = std::atoi(env);
-    if (v == 1 || v == 4 || v == 8 || v == 16) c->nl = v;
+    if (v == 4 || v == 8 || v == 16) c->nl = v;
   }
   const int64_t S = c->S;
   cudaError_t e = cudaSuccess;
@@ -450,6 +514,12 @@ mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* po
     A(dalloc(&c->x32, n));
     A(dalloc(&c->ab32, 2 * n));
   }
+  if (precision == MXE_FP32_FF) {
+    A(dalloc(&c->pos32lo, n));
+    A(dalloc(&c->x32lo, n));
+    A(dalloc(&c->ab32lo, 2 * n));
+  }
+  A(init_ff_exp_table());
   A(dalloc(&c->gq, 3 * n));
   A(dalloc(&c->gs, n));
   A(dalloc(&c->mu_ex, S * n));
@@ -484,6 +554,11 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   if (!c) return MXE_OK;
   Guard gd(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& t : c->timed) {
+    cudaEventDestroy(t.e0);
+    cudaEventDestroy(t.e1);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
   dfree(c->cell_of);
   dfree(c->cell_slot);
   dfree(c->abs_cell);
@@ -510,6 +585,9 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->pos32);
   dfree(c->x32);
   dfree(c->ab32);
+  dfree(c->pos32lo);
+  dfree(c->x32lo);
+  dfree(c->ab32lo);
   dfree(c->gq);
   dfree(c->gs);
   dfree(c->mu_ex);
@@ -565,6 +643,41 @@ mxe_status mxe_export_bonds(mxe_ctx* c, int32_t* offsets_dev, int32_t* idx_dev, 
   return MXE_OK;
 }
 
+mxe_status mxe_timing_enable(mxe_ctx* c, int32_t enable) {
+  if (!c) return MXE_ERR_ARG;
+  c->timing = enable != 0;
+  return MXE_OK;
+}
+
+mxe_status mxe_timing_read(mxe_ctx* c, int32_t max_entries, char* names, int64_t* counts, double* total_ms,
+                           int32_t* n_entries) {
+  if (!c || max_entries < 0 || (max_entries > 0 && (!names || !counts || !total_ms))) return MXE_ERR_ARG;
+  Guard gd(c->device);
+  CK(cudaStreamSynchronize(c->stream));
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  for (auto& t : c->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.e0, t.e1) != cudaSuccess) cudaGetLastError();
+    auto& a = agg[t.cls];
+    a.first += 1;
+    a.second += ms;
+    c->event_pool.push_back(t.e0);
+    c->event_pool.push_back(t.e1);
+  }
+  c->timed.clear();
+  int32_t k = 0;
+  for (auto& kv : agg) {
+    if (k >= max_entries) break;
+    std::memset(names + (size_t)k * MXE_TIMING_NAME_LEN, 0, MXE_TIMING_NAME_LEN);
+    std::strncpy(names + (size_t)k * MXE_TIMING_NAME_LEN, kv.first.c_str(), MXE_TIMING_NAME_LEN - 1);
+    counts[k] = kv.second.first;
+    total_ms[k] = kv.second.second;
+    ++k;
+  }
+  if (n_entries) *n_entries = k;
+  return MXE_OK;
+}
+
 mxe_status mxe_sync_status(mxe_ctx* c) {
   if (!c) return MXE_ERR_ARG;
   Guard gd(c->device);
@@ -595,7 +708,7 @@ mxe_status mxe_free_energy_grad_async(mxe_ctx* c, const mxe_state* s, double* F4
   if (!want_mu) A.mu_ex = nullptr;
   mxe_status ms = enqueue_passes(c, s, A, want_mu);
   if (ms != MXE_OK) return ms;
-  CK(launch_energy_reduce(c->site_E, c->n, c->partials, F4_dev, c->stream));
+  CK(TIMED("energy_reduce", launch_energy_reduce(c->site_E, c->n, c->partials, F4_dev, c->stream)));
   return MXE_OK;
 }
 
@@ -643,7 +756,7 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
   H.sigma_hi = fp.sigma_max > 0.0 ? fp.sigma_max : INFINITY;
   CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   if (c->precision != MXE_FP64)
-    CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, st));
+    CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, nullptr, nullptr, st)));
   PassArgs A;
   fill_pass(c, s, A);
   A.ctrl = c->ctrl;
@@ -652,13 +765,17 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
   mxe_status result = MXE_OK;
   int last_iter = -1, rebuilds = 0;
   for (;;) {
-    for (int it = 0; it < chunk; ++it) {
-      CK(launch_density(c->precision, c->nl, c->dp, c->grid, A, st));
-      CK(launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st));
-      CK(launch_fire_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->partials, c->ctrl, c->flags, st));
-      CK(launch_fire_logic(c->partials, n, c->ctrl, c->flags, st));
-      CK(launch_fire_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n, c->grid,
-                            c->precision != MXE_FP64 ? c->pos32 : nullptr, c->ctrl, st));
+    // enqueue no more iterations than can still run: max_iter updates plus the
+    // final evaluation
+    const int left = max_iter + 1 - H.iter;
+    const int todo = std::max(1, std::min(chunk, left));
+    for (int it = 0; it < todo; ++it) {
+      CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
+      CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
+      CK(TIMED("fire_reduce", launch_fire_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->partials, c->ctrl, c->flags, st)));
+      CK(TIMED("fire_logic", launch_fire_logic(c->partials, n, c->ctrl, c->flags, st)));
+      CK(TIMED("fire_update", launch_fire_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n, c->grid,
+                            c->precision != MXE_FP64 ? c->pos32 : nullptr, c->ctrl, st)));
     }
     CK(cudaMemcpyAsync(&H, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -701,7 +818,7 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
     H.sigma_max_build = c->sigma_max_build;
     CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
     if (c->precision != MXE_FP64)
-      CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, st));
+      CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, nullptr, nullptr, st)));
     // the rebuild may have reallocated the lists: take the current pointers
     fill_pass(c, s, A);
     A.ctrl = c->ctrl;
@@ -739,9 +856,9 @@ mxe_status mxe_diffuse_step_async(mxe_ctx* c, mxe_state* s, const double* mu_ex_
     mu = c->mu_ex;
   }
   CK(cudaMemsetAsync(c->step_flags, 0, sizeof(int), st));
-  CK(launch_flux(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, c->flux_tmp, c->x_new,
-                 c->step_flags, st));
-  CK(launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, st));
+  CK(TIMED("flux", launch_flux(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, c->flux_tmp, c->x_new,
+                 c->step_flags, st)));
+  CK(TIMED("commit", launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, st)));
   return MXE_OK;
 }
 

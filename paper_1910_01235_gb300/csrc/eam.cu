@@ -24,9 +24,25 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
+#include "ff.cuh"
 #include "mxe_internal.cuh"
 
 namespace mxe {
+
+__constant__ FFExpTable c_exp_table;  // 2^(j/32) as float pairs
+
+cudaError_t init_ff_exp_table() {
+  FFExpTable T;
+  for (int j = 0; j < 32; ++j) {
+    const double v = std::exp2((double)j / 32.0);
+    T.hi[j] = (float)v;
+    T.lo[j] = (float)(v - (double)T.hi[j]);
+  }
+  return cudaMemcpyToSymbol(c_exp_table, &T, sizeof(T));
+}
+
 namespace {
 
 // ---------------------------------------------------------------- accumulators
@@ -35,6 +51,7 @@ struct AccD {
   __device__ __forceinline__ void zero() { v = 0.0; }
   __device__ __forceinline__ void add(double x) { v += x; }
   __device__ __forceinline__ void add(float x) { v += (double)x; }
+  __device__ __forceinline__ void add(ff x) { v += ff_to_double(x); }
   __device__ __forceinline__ double get() const { return v; }
   __device__ __forceinline__ void team_reduce(int nl) {
     for (int o = nl >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -81,6 +98,13 @@ struct Traits<2> {
   using R = float;
   using Acc = AccFF;
 };
+// 3: float-float node arithmetic (about 48 bits), for the chemical-potential
+// passes of the FP32 modes; pair sums are added into FP64 per-site sums.
+template <>
+struct Traits<3> {
+  using R = ff;
+  using Acc = AccD;
+};
 
 // ---------------------------------------------------------------- math
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -104,6 +128,11 @@ __device__ __forceinline__ void r_from_r2(double r2, double& r, double& rinv) {
   rinv = 1.0 / r;
 }
 
+__device__ __forceinline__ void r_from_r2(ff r2, ff& r, ff& rinv) {
+  r = ff_sqrt(r2);
+  rinv = ff_recip(r);
+}
+
 // quintic switch S(r) and dS/dr
 __device__ __forceinline__ void sw(const DevPot& P, float r, float& S, float& dS) {
   float t = fminf(fmaxf((r - P.rs_f) * P.inv_w_f, 0.f), 1.f);
@@ -120,9 +149,31 @@ __device__ __forceinline__ void sw(const DevPot& P, double r, double& S, double&
   dS = (t2 * (u * u)) * (-30.0 * P.inv_w);
 }
 
+__device__ __forceinline__ void sw(const DevPot& P, ff r, ff& S, ff& dS) {
+  if (r.hi <= P.rs_f && !(r.hi == P.rs_f && r.lo > 0.f)) {  // r <= r_switch: S = 1
+    S = ff(1.0f, 0.f);
+    dS = ff(0.f, 0.f);
+    return;
+  }
+  ff t = (r - P.rs_ff) * P.inv_w_ff;
+  if (!(t < ff(1.0f, 0.f))) {
+    S = ff(0.f, 0.f);
+    dS = ff(0.f, 0.f);
+    return;
+  }
+  const ff t2 = t * t;
+  const ff u = ff_add_f(-t, 1.0f);
+  S = ff_add_f(t2 * t * ff_add_f(t * ff_add_f(ff_mul_f(t, -6.0f), 15.0f), -10.0f), 1.0f);
+  dS = t2 * (u * u) * P.dS_scale_ff;
+}
+
 // raw exponential part of a radial term
 __device__ __forceinline__ float rad_raw(const RadialFn& F, float r) { return ex2_approx(fmaf(-F.c1, r, F.c0)); }
 __device__ __forceinline__ double rad_raw(const RadialFn& F, double r) { return F.A * exp(F.kappa - F.lambda * r); }
+__device__ __forceinline__ ff rad_raw(const RadialFn& F, ff r) {
+  return ff_exp(F.lnA_kappa_ff - F.lambda_ff * r, c_exp_table);
+}
+__device__ __forceinline__ ff rad_lam(const RadialFn& F, ff) { return F.lambda_ff; }
 __device__ __forceinline__ float rad_lam(const RadialFn& F, float) { return F.lam_f; }
 __device__ __forceinline__ double rad_lam(const RadialFn& F, double) { return F.lambda; }
 
@@ -132,6 +183,8 @@ template <>
 __device__ __forceinline__ float sqrt6<float>() { return 2.44948974f; }
 template <>
 __device__ __forceinline__ double sqrt6<double>() { return kSqrt6; }
+template <>
+__device__ __forceinline__ ff sqrt6<ff>() { return ff(kSqrt6); }
 
 // ---------------------------------------------------------------- site data
 template <int PREC, int S>
@@ -151,6 +204,18 @@ __device__ __forceinline__ void load_site(const PassArgs& A, int64_t j, SiteData
   d.sig = A.sigma[j];
 #pragma unroll
   for (int k = 0; k < S; ++k) d.x[k] = A.x[k * n + j];
+}
+template <int S>
+__device__ __forceinline__ void load_site(const PassArgs& A, int64_t j, SiteData<3, S>& d) {
+  const float4 P = __ldg(&A.pos32[j]), Pl = __ldg(&A.pos32lo[j]);
+  d.p[0] = ff(P.x, Pl.x);
+  d.p[1] = ff(P.y, Pl.y);
+  d.p[2] = ff(P.z, Pl.z);
+  d.sig = ff(P.w, Pl.w);
+  const float4 X = __ldg(&A.x32[j]), Xl = __ldg(&A.x32lo[j]);
+  const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
+#pragma unroll
+  for (int k = 0; k < S; ++k) d.x[k] = ff(xs[k], xl[k]);
 }
 template <int PREC, int S>
 __device__ __forceinline__ void load_site(const PassArgs& A, int64_t j, SiteData<PREC, S>& d) {
@@ -184,6 +249,15 @@ __device__ __forceinline__ void separation(const DevGrid& g, const SiteData<PREC
   for (int a = 0; a < 3; ++a) d[a] = (sj.p[a] - si.p[a]) + (float)s[a] * g.h_f[a];
 }
 
+template <int S>
+__device__ __forceinline__ void separation(const DevGrid& g, const SiteData<3, S>& si, const SiteData<3, S>& sj,
+                                           uint32_t code, ff d[3]) {
+  const int c = (int)(code);
+  const float s[3] = {(float)(c / 9 - 1), (float)((c / 3) % 3 - 1), (float)(c % 3 - 1)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = (sj.p[a] - si.p[a]) + ff(s[a] * g.h_f[a], s[a] * g.h_lo[a]);
+}
+
 // neighbours' embedding coefficients for pass 2
 template <int S>
 __device__ __forceinline__ void load_ab(const PassArgs& A, int64_t j, double a[S], double b[S],
@@ -192,6 +266,16 @@ __device__ __forceinline__ void load_ab(const PassArgs& A, int64_t j, double a[S
   for (int k = 0; k < S; ++k) {
     a[k] = A.a[k * A.n + j];
     b[k] = A.b[k * A.n + j];
+  }
+}
+template <int S>
+__device__ __forceinline__ void load_ab(const PassArgs& A, int64_t j, ff a[S], ff b[S], SiteData<3, S>*) {
+  const float4 v0 = __ldg(&A.ab32[2 * j]), l0 = __ldg(&A.ab32lo[2 * j]);
+  a[0] = ff(v0.x, l0.x);
+  b[0] = ff(v0.y, l0.y);
+  if (S > 1) {
+    a[1 < S ? 1 : 0] = ff(v0.z, l0.z);
+    b[1 < S ? 1 : 0] = ff(v0.w, l0.w);
   }
 }
 template <int PREC, int S>
@@ -304,7 +388,7 @@ __global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A
       // rho_i^k += sum_l x_jl f_kl
 #pragma unroll
       for (int k = 0; k < S; ++k) {
-        R sb = 0, sa = 0;
+        R sb = (R)0, sa = (R)0;
 #pragma unroll
         for (int l = 0; l < S; ++l)
 #pragma unroll
@@ -340,13 +424,26 @@ __global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A
     const double xk = A.x[k * n + i];
     double e = 0.0, ak = 0.0, bk = 0.0;
     if (rbar > kRhoMin) {
-      const double sq = sqrt(rbar);
-      const double F = -P.E[k] * sq;
-      const double dF = -P.E[k] / (2.0 * sq);
-      const double d2F = P.E[k] / (4.0 * rbar * sq);
-      e = F + dF * (ravg - rbar);
-      ak = xk * d2F * (ravg - rbar);
-      bk = xk * dF;
+      if (PREC == 0 || PREC == 3) {
+        const double sq = sqrt(rbar);
+        const double F = -P.E[k] * sq;
+        const double dF = -P.E[k] / (2.0 * sq);
+        const double d2F = P.E[k] / (4.0 * rbar * sq);
+        e = F + dF * (ravg - rbar);
+        ak = xk * d2F * (ravg - rbar);
+        bk = xk * dF;
+      } else {
+        // embedding arithmetic in FP32 (the difference <rho> - rho_bar is taken
+        // in FP64 first: it is small against rho)
+        const float rf = (float)rbar, df = (float)(ravg - rbar), Ef = (float)P.E[k], xf = (float)xk;
+        const float isq = rsqrt_approx(rf);
+        const float sq = rf * isq;
+        const float dF = -0.5f * Ef * isq;
+        const float d2F = 0.25f * Ef * isq * isq * isq;
+        e = (double)(-Ef * sq) + (double)(dF * df);
+        ak = (double)(xf * d2F * df);
+        bk = (double)(xf * dF);
+      }
     } else {
       flag |= kFlagGeometry;
     }
@@ -362,16 +459,31 @@ __global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A
     A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
     if (S > 2) A.ab32[2 * i + 1] = make_float4(ab[4], ab[5], ab[6], ab[7]);
   }
+  if (PREC == 3) {
+    float lo[4];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double av = k < S ? A.a[k * n + i] : 0.0, bv = k < S ? A.b[k * n + i] : 0.0;
+      lo[2 * k] = (float)(av - (double)(float)av);
+      lo[2 * k + 1] = (float)(bv - (double)(float)bv);
+    }
+    A.ab32lo[2 * i] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+  }
   if (flag) atomicOr(A.flags, flag);
 }
 
 // ---------------------------------------------------------------- K3: gradient pass
 // MODE kGradAll: dF/dq, dF/dsigma, mu, energies; kGradForce: dF/dq, dF/dsigma,
-// energies (no mu); kGradMu: mu and energies only (no derivatives).
+// energies (no mu); kGradForceNoE: dF/dq, dF/dsigma only (relaxation loop);
+// kGradMu: mu and energies only (no derivatives).
+// Without mu, the derivative of the pair's weighted radial terms at a node is
+// formed as G = dS sum_u c_u E_u - S sum_u (c_u lambda_u) E_u (E_u the raw
+// exponentials), three FP32 operations per term.
 template <int PREC, int S, int NL, int MODE>
 __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs A) {
   constexpr bool DER = MODE != kGradMu;
-  constexpr bool MU = MODE != kGradForce;
+  constexpr bool MU = MODE == kGradAll || MODE == kGradMu;
+  constexpr bool EN = MODE != kGradForceNoE;
   using R = typename Traits<PREC>::R;
   using Acc = typename Traits<PREC>::Acc;
   constexpr int NF = S * S;
@@ -409,11 +521,11 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
       // pair weights of the distinct radial terms
       R cphi[NP], cfa[NF], cfs[NF];
 #pragma unroll
-      for (int u = 0; u < NP; ++u) cphi[u] = 0;
+      for (int u = 0; u < NP; ++u) cphi[u] = (R)0;
 #pragma unroll
       for (int v = 0; v < NF; ++v) {
-        cfa[v] = 0;
-        cfs[v] = 0;
+        cfa[v] = (R)0;
+        cfs[v] = (R)0;
       }
 #pragma unroll
       for (int k = 0; k < S; ++k)
@@ -429,16 +541,22 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
               cfs[v] += ai[k] * sj.x[l] + aj[k] * si.x[l];
             }
         }
+      R clphi[NP], clf[NF];  // weights times decay rates (factored derivative)
+#pragma unroll
+      for (int u = 0; u < NP; ++u) clphi[u] = cphi[u] * rad_lam(P.phi[u], s_i);
+#pragma unroll
+      for (int v = 0; v < NF; ++v) clf[v] = cfa[v] * rad_lam(P.f[v], s_i);
+      R epn = (R)0;  // sum over nodes of S sum_u c_u E_u (pair energy, factored path)
       // static point: density terms only
       R fst[NF], Gs;
       {
         R r, rinv, Sw, dS;
         r_from_r2(D2, r, rinv);
         sw(P, r, Sw, dS);
-        Gs = 0;
+        Gs = (R)0;
 #pragma unroll
         for (int v = 0; v < NF; ++v) {
-          fst[v] = 0;
+          fst[v] = (R)0;
           if (v < P.n_f) {
             const R e = rad_raw(P.f[v], r);
             fst[v] = e * Sw;
@@ -450,10 +568,10 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
       // 12 nodes
       R aphi[NP], af[NF];
 #pragma unroll
-      for (int u = 0; u < NP; ++u) aphi[u] = 0;
+      for (int u = 0; u < NP; ++u) aphi[u] = (R)0;
 #pragma unroll
-      for (int v = 0; v < NF; ++v) af[v] = 0;
-      R T = 0, U[3] = {0, 0, 0}, Vs = 0;
+      for (int v = 0; v < NF; ++v) af[v] = (R)0;
+      R T = (R)0, U[3] = {(R)0, (R)0, (R)0}, Vs = (R)0;
 #pragma unroll
       for (int site = 0; site < 2; ++site) {
         const R s = site == 0 ? s_i : s_j;
@@ -468,21 +586,41 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
             R r, rinv, Sw, dS;
             r_from_r2(r2, r, rinv);
             sw(P, r, Sw, dS);
-            R G = 0;
+            R G = (R)0;
+            if constexpr (!MU) {
+              R A1p = (R)0, A1f = (R)0, A2 = (R)0;
 #pragma unroll
-            for (int u = 0; u < NP; ++u)
-              if (u < P.n_phi) {
-                const R e = rad_raw(P.phi[u], r);
-                aphi[u] += e * Sw;
-                if (DER) G += cphi[u] * (e * (dS - rad_lam(P.phi[u], r) * Sw));
-              }
+              for (int u = 0; u < NP; ++u)
+                if (u < P.n_phi) {
+                  const R e = rad_raw(P.phi[u], r);
+                  A1p += cphi[u] * e;
+                  A2 += clphi[u] * e;
+                }
 #pragma unroll
-            for (int v = 0; v < NF; ++v)
-              if (v < P.n_f) {
-                const R e = rad_raw(P.f[v], r);
-                if (MU) af[v] += e * Sw;
-                if (DER) G += cfa[v] * (e * (dS - rad_lam(P.f[v], r) * Sw));
-              }
+              for (int v = 0; v < NF; ++v)
+                if (v < P.n_f) {
+                  const R e = rad_raw(P.f[v], r);
+                  A1f += cfa[v] * e;
+                  A2 += clf[v] * e;
+                }
+              G = (A1p + A1f) * dS - A2 * Sw;
+              if (EN) epn += A1p * Sw;
+            } else {
+#pragma unroll
+              for (int u = 0; u < NP; ++u)
+                if (u < P.n_phi) {
+                  const R e = rad_raw(P.phi[u], r);
+                  aphi[u] += e * Sw;
+                  if (DER) G += cphi[u] * (e * (dS - rad_lam(P.phi[u], r) * Sw));
+                }
+#pragma unroll
+              for (int v = 0; v < NF; ++v)
+                if (v < P.n_f) {
+                  const R e = rad_raw(P.f[v], r);
+                  af[v] += e * Sw;
+                  if (DER) G += cfa[v] * (e * (dS - rad_lam(P.f[v], r) * Sw));
+                }
+            }
             w2[pm] = G * rinv;
           }
           T += w2[0] + w2[1];
@@ -497,14 +635,18 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
         for (int c = 0; c < 3; ++c) gacc[c].add(-(d[c] * Tt + U[c] * inv12));
         gsig.add(Vs * inv12);
       }
-      R ep = 0;
+      if constexpr (!MU) {
+        if (EN) epair.add((R)0.5 * inv12 * epn);
+      } else {
+        R ep = (R)0;
 #pragma unroll
-      for (int u = 0; u < NP; ++u) ep += cphi[u] * aphi[u];
-      epair.add((R)0.5 * inv12 * ep);
+        for (int u = 0; u < NP; ++u) ep += cphi[u] * aphi[u];
+        epair.add((R)0.5 * inv12 * ep);
+      }
 #pragma unroll
       for (int k = 0; k < S; ++k) {
         if (!MU) break;
-        R m = 0;
+        R m = (R)0;
 #pragma unroll
         for (int l = 0; l < S; ++l) {
 #pragma unroll
@@ -540,17 +682,11 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
     A.gq[2 * n + i] = g2;
   }
   if (DER && A.gs) A.gs[i] = gs;
-  double xv = 1.0, mix = 0.0, emb = 0.0;
-#pragma unroll
-  for (int k = 0; k < S; ++k) {
-    const double xk = A.x[k * n + i];
-    xv -= xk;
-    if (xk > 0.0) mix += xk * log(xk);
-    emb += xk * A.e[k * n + i];
-  }
-  if (xv > 0.0) mix += xv * log(xv);
   bool finite = !DER || (isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs));
   if (MU) {
+    double xv = 1.0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) xv -= A.x[k * n + i];
     const double lv = log(fmax(xv, kLogFloor));
 #pragma unroll
     for (int k = 0; k < S; ++k) {
@@ -560,31 +696,56 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
       if (A.mu) A.mu[k * n + i] = m + kT * (log(fmax(A.x[k * n + i], kLogFloor)) - lv);
     }
   }
-  const double EV = epair.get() + emb;
-  const double Fv = -3.0 * kT * log(sg);
-  const double Fm = kT * mix;
-  if (A.site_E) {
+  if (A.site_E) {  // the relaxation loop asks for no energies: skip their FP64 logarithms
+    double xv = 1.0, mix = 0.0, emb = 0.0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const double xk = A.x[k * n + i];
+      xv -= xk;
+      if (xk > 0.0) mix += xk * log(xk);
+      emb += xk * A.e[k * n + i];
+    }
+    if (xv > 0.0) mix += xv * log(xv);
+    const double EV = epair.get() + emb;
+    const double Fv = -3.0 * kT * log(sg);
+    const double Fm = kT * mix;
     A.site_E[i] = EV;
     A.site_E[n + i] = Fv;
     A.site_E[2 * n + i] = Fm;
+    finite = finite && isfinite(EV) && isfinite(Fv) && isfinite(Fm);
   }
-  if (!(finite && isfinite(EV) && isfinite(Fv) && isfinite(Fm))) flag |= kFlagNonfinite;
+  if (!finite) flag |= kFlagNonfinite;
   if (flag) atomicOr(A.flags, flag);
 }
 
 // ---------------------------------------------------------------- K7: pack
 __global__ void k_pack(const double* __restrict__ q, const double* __restrict__ sigma, const double* __restrict__ x,
                        const int* __restrict__ abs_cell, int64_t n, int S, DevGrid g, float4* __restrict__ pos32,
-                       float4* __restrict__ x32) {
+                       float4* __restrict__ x32, float4* __restrict__ pos32lo, float4* __restrict__ x32lo) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float p[3];
+  double pd[4];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) p[a] = (float)(q[a * n + i] - (double)abs_cell[a * n + i] * g.h[a]);
-  pos32[i] = make_float4(p[0], p[1], p[2], (float)sigma[i]);
-  float xs[4] = {0, 0, 0, 0};
-  for (int k = 0; k < S && k < 4; ++k) xs[k] = (float)x[k * n + i];
+  for (int a = 0; a < 3; ++a) pd[a] = q[a * n + i] - (double)abs_cell[a * n + i] * g.h[a];
+  pd[3] = sigma[i];
+  float p[4], pl[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    p[a] = (float)pd[a];
+    pl[a] = (float)(pd[a] - (double)p[a]);
+  }
+  pos32[i] = make_float4(p[0], p[1], p[2], p[3]);
+  float xs[4] = {0, 0, 0, 0}, xl[4] = {0, 0, 0, 0};
+  for (int k = 0; k < S && k < 4; ++k) {
+    const double xv = x[k * n + i];
+    xs[k] = (float)xv;
+    xl[k] = (float)(xv - (double)xs[k]);
+  }
   x32[i] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+  if (pos32lo) {
+    pos32lo[i] = make_float4(pl[0], pl[1], pl[2], pl[3]);
+    x32lo[i] = make_float4(xl[0], xl[1], xl[2], xl[3]);
+  }
 }
 
 // FP64 embedding coefficients -> the packed FP32 records the FP32 gradient pass gathers
@@ -662,16 +823,25 @@ cudaError_t launch_gradient_t(int mode, const DevPot& P, const DevGrid& g, const
   const int threads = 256;
   const int64_t work = a.n * NL;
   const unsigned blocks = (unsigned)((work + threads - 1) / threads);
-  if (mode == kGradForce) {
-    k_gradient<PREC, S, NL, kGradForce><<<blocks, threads, 0, s>>>(P, g, a);
-  } else if (PREC == 0) {
-    // the FP64 instantiations also serve the accurate chemical potentials of the FP32 paths
-    if (mode == kGradAll)
+  if constexpr (PREC == 3) {  // float-float: chemical potentials and energies only
+    if (mode != kGradMu) return cudaErrorInvalidValue;
+    k_gradient<3, S, NL, kGradMu><<<blocks, threads, 0, s>>>(P, g, a);
+  } else if constexpr (PREC == 0) {
+    if (mode == kGradForce)
+      k_gradient<0, S, NL, kGradForce><<<blocks, threads, 0, s>>>(P, g, a);
+    else if (mode == kGradForceNoE)
+      k_gradient<0, S, NL, kGradForceNoE><<<blocks, threads, 0, s>>>(P, g, a);
+    else if (mode == kGradAll)
       k_gradient<0, S, NL, kGradAll><<<blocks, threads, 0, s>>>(P, g, a);
     else
       k_gradient<0, S, NL, kGradMu><<<blocks, threads, 0, s>>>(P, g, a);
-  } else {
-    return cudaErrorInvalidValue;
+  } else {  // FP32 node arithmetic: forces (and energies)
+    if (mode == kGradForce)
+      k_gradient<PREC, S, NL, kGradForce><<<blocks, threads, 0, s>>>(P, g, a);
+    else if (mode == kGradForceNoE)
+      k_gradient<PREC, S, NL, kGradForceNoE><<<blocks, threads, 0, s>>>(P, g, a);
+    else
+      return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -680,7 +850,6 @@ cudaError_t launch_gradient_t(int mode, const DevPot& P, const DevGrid& g, const
 template <int PREC, int S>
 cudaError_t dispatch_nl(int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
   switch (nl) {
-    case 1: return mode >= 0 ? launch_gradient_t<PREC, S, 1>(mode, P, g, a, s) : launch_density_t<PREC, S, 1>(P, g, a, s);
     case 4: return mode >= 0 ? launch_gradient_t<PREC, S, 4>(mode, P, g, a, s) : launch_density_t<PREC, S, 4>(P, g, a, s);
     case 8: return mode >= 0 ? launch_gradient_t<PREC, S, 8>(mode, P, g, a, s) : launch_density_t<PREC, S, 8>(P, g, a, s);
     case 16:
@@ -705,6 +874,7 @@ cudaError_t dispatch(int mode, int precision, int nl, const DevPot& P, const Dev
     case 0: return dispatch_s<0>(mode, nl, P, g, a, s);
     case 1: return dispatch_s<1>(mode, nl, P, g, a, s);
     case 2: return dispatch_s<2>(mode, nl, P, g, a, s);
+    case 3: return dispatch_s<3>(mode, nl, P, g, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -712,9 +882,10 @@ cudaError_t dispatch(int mode, int precision, int nl, const DevPot& P, const Dev
 }  // namespace
 
 cudaError_t launch_pack(const double* q, const double* sigma, const double* x, const int* abs_cell, int64_t n,
-                        int S, const DevGrid& g, float4* pos32, float4* x32, cudaStream_t s) {
+                        int S, const DevGrid& g, float4* pos32, float4* x32, float4* pos32lo, float4* x32lo,
+                        cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, sigma, x, abs_cell, n, S, g, pos32, x32);
+  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, sigma, x, abs_cell, n, S, g, pos32, x32, pos32lo, x32lo);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/mxe.h"
+#include "ff.cuh"
 
 namespace mxe {
 
@@ -35,10 +36,12 @@ enum : int {
 // One distinct radial term g(r) = A exp(kappa - lambda r) S(r).
 //  FP64: A, kappa, lambda.  FP32: g_raw = exp2(c0 - c1 r) with
 //  c0 = log2(A) + kappa log2(e), c1 = lambda log2(e).
+//  Float-float: g_raw = exp(lnA_kappa - lambda r) with both constants as float pairs.
 struct RadialFn {
   double A, kappa, lambda;
   float c0, c1, lam_f;
   int on;
+  ff lnA_kappa_ff, lambda_ff;
 };
 
 // Potential in the form the kernels read (passed by value).
@@ -52,12 +55,13 @@ struct DevPot {
   double E[kMaxS];
   double rs, rc, inv_w;          // switch start, cutoff, 1/(rc - rs)
   float rs_f, rc_f, inv_w_f, dS_scale_f;
+  ff rs_ff, inv_w_ff, dS_scale_ff;
 };
 
 // Box / cell grid for positions and image codes.
 struct DevGrid {
   double L[3], invL[3], h[3];
-  float h_f[3], L_f[3], invL_f[3];
+  float h_f[3], h_lo[3], L_f[3], invL_f[3];  // h = h_f + h_lo (float pair)
   int nc[3];
 };
 
@@ -110,8 +114,11 @@ cudaError_t launch_site_max(const double* sigma, const double* q, int64_t n, uns
                             cudaStream_t s);
 
 // eam.cu
+// pos32/x32: FP32 records; pos32lo/x32lo (optional): the float-pair remainders
 cudaError_t launch_pack(const double* q, const double* sigma, const double* x, const int* abs_cell, int64_t n,
-                        int S, const DevGrid& g, float4* pos32, float4* x32, cudaStream_t s);
+                        int S, const DevGrid& g, float4* pos32, float4* x32, float4* pos32lo, float4* x32lo,
+                        cudaStream_t s);
+cudaError_t init_ff_exp_table();
 struct PassArgs {
   const double* q;
   const double* sigma;
@@ -119,6 +126,8 @@ struct PassArgs {
   const double* T;
   const float4* pos32;
   const float4* x32;
+  const float4* pos32lo;  // float-float passes: remainders of pos32, x32, ab32
+  const float4* x32lo;
   const int* nb_off;
   const uint32_t* nb_ent;
   int64_t n;
@@ -129,6 +138,7 @@ struct PassArgs {
   double* b;
   double* e;
   float4* ab32;     // [n][2] packed (a_k, b_k) for the mixed pass-2 gathers
+  float4* ab32lo;
   // pass-2 outputs
   double* gq;
   double* gs;
@@ -141,7 +151,7 @@ struct PassArgs {
 };
 cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                            cudaStream_t s);
-enum { kGradAll = 0, kGradForce = 1, kGradMu = 2 };
+enum { kGradAll = 0, kGradForce = 1, kGradMu = 2, kGradForceNoE = 3 };
 cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                             cudaStream_t s);
 cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);

@@ -54,7 +54,9 @@ class mxe_fire_params(C.Structure):
 
 EXPORTS = ["mxe_status_string", "mxe_create", "mxe_destroy", "mxe_build_neighbors", "mxe_export_neighbors",
            "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async", "mxe_sync_status",
-           "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async", "mxe_diffuse_step_noalloc"]
+           "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async", "mxe_diffuse_step_noalloc",
+           "mxe_timing_enable", "mxe_timing_read"]
+TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
 
 
@@ -91,6 +93,8 @@ def lib():
             L.mxe_diffuse_step.argtypes = [p, p, p, d, d, d]
             L.mxe_diffuse_step_async.argtypes = [p, p, p, d, d, d]
             L.mxe_diffuse_step_noalloc.argtypes = [i64, C.c_int32, p, p, p, p, p, d, d, d, p]
+            L.mxe_timing_enable.argtypes = [p, C.c_int32]
+            L.mxe_timing_read.argtypes = [p, C.c_int32, p, p, p, C.POINTER(C.c_int32)]
             for nm in EXPORTS:
                 if nm != "mxe_status_string":
                     getattr(L, nm).restype = C.c_int
@@ -150,6 +154,24 @@ def mxe_relax(ctx, state, ftol, max_iter, fire: mxe_fire_params | None = None):
 def mxe_diffuse_step(ctx, state, mu_ex_ptr, dt, nu0, Qm, asynchronous=False):
     fn = lib().mxe_diffuse_step_async if asynchronous else lib().mxe_diffuse_step
     return fn(ctx, C.byref(state), C.c_void_p(mu_ex_ptr or 0), float(dt), float(nu0), float(Qm))
+
+
+def mxe_timing_enable(ctx, enable: bool):
+    return lib().mxe_timing_enable(ctx, 1 if enable else 0)
+
+
+def mxe_timing_read(ctx, max_entries=64):
+    """Returns (status, {class: (launches, total_ms)}) and clears the record."""
+    names = C.create_string_buffer(max_entries * TIMING_NAME_LEN)
+    counts = (C.c_int64 * max_entries)()
+    total = (C.c_double * max_entries)()
+    k = C.c_int32(0)
+    st = lib().mxe_timing_read(ctx, max_entries, names, counts, total, C.byref(k))
+    out = {}
+    for e in range(k.value):
+        nm = names.raw[e * TIMING_NAME_LEN:(e + 1) * TIMING_NAME_LEN].split(b"\0", 1)[0].decode()
+        out[nm] = (int(counts[e]), float(total[e]))
+    return st, out
 
 
 def mxe_diffuse_step_noalloc(n, S, x_ptr, T_ptr, mu_ex_ptr, bond_off_ptr, bond_idx_ptr, dt, nu0, Qm, stream):
