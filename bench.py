@@ -46,6 +46,30 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# ---------------------------------------------------------------- replicas
+# With N ranks every rank runs its own independent replica of the workload (its
+# own seed): the path has no data exchange between systems, so there is no
+# data-path collective; the ranks meet only at barriers and at the maximum of
+# their step times.
+def replica_workload(rank):
+    return W.config_binary_alloy(seed=W.SEED + rank)
+
+
+def max_over_ranks(value, dist, device=None):
+    """Maximum of a float over all ranks (identity with one rank)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank_step, ms_per_step_max, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank_step / (ms_per_step_max / 1e3)
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples during the timed region (clock, reasons)."""
@@ -112,12 +136,14 @@ def ops_per_pair(kernel, n_phi, n_f, S):
         static = 2 + 11 + 4 * n_f + 1
         pair = 20 + S * S + 4 * S * S + (n_phi + n_f) + 9 + 24
         return 12 * node + static + pair
-    # float-float passes: add 20, mul 7, exp 110 FP32 operations (see csrc/ff.cuh)
-    term = 7 + 20 + 110 + 7 + 20
+    # float-float passes (csrc/ff.cuh): add 11, mul 7, exp 95 FP32 operations; per
+    # radial term at a node: argument 18 + exp 95 + switch product 7 + sum 11
+    term = 18 + 95 + 7 + 11
+    node = 11 + 10 + 3                      # node distance, square root, switch test
     if kernel.startswith("density_ff"):
-        return 13 * (55 + term * n_f) + 60
+        return 13 * (node + term * n_f) + 300
     if kernel.startswith("gradient_ff"):
-        return 12 * (55 + term * (n_phi + n_f)) + (55 + term * n_f) + 80
+        return 12 * (node + term * (n_phi + n_f)) + (node + term * n_f) + 500
     return None
 
 
@@ -145,7 +171,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sys0 = W.config_binary_alloy()
+    sys0 = replica_workload(rank)
     n = sys0.n
     K = args.fire_iters
     fire = M.make_fire(check_every=K + 1)
@@ -214,11 +240,7 @@ def run_ours(args):
         ms, kern, npairs = timed_arm(p, steps, warm, kernel_events=True)
         if sampler:
             clocks = sampler.stop()
-        t = torch.tensor([ms / steps], dtype=torch.float64)
-        if world > 1:
-            t = t.to(dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        results[p] = (float(t.item()), steps, warm, npairs, kern)
+        results[p] = (max_over_ranks(ms / steps, dist, dev), steps, warm, npairs, kern)
 
     # e2e through the public API with host buffers
     def e2e(prec, steps):
@@ -261,11 +283,7 @@ def run_ours(args):
         return tot / steps, h2d, d2h
 
     e2e_ms, h2d, d2h = e2e(main_prec, max(1, min(args.steps, 5)))
-    t = torch.tensor([e2e_ms], dtype=torch.float64)
-    if world > 1:
-        t = t.to(dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     if world > 1:
         dist.barrier()
@@ -276,7 +294,7 @@ def run_ours(args):
 
     evals_per_step = n * (K + 2)
     ms, steps, warm, npairs, kern = results[main_prec]
-    value = world * evals_per_step / (ms / 1e3)
+    value = aggregate_rate(evals_per_step, ms, world)
     dp = sys0.pot
     n_phi = 3 if dp.cross_geomean else 2
     n_f = 2
@@ -310,10 +328,10 @@ def run_ours(args):
                    "evals_per_step": K + 2, "neighbor_pairs": npairs, "parallelism": f"replicas{world}",
                    "l2": "flushed between steps (256 MB write)", "precision": main_prec},
         "diffusion_steps_per_s": world * 1e3 / ms,
-        "precisions": {p: {"ms_per_step": r[0], "site_evals_per_s": world * evals_per_step / (r[0] / 1e3),
+        "precisions": {p: {"ms_per_step": r[0], "site_evals_per_s": aggregate_rate(evals_per_step, r[0], world),
                            "steps": r[1]} for p, r in results.items()},
         "kernels": shares,
-        "e2e": {"value": world * evals_per_step / (e2e_ms / 1e3), "unit": "site-evals/s",
+        "e2e": {"value": aggregate_rate(evals_per_step, e2e_ms, world), "unit": "site-evals/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 pipe)", "frac": (achieved / (peak_ops / 1e12)) if achieved else None,

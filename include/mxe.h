@@ -232,6 +232,19 @@ MXE_API mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double
 MXE_API mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
                                   double dt, double nu0, double Qm);
 
+/* Reservoir groups of the Euler step (Sec. 4: fix setatomicfraction, fix
+ * setchemicalpotential; Algorithm 1: applied after the mass-transport step and
+ * after the force computation).  fix_mu_mask [n] (nonzero: the site is in the
+ * chemical-potential group) with fix_mu_value [S][n]: in every rate of
+ * mxe_diffuse_step such a site enters with the held excess chemical potential
+ * in place of the computed one.  fix_x_mask [n] with fix_x_value [S][n]: after
+ * the Euler step such a site has x set to the held value (the range check then
+ * applies to the held value).  Caller-owned device arrays; the context keeps
+ * the pointers until the next call (NULL mask and value: no group).  Mass is
+ * no longer conserved when a group exchanges with the rest.                   */
+MXE_API mxe_status mxe_set_reservoirs(mxe_ctx *ctx, const uint8_t *fix_x_mask_dev, const double *fix_x_value_dev,
+                                      const uint8_t *fix_mu_mask_dev, const double *fix_mu_value_dev);
+
 /* Event timing of the context's kernels, for profiling.  While enabled, every
  * kernel launch of the context is bracketed by CUDA events on the context's
  * stream and filed under its kernel class.  mxe_timing_read synchronises the

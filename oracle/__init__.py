@@ -98,6 +98,8 @@ def lib():
             L.orc_pair_average_value.restype = C.c_double
             L.orc_free_energy.argtypes = [p, p, p, p, C.c_int] + [p] * 10
             L.orc_diffuse_step.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double, C.c_double]
+            L.orc_diffuse_step_res.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double,
+                                               C.c_double, p, p, p, p]
             L.orc_relax.argtypes = [p, p, p, p, C.c_double, C.c_double, C.c_int, p, p, p]
             L.orc_num_threads.argtypes = []
             _lib = L
@@ -245,16 +247,25 @@ def free_energy(sys, nb=None, mode=0, q=None, sigma=None, x=None, r_list=None):
     return out
 
 
-def diffuse_step(sys, mu_ex, bond_csr, dt, x=None, nu0=None, Qm=None):
+def diffuse_step(sys, mu_ex, bond_csr, dt, x=None, nu0=None, Qm=None, fix_x=None, fix_mu=None):
     """One forward-Euler step of Eq. MassTransport (reading described in the
-    C source).  Returns (status, x_new)."""
+    C source).  fix_x / fix_mu: optional (mask [n] bool, values [S, n])
+    reservoirs (Sec. 4: setatomicfraction, setchemicalpotential).
+    Returns (status, x_new)."""
     xx = _f64(sys.x if x is None else x).copy()
     T = _f64(sys.T)
     mu = _f64(mu_ex)
     off, idx = bond_csr
-    st = lib().orc_diffuse_step(sys.n, xx.shape[0], _ptr(xx), _ptr(T), _ptr(mu), _ptr(off), _ptr(idx),
-                                float(dt), float(sys.nu0 if nu0 is None else nu0),
-                                float(sys.Qm if Qm is None else Qm))
+    fxm = fxv = fmm = fmv = None
+    if fix_x is not None:
+        fxm = np.ascontiguousarray(fix_x[0], dtype=np.uint8)
+        fxv = _f64(fix_x[1])
+    if fix_mu is not None:
+        fmm = np.ascontiguousarray(fix_mu[0], dtype=np.uint8)
+        fmv = _f64(fix_mu[1])
+    st = lib().orc_diffuse_step_res(sys.n, xx.shape[0], _ptr(xx), _ptr(T), _ptr(mu), _ptr(off), _ptr(idx),
+                                    float(dt), float(sys.nu0 if nu0 is None else nu0),
+                                    float(sys.Qm if Qm is None else Qm), _ptr(fxm), _ptr(fxv), _ptr(fmm), _ptr(fmv))
     return int(st), xx
 
 

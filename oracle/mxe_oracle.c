@@ -635,10 +635,19 @@ int orc_free_energy(const orc_system *sys, const orc_potential *P,
  * x is updated in place only if every x'_ik >= -tol and sum_k x'_ik <= 1 + tol.
  */
 /* ------------------------------------------------------------------ */
-int orc_diffuse_step(int64_t n, int S, double *x, const double *T, const double *mu_ex,
-                     const int32_t *b_off, const int32_t *b_idx,
-                     double dt, double nu0, double Qm)
+int orc_diffuse_step_res(int64_t n, int S, double *x, const double *T, const double *mu_ex,
+                         const int32_t *b_off, const int32_t *b_idx, double dt, double nu0, double Qm,
+                         const uint8_t *fix_x_mask, const double *fix_x_value,
+                         const uint8_t *fix_mu_mask, const double *fix_mu_value)
 {
+    /* Reservoirs (Sec. 4: fix setchemicalpotential, fix setatomicfraction):
+       a site in the chemical-potential group enters every rate with the held
+       value in place of its computed mu; a site in the molar-fraction group
+       has its x set to the held value after the Euler step. */
+    double *mu = (double *)malloc(sizeof(double) * (size_t)(S * n + 1));
+    for (int k = 0; k < S; ++k)
+        for (int64_t i = 0; i < n; ++i)
+            mu[k * n + i] = (fix_mu_mask && fix_mu_mask[i]) ? fix_mu_value[k * n + i] : mu_ex[k * n + i];
     double *xn = (double *)malloc(sizeof(double) * (size_t)(S * n + 1));
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
@@ -656,11 +665,12 @@ int orc_diffuse_step(int64_t n, int S, double *x, const double *T, const double 
                 for (int kk = 0; kk < S; ++kk) xjv -= x[kk * n + j];
                 double Dij = nu0 * exp(-beta_i * Qm);
                 double Dji = nu0 * exp(-beta_j * Qm);
-                double out_ij = Dij * x[k * n + i] * xjv * exp(beta_i * (mu_ex[k * n + i] - mu_ex[k * n + j]));
-                double in_ji = Dji * x[k * n + j] * xiv * exp(beta_j * (mu_ex[k * n + j] - mu_ex[k * n + i]));
+                double out_ij = Dij * x[k * n + i] * xjv * exp(beta_i * (mu[k * n + i] - mu[k * n + j]));
+                double in_ji = Dji * x[k * n + j] * xiv * exp(beta_j * (mu[k * n + j] - mu[k * n + i]));
                 rate += in_ji - out_ij;
             }
             double v = x[k * n + i] + dt * rate;
+            if (fix_x_mask && fix_x_mask[i]) v = fix_x_value[k * n + i];
             xn[k * n + i] = v;
             tot += v;
             if (!(v >= -ORC_X_TOL)) bad = 1;
@@ -669,7 +679,15 @@ int orc_diffuse_step(int64_t n, int S, double *x, const double *T, const double 
     }
     if (!bad) memcpy(x, xn, sizeof(double) * (size_t)(S * n));
     free(xn);
+    free(mu);
     return bad ? ORC_ERR_X_RANGE : ORC_OK;
+}
+
+int orc_diffuse_step(int64_t n, int S, double *x, const double *T, const double *mu_ex,
+                     const int32_t *b_off, const int32_t *b_idx,
+                     double dt, double nu0, double Qm)
+{
+    return orc_diffuse_step_res(n, S, x, T, mu_ex, b_off, b_idx, dt, nu0, Qm, NULL, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------ */

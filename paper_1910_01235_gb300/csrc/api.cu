@@ -68,6 +68,12 @@ struct mxe_ctx {
   double *vq = nullptr, *vs = nullptr, *q0 = nullptr, *s0 = nullptr;
   double* x_new = nullptr;
   double* flux_tmp = nullptr;  // per-site factors of the Euler step
+  double* mu_eff = nullptr;    // mu with the reservoir values
+  // reservoir groups (caller-owned device arrays, kept until changed)
+  const uint8_t* fix_x_mask = nullptr;
+  const double* fix_x_value = nullptr;
+  const uint8_t* fix_mu_mask = nullptr;
+  const double* fix_mu_value = nullptr;
   int* flags = nullptr;
   int* step_flags = nullptr;
   Ctrl* ctrl = nullptr;
@@ -362,11 +368,26 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
   CK(TIMED("build_misc", launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st)));
   CK(TIMED("build_misc", launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st)));
+  // largest stencil candidate set: the cell-staged kernels need it in shared memory
+  CK(cudaMemsetAsync(c->max_row, 0, 2 * sizeof(int), st));
+  CK(TIMED("build_misc", launch_cand_max(ncell, g, c->cell_start, c->max_row + 1, st)));
+  CK(cudaMemcpyAsync(c->ints_h + 2, c->max_row + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int cand_cap = std::max(c->ints_h[2], 1);
+  // MXE_NEIGHBOR_PER_SITE forces the warp-per-site kernels (they are the
+  // fallback for stencils too dense for shared memory; tests compare both)
+  const bool staged = cell_stage_bytes(cand_cap, 256, true) <= 64 * 1024 && !std::getenv("MXE_NEIGHBOR_PER_SITE");
   // counts
   const double rl2 = r_list * r_list, rb2 = r_bond * r_bond;
-  CK(cudaMemsetAsync(c->max_row, 0, sizeof(int), st));
-  CK(TIMED("build_count", launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
-                      rl2, rb2, band, c->nb_cnt, c->bd_cnt, c->max_row, st)));
+  if (staged) {
+    CK(TIMED("build_count", launch_cell_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, c->cell_start,
+                                              c->cell_sites, rl2, rb2, band, cand_cap, c->nb_cnt, c->bd_cnt,
+                                              c->max_row, c->flags, st)));
+  } else {
+    CK(TIMED("build_count", launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of,
+                                             c->cell_start, c->cell_sites, rl2, rb2, band, c->nb_cnt, c->bd_cnt,
+                                             c->max_row, st)));
+  }
   CK(TIMED("build_misc", launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st)));
   CK(TIMED("build_misc", launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st)));
   CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
@@ -388,8 +409,15 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   }
   const int max_row = c->ints_h[0];
   if ((int64_t)max_row * 5 > 200 * 1024) return MXE_ERR_NBR_OVERFLOW;
-  CK(TIMED("build_fill", launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of, c->cell_start, c->cell_sites,
-                     c->abs_cell, rl2, rb2, band, c->nb_off, c->nb_ent, c->bd_off, c->bd_idx, max_row, st)));
+  if (staged && max_row <= 256) {
+    CK(TIMED("build_fill", launch_cell_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, c->cell_start,
+                                            c->cell_sites, c->abs_cell, rl2, rb2, band, cand_cap, c->nb_off,
+                                            c->nb_ent, c->bd_off, c->bd_idx, max_row, c->flags, st)));
+  } else {
+    CK(TIMED("build_fill", launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of,
+                                           c->cell_start, c->cell_sites, c->abs_cell, rl2, rb2, band, c->nb_off,
+                                           c->nb_ent, c->bd_off, c->bd_idx, max_row, st)));
+  }
   CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
   c->n_pairs = npairs;
   c->n_bonds = nbonds;
@@ -500,7 +528,7 @@ mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* po
   A(dalloc(&c->nb_off, n + 1));
   A(dalloc(&c->bd_off, n + 1));
   A(dalloc(&c->totals, 4));
-  A(dalloc(&c->max_row, 1));
+  A(dalloc(&c->max_row, 2));
   A(dalloc(&c->smax_bits, 2));
   A(dalloc(&c->qf, n));
   A(dalloc(&c->q_build, 3 * n));
@@ -532,6 +560,7 @@ mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* po
   A(dalloc(&c->s0, n));
   A(dalloc(&c->x_new, S * n));
   A(dalloc(&c->flux_tmp, flux_scratch_len(n, (int)S)));
+  A(dalloc(&c->mu_eff, S * n));
   A(dalloc(&c->flags, 1));
   A(dalloc(&c->step_flags, 1));
   A(dalloc(&c->ctrl, 1));
@@ -600,6 +629,7 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->s0);
   dfree(c->x_new);
   dfree(c->flux_tmp);
+  dfree(c->mu_eff);
   dfree(c->flags);
   dfree(c->step_flags);
   dfree(c->ctrl);
@@ -640,6 +670,18 @@ mxe_status mxe_export_bonds(mxe_ctx* c, int32_t* offsets_dev, int32_t* idx_dev, 
   if (idx_dev) CK(copy_d2d(idx_dev, c->bd_idx, sizeof(int32_t) * c->n_bonds, c->stream));
   if (n_bonds_out) *n_bonds_out = c->n_bonds;
   CK(cudaStreamSynchronize(c->stream));
+  return MXE_OK;
+}
+
+mxe_status mxe_set_reservoirs(mxe_ctx* c, const uint8_t* fix_x_mask_dev, const double* fix_x_value_dev,
+                              const uint8_t* fix_mu_mask_dev, const double* fix_mu_value_dev) {
+  if (!c) return MXE_ERR_ARG;
+  if ((fix_x_mask_dev == nullptr) != (fix_x_value_dev == nullptr)) return MXE_ERR_ARG;
+  if ((fix_mu_mask_dev == nullptr) != (fix_mu_value_dev == nullptr)) return MXE_ERR_ARG;
+  c->fix_x_mask = fix_x_mask_dev;
+  c->fix_x_value = fix_x_value_dev;
+  c->fix_mu_mask = fix_mu_mask_dev;
+  c->fix_mu_value = fix_mu_value_dev;
   return MXE_OK;
 }
 
@@ -762,6 +804,7 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
   A.ctrl = c->ctrl;
   A.check_skin = 1;
   A.site_E = nullptr;
+  A.lean = 1;
   mxe_status result = MXE_OK;
   int last_iter = -1, rebuilds = 0;
   for (;;) {
@@ -824,6 +867,7 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
     A.ctrl = c->ctrl;
     A.check_skin = 1;
     A.site_E = nullptr;
+    A.lean = 1;
   }
   if (iters_out) *iters_out = H.iter;
   if (fmax_out) *fmax_out = H.fmax;
@@ -856,8 +900,9 @@ mxe_status mxe_diffuse_step_async(mxe_ctx* c, mxe_state* s, const double* mu_ex_
     mu = c->mu_ex;
   }
   CK(cudaMemsetAsync(c->step_flags, 0, sizeof(int), st));
-  CK(TIMED("flux", launch_flux(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, c->flux_tmp, c->x_new,
-                 c->step_flags, st)));
+  CK(TIMED("flux", launch_flux_res(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, c->flux_tmp,
+                                   c->x_new, c->step_flags, c->fix_x_mask, c->fix_x_value, c->fix_mu_mask,
+                                   c->fix_mu_value, c->mu_eff, st)));
   CK(TIMED("commit", launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, st)));
   return MXE_OK;
 }

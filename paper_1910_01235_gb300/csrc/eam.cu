@@ -53,6 +53,10 @@ struct AccD {
   __device__ __forceinline__ void add(float x) { v += (double)x; }
   __device__ __forceinline__ void add(ff x) { v += ff_to_double(x); }
   __device__ __forceinline__ double get() const { return v; }
+  __device__ __forceinline__ float2 get_pair() const {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  }
   __device__ __forceinline__ void team_reduce(int nl) {
     for (int o = nl >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   }
@@ -71,6 +75,7 @@ struct AccFF {
     lo += err;
   }
   __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ float2 get_pair() const { return make_float2(hi, lo); }
   __device__ __forceinline__ void team_reduce(int nl) {
     for (int o = nl >> 1; o > 0; o >>= 1) {
       float oh = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -320,8 +325,17 @@ __device__ __forceinline__ bool chunk_halted(const PassArgs& A) {
 }
 
 // ---------------------------------------------------------------- K2: density pass
+// Minimum resident blocks per SM for the two passes (0: let the compiler choose
+// the register budget); set at build time.
+#ifndef MXE_DENSITY_MIN_BLOCKS
+#define MXE_DENSITY_MIN_BLOCKS 0
+#endif
+#ifndef MXE_GRADIENT_MIN_BLOCKS
+#define MXE_GRADIENT_MIN_BLOCKS 0
+#endif
+
 template <int PREC, int S, int NL>
-__global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A) {
+__global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot P, DevGrid g, PassArgs A) {
   using R = typename Traits<PREC>::R;
   using Acc = typename Traits<PREC>::Acc;
   constexpr int NF = S * S;
@@ -365,11 +379,13 @@ __global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A
         }
       }
       // 12 nodes: site i moved (base_i), site j moved (base_j), each +-s along each axis
-#pragma unroll
+      // float-float node arithmetic is long: keep its node loops rolled so the
+      // kernel fits the instruction cache
+#pragma unroll(PREC == 3 ? 1 : 2)
       for (int site = 0; site < 2; ++site) {
         const R s = site == 0 ? s_i : s_j;
         const R base = D2 + s * s;
-#pragma unroll
+#pragma unroll(PREC == 3 ? 1 : 3)
         for (int a = 0; a < 3; ++a) {
           const R tw = (R)2 * s * d[a];
 #pragma unroll
@@ -417,6 +433,33 @@ __global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A
   const int64_t n = A.n;
   int flag = bad ? kFlagGeometry : 0;
   float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if constexpr (PREC == 1 || PREC == 2) {
+    if (A.lean) {
+      // relaxation loop: only the packed FP32 (a, b) are needed; all in FP32
+      const float4 X = A.x32[i];
+      const float xs[4] = {X.x, X.y, X.z, X.w};
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        const float2 b2 = rb[k].get_pair(), a2 = ra[k].get_pair();
+        const float rf = b2.x + b2.y;
+        const float df = fmaf(a2.x, 1.0f / 12.0f, -b2.x) + fmaf(a2.y, 1.0f / 12.0f, -b2.y);
+        if (rf > (float)kRhoMin) {
+          const float Ef = (float)P.E[k];
+          const float isq = rsqrt_approx(rf);
+          const float dF = -0.5f * Ef * isq;
+          const float d2F = 0.25f * Ef * isq * isq * isq;
+          ab[2 * k] = xs[k] * d2F * df;
+          ab[2 * k + 1] = xs[k] * dF;
+        } else {
+          flag |= kFlagGeometry;
+        }
+      }
+      A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
+      if (S > 2) A.ab32[2 * i + 1] = make_float4(ab[4], ab[5], ab[6], ab[7]);
+      if (flag) atomicOr(A.flags, flag);
+      return;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     const double rbar = rb[k].get();
@@ -480,7 +523,7 @@ __global__ void __launch_bounds__(256) k_density(DevPot P, DevGrid g, PassArgs A
 // formed as G = dS sum_u c_u E_u - S sum_u (c_u lambda_u) E_u (E_u the raw
 // exponentials), three FP32 operations per term.
 template <int PREC, int S, int NL, int MODE>
-__global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs A) {
+__global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPot P, DevGrid g, PassArgs A) {
   constexpr bool DER = MODE != kGradMu;
   constexpr bool MU = MODE == kGradAll || MODE == kGradMu;
   constexpr bool EN = MODE != kGradForceNoE;
@@ -572,11 +615,13 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
 #pragma unroll
       for (int v = 0; v < NF; ++v) af[v] = (R)0;
       R T = (R)0, U[3] = {(R)0, (R)0, (R)0}, Vs = (R)0;
-#pragma unroll
+      // float-float node arithmetic is long: keep its node loops rolled so the
+      // kernel fits the instruction cache
+#pragma unroll(PREC == 3 ? 1 : 2)
       for (int site = 0; site < 2; ++site) {
         const R s = site == 0 ? s_i : s_j;
         const R base = D2 + s * s;
-#pragma unroll
+#pragma unroll(PREC == 3 ? 1 : 3)
         for (int a = 0; a < 3; ++a) {
           const R tw = (R)2 * s * d[a];
           R w2[2];
@@ -675,7 +720,15 @@ __global__ void __launch_bounds__(256) k_gradient(DevPot P, DevGrid g, PassArgs 
   const double sg = A.sigma[i];
   int flag = 0;
   double g0 = gacc[0].get(), g1 = gacc[1].get(), g2 = gacc[2].get();
-  double gs = gsig.get() - 3.0 * kT / sg;
+  double gs;
+  if constexpr (PREC == 1 || PREC == 2) {
+    // FP32 modes: the thermal term in FP32 (no FP64 division)
+    const float2 gp = gsig.get_pair();
+    const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)sg;
+    gs = (double)((gp.x - th) + gp.y);
+  } else {
+    gs = gsig.get() - 3.0 * kT / sg;
+  }
   if (DER && A.gq) {
     A.gq[i] = g0;
     A.gq[n + i] = g1;

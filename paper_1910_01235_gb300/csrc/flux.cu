@@ -28,12 +28,24 @@ namespace {
 
 constexpr double kEMin = 1e-250, kEMax = 1e250;
 
+// Reservoirs (Sec. 4, fix setchemicalpotential / setatomicfraction): a site
+// of the chemical-potential group enters every rate with its held mu; a site of
+// the molar-fraction group has x set to its held value after the step.
+struct Reservoirs {
+  const uint8_t* fix_x_mask;
+  const double* fix_x_value;
+  const uint8_t* fix_mu_mask;
+  const double* fix_mu_value;
+  double* mu_eff;  // [S][n] scratch: mu with the held values (when fix_mu_mask is set)
+};
+
 template <int S>
 __global__ void __launch_bounds__(256) k_flux_prep(const double* __restrict__ x, const double* __restrict__ T,
                                                    const double* __restrict__ mu, int64_t n, double nu0, double Qm,
-                                                   double* __restrict__ fl) {
+                                                   double* __restrict__ fl, Reservoirs res) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const bool held = res.fix_mu_mask && res.fix_mu_mask[i];
   const double beta = 1.0 / (kKB * T[i]);
   double xv = 1.0;
 #pragma unroll
@@ -43,7 +55,9 @@ __global__ void __launch_bounds__(256) k_flux_prep(const double* __restrict__ x,
   fl[2 * n + i] = xv;
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const double E = exp(beta * mu[k * n + i]);
+    const double m = held ? res.fix_mu_value[k * n + i] : mu[k * n + i];
+    if (res.mu_eff) res.mu_eff[k * n + i] = m;
+    const double E = exp(beta * m);
     fl[(3 + 2 * k) * n + i] = E;
     fl[(4 + 2 * k) * n + i] = 1.0 / E;
   }
@@ -63,12 +77,13 @@ __device__ __forceinline__ bool normal_E(const Site& s) { return s.E > kEMin && 
 
 template <int S>
 __global__ void __launch_bounds__(256) k_flux(const double* __restrict__ x, const double* __restrict__ T,
-                                              const double* __restrict__ mu, const double* __restrict__ fl,
+                                              const double* __restrict__ mu_in, const double* __restrict__ fl,
                                               const int* __restrict__ bd_off, const int* __restrict__ bd_idx,
                                               int64_t n, double dt, double* __restrict__ x_new,
-                                              int* __restrict__ flags) {
+                                              int* __restrict__ flags, Reservoirs res) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double* __restrict__ mu = res.mu_eff ? res.mu_eff : mu_in;
   Site si[S];
 #pragma unroll
   for (int k = 0; k < S; ++k) {
@@ -103,9 +118,10 @@ __global__ void __launch_bounds__(256) k_flux(const double* __restrict__ x, cons
   }
   double tot = 0.0;
   bool ok = true;
+  const bool held_x = res.fix_x_mask && res.fix_x_mask[i];
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const double v = __dadd_rn(si[k].x, __dmul_rn(dt, rate[k]));
+    const double v = held_x ? res.fix_x_value[k * n + i] : __dadd_rn(si[k].x, __dmul_rn(dt, rate[k]));
     x_new[k * n + i] = v;
     tot += v;
     ok = ok && (v >= -kXTol);
@@ -127,24 +143,37 @@ __global__ void k_commit(double* __restrict__ x, const double* __restrict__ x_ne
 
 int64_t flux_scratch_len(int64_t n, int S) { return (3 + 2 * (int64_t)S) * n; }
 
+namespace {
+template <int S>
+void flux_kernels(unsigned blocks, const double* x, const double* T, const double* mu_ex, const int* bd_off,
+                  const int* bd_idx, int64_t n, double dt, double nu0, double Qm, double* scratch, double* x_new,
+                  int* flags, const Reservoirs& res, cudaStream_t s) {
+  k_flux_prep<S><<<blocks, 256, 0, s>>>(x, T, mu_ex, n, nu0, Qm, scratch, res);
+  k_flux<S><<<blocks, 256, 0, s>>>(x, T, mu_ex, scratch, bd_off, bd_idx, n, dt, x_new, flags, res);
+}
+}  // namespace
+
+cudaError_t launch_flux_res(const double* x, const double* T, const double* mu_ex, const int* bd_off,
+                            const int* bd_idx, int64_t n, int S, double dt, double nu0, double Qm, double* scratch,
+                            double* x_new, int* flags, const uint8_t* fix_x_mask, const double* fix_x_value,
+                            const uint8_t* fix_mu_mask, const double* fix_mu_value, double* mu_eff,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  Reservoirs res{fix_x_mask, fix_x_value, fix_mu_mask, fix_mu_value, fix_mu_mask ? mu_eff : nullptr};
+  switch (S) {
+    case 1: flux_kernels<1>(blocks, x, T, mu_ex, bd_off, bd_idx, n, dt, nu0, Qm, scratch, x_new, flags, res, s); break;
+    case 2: flux_kernels<2>(blocks, x, T, mu_ex, bd_off, bd_idx, n, dt, nu0, Qm, scratch, x_new, flags, res, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_flux(const double* x, const double* T, const double* mu_ex, const int* bd_off, const int* bd_idx,
                         int64_t n, int S, double dt, double nu0, double Qm, double* scratch, double* x_new,
                         int* flags, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((n + 255) / 256);
-  switch (S) {
-    case 1:
-      k_flux_prep<1><<<blocks, 256, 0, s>>>(x, T, mu_ex, n, nu0, Qm, scratch);
-      k_flux<1><<<blocks, 256, 0, s>>>(x, T, mu_ex, scratch, bd_off, bd_idx, n, dt, x_new, flags);
-      break;
-    case 2:
-      k_flux_prep<2><<<blocks, 256, 0, s>>>(x, T, mu_ex, n, nu0, Qm, scratch);
-      k_flux<2><<<blocks, 256, 0, s>>>(x, T, mu_ex, scratch, bd_off, bd_idx, n, dt, x_new, flags);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return launch_flux_res(x, T, mu_ex, bd_off, bd_idx, n, S, dt, nu0, Qm, scratch, x_new, flags, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, s);
 }
 
 cudaError_t launch_commit_x(double* x, const double* x_new, int64_t count, const int* step_flags, int* flags,

@@ -105,6 +105,18 @@ cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* su
                             const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
                             const int* abs_cell, double rl2, double rb2, float band, const int* nb_off,
                             uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row, cudaStream_t s);
+// cell-staged variants (one block per cell, candidates staged in shared memory)
+cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const int* cell_start, int* out, cudaStream_t s);
+size_t cell_stage_bytes(int cand_cap, int max_row, bool fill);
+cudaError_t launch_cell_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                              int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                              double rl2, double rb2, float band, int cand_cap, int* nb_cnt, int* bd_cnt,
+                              int* max_row, int* flags, cudaStream_t s);
+cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                             int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                             const int* abs_cell, double rl2, double rb2, float band, int cand_cap,
+                             const int* nb_off, uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row,
+                             int* flags, cudaStream_t s);
 // exclusive scan of n int32 counts into out[0..n] (out[n] = total, int64 total in *total64)
 cudaError_t launch_scan(const int* in, int* out, int64_t n, long long* total64, int* tmp, int64_t tmp_len,
                         cudaStream_t s);
@@ -148,6 +160,7 @@ struct PassArgs {
   Ctrl* ctrl;       // optional: kernels return at once if ctrl->halted
   int* flags;
   int check_skin;   // pass 1 checks the rebuild criterion in ctrl first
+  int lean;         // FP32 density pass of the relaxation: write only the packed (a, b)
 };
 cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                            cudaStream_t s);
@@ -167,6 +180,12 @@ cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs,
 
 // flux.cu
 int64_t flux_scratch_len(int64_t n, int S);
+// with reservoir groups (any pointer may be null); mu_eff: [S][n] scratch
+cudaError_t launch_flux_res(const double* x, const double* T, const double* mu_ex, const int* bd_off,
+                            const int* bd_idx, int64_t n, int S, double dt, double nu0, double Qm, double* scratch,
+                            double* x_new, int* flags, const uint8_t* fix_x_mask, const double* fix_x_value,
+                            const uint8_t* fix_mu_mask, const double* fix_mu_value, double* mu_eff,
+                            cudaStream_t s);
 cudaError_t launch_flux(const double* x, const double* T, const double* mu_ex, const int* bd_off, const int* bd_idx,
                         int64_t n, int S, double dt, double nu0, double Qm, double* scratch, double* x_new,
                         int* flags, cudaStream_t s);

@@ -264,6 +264,214 @@ __global__ void k_nbr_fill(const double* __restrict__ q, const float4* __restric
   }
 }
 
+// ---------------------------------------------------------------- cell-staged build
+// One block per cell: the block stages the candidates of the cell's distinct
+// stencil cells (FP32 position, index) in shared memory once, then each warp
+// takes one home site of the cell at a time and tests it against the staged
+// candidates with the same rule as above.  The warp-per-site kernels above are
+// the fallback when a stencil holds more candidates than shared memory fits.
+constexpr int kCellThreads = 128;
+
+struct CellStage {
+  int ncand;
+};
+
+__device__ __forceinline__ CellStage stage_cell(int cell, const DevGrid& g, const int* __restrict__ cell_start,
+                                                const int* __restrict__ cell_sites, const float4* __restrict__ qf,
+                                                float4* cq, int* cj, int* s_off, int* s_beg, int cand_cap,
+                                                int* __restrict__ flags) {
+  if (threadIdx.x == 0) {
+    const Stencil st = make_stencil(cell, g);
+    int k = 0, tot = 0;
+    for (int ax = 0; ax < st.cnt[0]; ++ax)
+      for (int ay = 0; ay < st.cnt[1]; ++ay)
+        for (int az = 0; az < st.cnt[2]; ++az) {
+          const int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+          s_beg[k] = cell_start[c];
+          s_off[k] = tot;
+          tot += cell_start[c + 1] - cell_start[c];
+          ++k;
+        }
+    for (int r = k; r < 28; ++r) s_off[r] = tot;
+  }
+  __syncthreads();
+  int ncand = s_off[27];
+  if (ncand > cand_cap) {  // cannot happen: cand_cap is the measured maximum
+    if (threadIdx.x == 0) atomicOr(flags, kFlagOverflow);
+    ncand = cand_cap;
+  }
+  for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
+    int k = 0;
+    while (t >= s_off[k + 1]) ++k;
+    const int j = cell_sites[s_beg[k] + (t - s_off[k])];
+    cj[t] = j;
+    cq[t] = qf[j];
+  }
+  __syncthreads();
+  return CellStage{ncand};
+}
+
+// Decisions for home site i against staged candidate t (FP64 rule inside the band).
+struct CandResult {
+  bool in, bond;
+  float k[3];
+};
+
+__device__ __forceinline__ CandResult test_cand(int64_t i, const double qi[3], const float4& qfi, int j,
+                                                const float4& qfj, const double* __restrict__ q, int64_t n,
+                                                const DevGrid& g, float rl2f, float rb2f, float band, double rl2,
+                                                double rb2, bool mob, int si, const uint8_t* __restrict__ sub,
+                                                bool need_k) {
+  CandResult r{false, false, {0.f, 0.f, 0.f}};
+  if (j == (int)i) return r;
+  const PairTestF pf = pair_test_f(qfi, qfj, g);
+  int din = decide_f(pf.r2, rl2f, band);
+  int dbo = decide_f(pf.r2, rb2f, band);
+  r.k[0] = pf.k[0];
+  r.k[1] = pf.k[1];
+  r.k[2] = pf.k[2];
+  if (din < 0 || (din > 0 && (dbo < 0 || (need_k && pf.near_half)))) {
+    const PairTest pt = pair_test(qi, q, n, j, g);
+    din = pt.r2 < rl2;
+    dbo = pt.r2 < rb2;
+    r.k[0] = (float)pt.k[0];
+    r.k[1] = (float)pt.k[1];
+    r.k[2] = (float)pt.k[2];
+  }
+  r.in = din > 0;
+  if (r.in && mob) {
+    const int sj = sub ? sub[j] : 0;
+    r.bond = sj == si && dbo > 0;
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_cell_count(
+    const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
+    int64_t n, DevGrid g, const int* __restrict__ cell_start, const int* __restrict__ cell_sites, double rl2,
+    double rb2, float band, int cand_cap, int* __restrict__ nb_cnt, int* __restrict__ bd_cnt,
+    int* __restrict__ max_row, int* __restrict__ flags) {
+  extern __shared__ unsigned char smem[];
+  __shared__ int s_off[28], s_beg[27];
+  float4* cq = reinterpret_cast<float4*>(smem);
+  int* cj = reinterpret_cast<int*>(cq + cand_cap);
+  const int cell = blockIdx.x;
+  const int hbeg = cell_start[cell], hend = cell_start[cell + 1];
+  if (hbeg == hend) return;  // uniform over the block
+  const CellStage cs = stage_cell(cell, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float rl2f = (float)rl2, rb2f = (float)rb2;
+  for (int h = hbeg + warp; h < hend; h += nwarps) {
+    const int64_t i = cell_sites[h];
+    const double qi[3] = {q[i], q[n + i], q[2 * n + i]};
+    const float4 qfi = qf[i];
+    const int si = sub ? sub[i] : 0;
+    const bool mob = (mobile_mask >> si) & 1u;
+    int cnt = 0, bcnt = 0;
+    for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
+      const int t = t0 + lane;
+      CandResult r{false, false, {0.f, 0.f, 0.f}};
+      if (t < cs.ncand) r = test_cand(i, qi, qfi, cj[t], cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, false);
+      cnt += __popc(__ballot_sync(0xffffffffu, r.in));
+      bcnt += __popc(__ballot_sync(0xffffffffu, r.bond));
+    }
+    if (lane == 0) {
+      nb_cnt[i] = cnt;
+      bd_cnt[i] = bcnt;
+      atomicMax(max_row, cnt);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_cell_fill(
+    const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
+    int64_t n, DevGrid g, const int* __restrict__ cell_start, const int* __restrict__ cell_sites,
+    const int* __restrict__ abs_cell, double rl2, double rb2, float band, int cand_cap,
+    const int* __restrict__ nb_off, uint32_t* __restrict__ nb_ent, const int* __restrict__ bd_off,
+    int* __restrict__ bd_idx, int max_row, int* __restrict__ flags) {
+  extern __shared__ unsigned char smem[];
+  __shared__ int s_off[28], s_beg[27];
+  float4* cq = reinterpret_cast<float4*>(smem);
+  int* cj = reinterpret_cast<int*>(cq + cand_cap);
+  const int cell = blockIdx.x;
+  const int hbeg = cell_start[cell], hend = cell_start[cell + 1];
+  if (hbeg == hend) return;
+  const CellStage cs = stage_cell(cell, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint32_t* buf = reinterpret_cast<uint32_t*>(cj + cand_cap) + (size_t)warp * max_row;
+  uint8_t* isb = reinterpret_cast<uint8_t*>(reinterpret_cast<uint32_t*>(cj + cand_cap) + (size_t)nwarps * max_row) +
+                 (size_t)warp * max_row;
+  const float rl2f = (float)rl2, rb2f = (float)rb2;
+  for (int h = hbeg + warp; h < hend; h += nwarps) {
+    const int64_t i = cell_sites[h];
+    const double qi[3] = {q[i], q[n + i], q[2 * n + i]};
+    const float4 qfi = qf[i];
+    const int Ai[3] = {abs_cell[i], abs_cell[n + i], abs_cell[2 * n + i]};
+    const int si = sub ? sub[i] : 0;
+    const bool mob = (mobile_mask >> si) & 1u;
+    int m = 0;
+    for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
+      const int t = t0 + lane;
+      CandResult r{false, false, {0.f, 0.f, 0.f}};
+      int j = 0;
+      if (t < cs.ncand) {
+        j = cj[t];
+        r = test_cand(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
+      }
+      uint32_t ent = 0;
+      if (r.in) {
+        int code = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          int sh = abs_cell[a * n + j] - Ai[a] - g.nc[a] * (int)r.k[a];
+          sh = sh < -1 ? -1 : (sh > 1 ? 1 : sh);
+          code = code * 3 + (sh + 1);
+        }
+        ent = (uint32_t)j | ((uint32_t)code << kCodeShift);
+      }
+      const unsigned msk = __ballot_sync(0xffffffffu, r.in);
+      if (r.in) {
+        const int pos = m + __popc(msk & ((1u << lane) - 1u));
+        if (pos < max_row) {
+          buf[pos] = ent;
+          isb[pos] = r.bond ? 1 : 0;
+        }
+      }
+      m += __popc(msk);
+    }
+    __syncwarp();
+    if (m > max_row) m = max_row;  // cannot happen: max_row is the counted maximum
+    const int off = nb_off[i], boff = bd_off[i];
+    for (int e = lane; e < m; e += 32) {
+      const uint32_t je = buf[e] & kIdxMask;
+      int rank = 0, brank = 0;
+      for (int f = 0; f < m; ++f) {
+        const int less = (buf[f] & kIdxMask) < je;
+        rank += less;
+        brank += less & isb[f];
+      }
+      nb_ent[off + rank] = buf[e];
+      if (isb[e]) bd_idx[boff + brank] = (int)je;
+    }
+    __syncwarp();
+  }
+}
+
+// Largest number of candidates of any cell's stencil.
+__global__ void k_cand_max(int64_t ncell, DevGrid g, const int* __restrict__ cell_start, int* __restrict__ out) {
+  const int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c0 >= ncell) return;
+  const Stencil st = make_stencil((int)c0, g);
+  int tot = 0;
+  for (int ax = 0; ax < st.cnt[0]; ++ax)
+    for (int ay = 0; ay < st.cnt[1]; ++ay)
+      for (int az = 0; az < st.cnt[2]; ++az) {
+        const int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+        tot += cell_start[c + 1] - cell_start[c];
+      }
+  atomicMax(out, tot);
+}
+
 // ---------------------------------------------------------------- scan
 constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
@@ -394,6 +602,47 @@ cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* su
   k_nbr_fill<<<grid_for(n * 32, threads), threads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_of, cell_start,
                                                              cell_sites, abs_cell, rl2, rb2, band, nb_off, nb_ent,
                                                              bd_off, bd_idx, max_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const int* cell_start, int* out, cudaStream_t s) {
+  if (ncell == 0) return cudaSuccess;
+  k_cand_max<<<grid_for(ncell, 256), 256, 0, s>>>(ncell, g, cell_start, out);
+  return cudaGetLastError();
+}
+
+size_t cell_stage_bytes(int cand_cap, int max_row, bool fill) {
+  size_t b = (size_t)cand_cap * (sizeof(float4) + sizeof(int));
+  if (fill) b += (size_t)(kCellThreads / 32) * (size_t)max_row * 5;
+  return b + 16;
+}
+
+cudaError_t launch_cell_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                              int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                              double rl2, double rb2, float band, int cand_cap, int* nb_cnt, int* bd_cnt,
+                              int* max_row, int* flags, cudaStream_t s) {
+  if (n == 0 || ncell == 0) return cudaSuccess;
+  const size_t shm = cell_stage_bytes(cand_cap, 0, false);
+  cudaError_t e = cudaFuncSetAttribute(k_cell_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  k_cell_count<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_start, cell_sites, rl2,
+                                                          rb2, band, cand_cap, nb_cnt, bd_cnt, max_row, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
+                             int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                             const int* abs_cell, double rl2, double rb2, float band, int cand_cap,
+                             const int* nb_off, uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row,
+                             int* flags, cudaStream_t s) {
+  if (n == 0 || ncell == 0) return cudaSuccess;
+  if (max_row < 1) max_row = 1;
+  const size_t shm = cell_stage_bytes(cand_cap, max_row, true);
+  cudaError_t e = cudaFuncSetAttribute(k_cell_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  k_cell_fill<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_start, cell_sites,
+                                                         abs_cell, rl2, rb2, band, cand_cap, nb_off, nb_ent, bd_off,
+                                                         bd_idx, max_row, flags);
   return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ class mxe_fire_params(C.Structure):
 EXPORTS = ["mxe_status_string", "mxe_create", "mxe_destroy", "mxe_build_neighbors", "mxe_export_neighbors",
            "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async", "mxe_sync_status",
            "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async", "mxe_diffuse_step_noalloc",
-           "mxe_timing_enable", "mxe_timing_read"]
+           "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs"]
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
 
@@ -94,6 +94,7 @@ def lib():
             L.mxe_diffuse_step_async.argtypes = [p, p, p, d, d, d]
             L.mxe_diffuse_step_noalloc.argtypes = [i64, C.c_int32, p, p, p, p, p, d, d, d, p]
             L.mxe_timing_enable.argtypes = [p, C.c_int32]
+            L.mxe_set_reservoirs.argtypes = [p, p, p, p, p]
             L.mxe_timing_read.argtypes = [p, C.c_int32, p, p, p, C.POINTER(C.c_int32)]
             for nm in EXPORTS:
                 if nm != "mxe_status_string":
@@ -154,6 +155,11 @@ def mxe_relax(ctx, state, ftol, max_iter, fire: mxe_fire_params | None = None):
 def mxe_diffuse_step(ctx, state, mu_ex_ptr, dt, nu0, Qm, asynchronous=False):
     fn = lib().mxe_diffuse_step_async if asynchronous else lib().mxe_diffuse_step
     return fn(ctx, C.byref(state), C.c_void_p(mu_ex_ptr or 0), float(dt), float(nu0), float(Qm))
+
+
+def mxe_set_reservoirs(ctx, fix_x_mask_ptr=0, fix_x_value_ptr=0, fix_mu_mask_ptr=0, fix_mu_value_ptr=0):
+    return lib().mxe_set_reservoirs(ctx, *[C.c_void_p(p) for p in (fix_x_mask_ptr, fix_x_value_ptr,
+                                                                   fix_mu_mask_ptr, fix_mu_value_ptr)])
 
 
 def mxe_timing_enable(ctx, enable: bool):
@@ -307,9 +313,63 @@ class MxeSystem:
                               asynchronous)
         return self._check(st, "mxe_diffuse_step", allow)
 
+    def set_reservoirs(self, fix_x=None, fix_mu=None):
+        """fix_x / fix_mu: (mask [n] bool, values [S, n]) numpy arrays or None
+        (Sec. 4: setatomicfraction / setchemicalpotential)."""
+        t = self.torch
+        self._res = []
+        ptrs = []
+        for grp in (fix_x, fix_mu):
+            if grp is None:
+                ptrs += [0, 0]
+                continue
+            m = t.as_tensor(np.ascontiguousarray(grp[0], dtype=np.uint8), device=self.device).contiguous()
+            v = t.as_tensor(np.ascontiguousarray(grp[1], dtype=np.float64), device=self.device).contiguous()
+            self._res += [m, v]
+            ptrs += [_ptr(m), _ptr(v)]
+        self._check(mxe_set_reservoirs(self.ctx, *ptrs), "mxe_set_reservoirs")
+
     def staggered_step(self, dt, ftol, max_iter, fire=None):
         """One step of the staggered scheme (Sec. 4): excess chemical potentials,
         one Euler step of x, then relaxation of (q, sigma) at fixed x."""
         self.free_energy_grad(with_mu=False)
         self.diffuse_step(dt, mu_ex=self.mu_ex)
         return self.relax(ftol, max_iter, fire)
+
+
+def _autograd_function():
+    import torch
+
+    class MxeFreeEnergy(torch.autograd.Function):
+        """F(q, sigma, x) as a differentiable scalar.  forward runs the CUDA
+        free-energy pass (neighbour sets rebuilt for the given state); backward
+        returns grad_out times (dF/dq, dF/dsigma, dF/dx) from that same pass,
+        with the vacancy fraction dependent (dF/dx = mu)."""
+
+        @staticmethod
+        def forward(ctx, q, sigma, x, system):
+            system.q.copy_(q.detach())
+            system.sigma.copy_(sigma.detach())
+            system.x.copy_(x.detach())
+            system.build_neighbors()
+            system.free_energy_grad(with_mu=True)
+            ctx.save_for_backward(system.gq.clone(), system.gs.clone(), system.mu.clone())
+            return system.F4[3].clone()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            gq, gs, mu = ctx.saved_tensors
+            return grad_out * gq, grad_out * gs, grad_out * mu, None
+
+    return MxeFreeEnergy
+
+
+_MxeFreeEnergy = None
+
+
+def free_energy(q, sigma, x, system):
+    """Differentiable free energy of `system` (an MxeSystem) at (q, sigma, x)."""
+    global _MxeFreeEnergy
+    if _MxeFreeEnergy is None:
+        _MxeFreeEnergy = _autograd_function()
+    return _MxeFreeEnergy.apply(q, sigma, x, system)

@@ -145,6 +145,25 @@ def test_neighbors_and_bonds_bit_exact(case):
     g.close()
 
 
+@pytest.mark.parametrize("case", ["single", "slab", "tight"])
+def test_neighbor_builders_agree(case, monkeypatch):
+    """The cell-staged builder and the warp-per-site fallback give the same CSR."""
+    if case == "tight":
+        s = W.perturb(W.config_vacancy_lattice(cells=4), 0.2, 0.0)
+    else:
+        s = CASES[case]()
+    lists = []
+    for per_site in (False, True):
+        if per_site:
+            monkeypatch.setenv("MXE_NEIGHBOR_PER_SITE", "1")
+        g = M.MxeSystem(s, "fp64")
+        g.build_neighbors()
+        lists.append([t.cpu().numpy() for t in (*g.export_neighbors(), *g.export_bonds())])
+        g.close()
+    for a, b in zip(*lists):
+        np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("which", ["binary_256k", "slab_4M"])
 def test_neighbors_full_size_sampled_rows(which):
     s = W.CONFIGS[which]()
@@ -233,6 +252,35 @@ def test_diffuse_step_parity_and_mass(prec, case):
     eps = np.finfo(float).eps
     for k in range(s.S):
         assert abs(x1[k].sum() - x0[k].sum().item()) <= 4 * s.n * eps
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ff"])
+def test_diffuse_with_reservoirs_parity(prec):
+    """Reservoir groups (Sec. 4): held x after the step, held mu in every rate."""
+    s = perturbed_single()
+    rng = np.random.default_rng(31)
+    mx = rng.random(s.n) < 0.1
+    mm = (rng.random(s.n) < 0.1) & ~mx
+    fix_x = (mx, np.clip(s.x + 0.05, 0.0, 0.97))
+    fix_mu = (mm, np.full((1, s.n), -2.3))
+    g, out = gpu_eval(s, prec)
+    g.set_reservoirs(fix_x=fix_x, fix_mu=fix_mu)
+    dt = stable_dt(s, g.r_bond, target=1e-4)
+    g.diffuse_step(dt, mu_ex=g.mu_ex)
+    st, off, idx = O.neighbors(s.q, s.L, out["r_list"])
+    fe = O.free_energy(s, (off, idx))
+    boff, bidx = O.bonds(s, g.r_bond, off, idx)
+    st, xo = O.diffuse_step(s, fe["mu_ex"], (boff, bidx), dt, fix_x=fix_x, fix_mu=fix_mu)
+    assert st == O.OK
+    x1 = g.x.cpu().numpy()
+    np.testing.assert_array_equal(x1[:, mx], fix_x[1][:, mx])
+    np.testing.assert_allclose(x1, xo, rtol=0, atol=1e-12)
+    # without the groups the step differs
+    g.set_reservoirs()
+    g.x.copy_(torch.as_tensor(s.x))
+    g.diffuse_step(dt, mu_ex=g.mu_ex)
+    assert np.abs(g.x.cpu().numpy() - x1).max() > 1e-6
     g.close()
 
 

@@ -476,3 +476,30 @@ def test_cu_vacancy_shape_matches_paper():
     c_vac = float(np.sum(1.0 - s.x.sum(axis=0))) / s.n
     assert abs(c_vac - g["c_vac"]) / g["c_vac"] < g["c_vac_rel_tol"]
     assert (s.nu0, s.Qm) == (g["nu0_per_s"], g["Qm_eV"])
+
+
+# ---------------------------------------------------------------- reservoirs
+def test_reservoir_steady_state_detailed_balance():
+    """Sec. 4 reservoir fixes.  Potential off (mu_ex = 0 in the bulk); one
+    layer holds x_r (setatomicfraction) and mu_r (setchemicalpotential).  The
+    steady state of the rate law has every bulk site at detailed balance with
+    the layer: x_b / (1 - x_b) = x_r / (1 - x_r) exp(2 beta (mu_r - 0))."""
+    s = W.config_vacancy_lattice(cells=4, pot=W.potential_off(), x0=0.3)
+    s.x[:] = 0.3
+    st, off, idx = O.neighbors(s.q, s.L, O.r_list_for(s))
+    fe = O.free_energy(s, (off, idx))
+    assert np.all(fe["mu_ex"] == 0.0)
+    boff, bidx = O.bonds(s, 3.0, off, idx)
+    layer = s.q[2] < 0.5 * s.a * 0.5
+    x_r, mu_r = 0.5, 0.01
+    fix_x = (layer, np.full((1, s.n), x_r))
+    fix_mu = (layer, np.full((1, s.n), mu_r))
+    dt = 20 * s.dt_default()
+    x = s.x.copy()
+    for _ in range(4000):
+        st, x = O.diffuse_step(s, fe["mu_ex"], (boff, bidx), dt, x=x, fix_x=fix_x, fix_mu=fix_mu)
+        assert st == O.OK
+    beta = 1.0 / (O.KB * s.T[0])
+    r = x_r / (1 - x_r) * np.exp(2 * beta * mu_r)
+    np.testing.assert_allclose(x[0, layer], x_r, rtol=0, atol=0)
+    np.testing.assert_allclose(x[0, ~layer], r / (1 + r), rtol=0, atol=1e-9)
