@@ -133,6 +133,45 @@ MXE_API const char *mxe_status_string(mxe_status s);
 MXE_API mxe_status mxe_create(mxe_ctx **out, const mxe_box *box, const mxe_potential *pot, int64_t n,
                       mxe_precision precision, void *cuda_stream);
 
+/* Batched ensemble: n_systems independent periodic systems of one potential
+ * in one context (each system is a separate instance of the problem of Sec. 4;
+ * systems share no pair, bond or reduction).  Sites are concatenated system
+ * after system: system b holds sites offsets[b] .. offsets[b+1]-1 (host array
+ * of n_systems + 1 nondecreasing values, offsets[0] = 0, offsets[n_systems] =
+ * n) in the box boxes[b] (host array of n_systems boxes); temperatures,
+ * compositions and sizes may differ between systems.  Every other call takes
+ * the concatenated state and works per system:
+ *  - neighbour and bond sets never cross systems; each system has its own cell
+ *    grid and minimum image; every box must hold 2 r_list (r_list from the
+ *    largest sigma of the whole batch);
+ *  - mxe_free_energy_grad writes F4_dev as [n_systems][4] (E_V, F_vib, F_mix,
+ *    F of each system, each summed in a fixed order);
+ *  - mxe_relax runs FIRE separately per system (own P, norms, dt, alpha,
+ *    n_pos and convergence test; a converged system stops moving while the
+ *    others continue).  It returns MXE_OK when every system converged,
+ *    MXE_ERR_NO_CONVERGE when any reached max_iter; iters_out is the largest
+ *    iteration count and fmax_out the largest fmax; mxe_relax_info gives
+ *    them per system;
+ *  - mxe_diffuse_step uses dt * scale_b in system b (mxe_set_dt_scale;
+ *    default 1), so systems at very different temperatures each take a
+ *    stable step.
+ * 1 <= n_systems <= 1048576.  mxe_create is this call with n_systems = 0 (one
+ * system, offsets ignored).                                                  */
+MXE_API mxe_status mxe_create_batch(mxe_ctx **out, int32_t n_systems, const mxe_box *boxes, const int64_t *offsets,
+                                    const mxe_potential *pot, int64_t n, mxe_precision precision,
+                                    void *cuda_stream);
+
+/* Per-system multipliers of the Euler step of a batch (host array of
+ * n_systems finite values >= 0; NULL restores 1).  MXE_ERR_ARG on a
+ * context without a batch.  Syncs.                                          */
+MXE_API mxe_status mxe_set_dt_scale(mxe_ctx *ctx, const double *scale);
+
+/* Outcome of the last mxe_relax per system (n_entries = n_systems, or 1 for a
+ * context without a batch): FIRE updates taken, fmax at the last evaluation,
+ * and whether fmax <= ftol was reached (host arrays, each may be NULL).      */
+MXE_API mxe_status mxe_relax_info(mxe_ctx *ctx, int32_t n_entries, int32_t *iters, double *fmax,
+                                  int32_t *converged);
+
 /* Release every device allocation of the context.  NULL is accepted. */
 MXE_API mxe_status mxe_destroy(mxe_ctx *ctx);
 
@@ -231,6 +270,39 @@ MXE_API mxe_status mxe_diffuse_step(mxe_ctx *ctx, mxe_state *state, const double
  * next mxe_sync_status.  The conditional commit of x happens on the device. */
 MXE_API mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const double *mu_ex_dev,
                                   double dt, double nu0, double Qm);
+
+/* The staggered scheme (Sec. 4, Algorithm 1) for n_steps steps, each:
+ *   1. excess chemical potentials mu_ex at the current state;
+ *   2. one Euler step of x as mxe_diffuse_step(dt, nu0, Qm) (per-system dt
+ *      scale and reservoir groups included);
+ *   3. relaxation of (q, sigma) at the new x as mxe_relax(ftol, max_iter,
+ *      fire): exactly max_iter + 1 force evaluations are enqueued; a system
+ *      that converges earlier stops moving.  Not converging within max_iter
+ *      is not an error here (the next step starts from the last iterate).
+ * The whole step is captured once in a CUDA graph on a private stream and
+ * replayed on the context's stream, so a step costs one graph launch and no
+ * host round trip; the graph is rebuilt when the state pointers, the step
+ * parameters, the pass shape or the lists change.  When the skin criterion
+ * fails, the graph stops itself; the host rebuilds the lists, finishes the
+ * interrupted step and resumes.  *steps_done (host, optional) receives the
+ * completed steps.  On MXE_ERR_GEOMETRY / NONFINITE / X_RANGE the run stops
+ * inside the failing step: steps before it are complete, and x is not
+ * advanced by a step whose range check failed.  mxe_relax_info then
+ * describes the relaxation of the last step.  Syncs at the end (and at each
+ * rebuild).                                                                  */
+MXE_API mxe_status mxe_run_staggered(mxe_ctx *ctx, mxe_state *state, int32_t n_steps, double dt, double nu0,
+                                     double Qm, double ftol, int32_t max_iter, const mxe_fire_params *fire,
+                                     int32_t *steps_done);
+
+/* Autotuner of the density and gradient passes: times every pass shape
+ * (lanes per site 4, 8, 16 -- the neighbour chunk one site's row is split
+ * into -- times 128 or 256 threads per block) on the given state over one
+ * staggered step's worth of passes and keeps the fastest for this context.
+ * Results do not depend on the shape beyond rounding order.  Requires a
+ * neighbour list.  lanes_out / threads_out (host, optional) receive the
+ * choice.  Syncs.  mxe_set_pass_shape sets a shape directly.                 */
+MXE_API mxe_status mxe_autotune(mxe_ctx *ctx, const mxe_state *state, int32_t *lanes_out, int32_t *threads_out);
+MXE_API mxe_status mxe_set_pass_shape(mxe_ctx *ctx, int32_t lanes, int32_t threads);
 
 /* Reservoir groups of the Euler step (Sec. 4: fix setatomicfraction, fix
  * setchemicalpotential; Algorithm 1: applied after the mass-transport step and

@@ -16,6 +16,25 @@
 
 using namespace mxe;
 
+// What a captured staggered step depends on beyond the context's own buffers.
+struct StepKey {
+  const double *q, *sigma, *x, *T;
+  const uint8_t* sub;
+  uint32_t mobile_mask;
+  double dt, nu0, Qm;
+  int32_t max_iter;
+  double dt0, alpha0;
+  int64_t list_gen;
+  int32_t nl, tpb;
+};
+
+inline bool same_key(const StepKey& a, const StepKey& b) {
+  return a.q == b.q && a.sigma == b.sigma && a.x == b.x && a.T == b.T && a.sub == b.sub &&
+         a.mobile_mask == b.mobile_mask && a.dt == b.dt && a.nu0 == b.nu0 && a.Qm == b.Qm &&
+         a.max_iter == b.max_iter && a.dt0 == b.dt0 && a.alpha0 == b.alpha0 && a.list_gen == b.list_gen &&
+         a.nl == b.nl && a.tpb == b.tpb;
+}
+
 struct mxe_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -77,6 +96,32 @@ struct mxe_ctx {
   int* flags = nullptr;
   int* step_flags = nullptr;
   Ctrl* ctrl = nullptr;
+
+  // batch of independent systems (nsys == 0: one system, box above)
+  int nsys = 0;
+  std::vector<mxe_box> boxes;
+  std::vector<int64_t> sys_off_h;
+  int* sys_of = nullptr;        // [n]
+  int* sys_off = nullptr;       // [nsys + 1]
+  DevGrid* grids = nullptr;     // [nsys]
+  int* cell_base = nullptr;     // [nsys + 1]
+  int* cell_sys = nullptr;      // [ncell_cap]
+  DevGrid* grids_h = nullptr;   // pinned staging of grids
+  int* cell_base_h = nullptr;   // pinned staging of cell_base
+  SysFire* sf = nullptr;        // [nsys] FIRE state of each system
+  SysFire* sf_h = nullptr;      // pinned copy after a relaxation
+  double* dt_sys = nullptr;     // [nsys] Euler step multipliers
+  Batch B{};
+  // pass shape: lanes per site and threads per block of the density/gradient passes
+  int tpb = 256;
+  // captured staggered step
+  int64_t list_gen = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  StepKey step_key{};
+  // result of the last relaxation, per system (one entry without a batch)
+  std::vector<int32_t> last_iters, last_reason;
+  std::vector<double> last_fmax;
 
   // event timing (profiling): launches bracketed by events, filed by class
   bool timing = false;
@@ -289,6 +334,8 @@ void fill_pass(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
   A.ctrl = nullptr;
   A.flags = c->flags;
   A.check_skin = 0;
+  A.batch = c->B;
+  A.tpb = c->tpb;
 }
 
 mxe_status ensure_cells(mxe_ctx* c, int64_t ncell) {
@@ -299,6 +346,11 @@ mxe_status ensure_cells(mxe_ctx* c, int64_t ncell) {
   CK(dalloc(&c->cell_count, cap));
   CK(dalloc(&c->cell_start, cap + 1));
   c->ncell_cap = cap;
+  if (c->nsys) {
+    dfree(c->cell_sys);
+    CK(dalloc(&c->cell_sys, cap));
+    c->B.cell_sys = c->cell_sys;
+  }
   int64_t need = std::max<int64_t>(c->n, cap) + 1;
   if (c->scan_len < scan_tmp_len(need)) {
     dfree(c->scan_tmp);
@@ -306,6 +358,34 @@ mxe_status ensure_cells(mxe_ctx* c, int64_t ncell) {
     CK(dalloc(&c->scan_tmp, c->scan_len));
   }
   return MXE_OK;
+}
+
+// Cell grid of one periodic box: cells no smaller than r_list; a sparse box
+// gets coarser cells so the grid never holds more than `limit` cells.
+int64_t plan_grid(const double L[3], double r_list, int64_t limit, DevGrid& g) {
+  double cell_min = r_list * (1.0 + 1e-9);
+  int64_t ncell = 1;
+  for (int pass = 0; pass < 64; ++pass) {
+    ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      int nc = (int)std::floor(L[a] / cell_min);
+      if (nc < 3) nc = 1;
+      g.nc[a] = nc;
+      ncell *= nc;
+    }
+    if (ncell <= limit) break;
+    cell_min *= 1.25;
+  }
+  for (int a = 0; a < 3; ++a) {
+    g.L[a] = L[a];
+    g.invL[a] = 1.0 / L[a];
+    g.h[a] = L[a] / g.nc[a];
+    g.h_f[a] = (float)g.h[a];
+    g.h_lo[a] = (float)(g.h[a] - (double)g.h_f[a]);
+    g.L_f[a] = (float)g.L[a];
+    g.invL_f[a] = (float)g.invL[a];
+  }
+  return ncell;
 }
 
 mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bond) {
@@ -322,34 +402,29 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   std::memcpy(&qmax, c->bits_h + 1, sizeof(double));
   const double r_list = (c->pot.r_cut + kSqrt6 * smax) + skin;
   if (!std::isfinite(r_list)) return MXE_ERR_ARG;
-  for (int a = 0; a < 3; ++a)
-    if (!(c->box.L[a] >= 2.0 * r_list)) return MXE_ERR_BOX_TOO_SMALL;
   DevGrid& g = c->grid;
-  // cells no smaller than r_list; a sparse box gets coarser cells so the grid
-  // never holds many more cells than sites
-  double cell_min = r_list * (1.0 + 1e-9);
-  int64_t ncell = 1;
-  for (int pass = 0; pass < 64; ++pass) {
-    ncell = 1;
-    for (int a = 0; a < 3; ++a) {
-      int nc = (int)std::floor(c->box.L[a] / cell_min);
-      if (nc < 3) nc = 1;
-      g.nc[a] = nc;
-      ncell *= nc;
-    }
-    if (ncell <= 8 * n + 4096) break;
-    cell_min *= 1.25;
-  }
   double Lmax = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    g.L[a] = c->box.L[a];
-    g.invL[a] = 1.0 / c->box.L[a];
-    g.h[a] = c->box.L[a] / g.nc[a];
-    g.h_f[a] = (float)g.h[a];
-    g.h_lo[a] = (float)(g.h[a] - (double)g.h_f[a]);
-    g.L_f[a] = (float)g.L[a];
-    g.invL_f[a] = (float)g.invL[a];
-    Lmax = std::max(Lmax, g.L[a]);
+  int64_t ncell = 0;
+  if (c->nsys == 0) {
+    for (int a = 0; a < 3; ++a) {
+      if (!(c->box.L[a] >= 2.0 * r_list)) return MXE_ERR_BOX_TOO_SMALL;
+      Lmax = std::max(Lmax, c->box.L[a]);
+    }
+    ncell = plan_grid(c->box.L, r_list, 8 * n + 4096, g);
+  } else {
+    // one grid per system, cells numbered system after system
+    for (int b = 0; b < c->nsys; ++b) {
+      for (int a = 0; a < 3; ++a) {
+        if (!(c->boxes[b].L[a] >= 2.0 * r_list)) return MXE_ERR_BOX_TOO_SMALL;
+        Lmax = std::max(Lmax, c->boxes[b].L[a]);
+      }
+      const int64_t nb = c->sys_off_h[b + 1] - c->sys_off_h[b];
+      c->cell_base_h[b] = (int)ncell;
+      ncell += plan_grid(c->boxes[b].L, r_list, 8 * nb + 64, c->grids_h[b]);
+      if (ncell > (int64_t)1 << 30) return MXE_ERR_NBR_OVERFLOW;
+    }
+    c->cell_base_h[c->nsys] = (int)ncell;
+    g = c->grids_h[0];  // kernels take each site's own grid from the table
   }
   // Error band of the FP32 |d|^2 (u = 2^-24): each component of d carries at
   // most delta = 6 u Qmax (rounded positions and their difference) + u Lmax
@@ -363,14 +438,20 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   const float band = (float)(band_d * (1.0 + 1e-6));
   mxe_status ms = ensure_cells(c, ncell);
   if (ms != MXE_OK) return ms;
+  if (c->nsys) {
+    CK(cudaMemcpyAsync(c->grids, c->grids_h, sizeof(DevGrid) * c->nsys, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->cell_base, c->cell_base_h, sizeof(int) * (c->nsys + 1), cudaMemcpyHostToDevice, st));
+    CK(TIMED("build_misc", launch_segment_ids(c->cell_base, c->nsys, ncell, c->cell_sys, st)));
+  }
+  const Batch& B = c->B;
   // cell lists
   CK(cudaMemsetAsync(c->cell_count, 0, sizeof(int) * ncell, st));
-  CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
+  CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, B, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
   CK(TIMED("build_misc", launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st)));
   CK(TIMED("build_misc", launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st)));
   // largest stencil candidate set: the cell-staged kernels need it in shared memory
   CK(cudaMemsetAsync(c->max_row, 0, 2 * sizeof(int), st));
-  CK(TIMED("build_misc", launch_cand_max(ncell, g, c->cell_start, c->max_row + 1, st)));
+  CK(TIMED("build_misc", launch_cand_max(ncell, g, B, c->cell_start, c->max_row + 1, st)));
   CK(cudaMemcpyAsync(c->ints_h + 2, c->max_row + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int cand_cap = std::max(c->ints_h[2], 1);
@@ -380,11 +461,11 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   // counts
   const double rl2 = r_list * r_list, rb2 = r_bond * r_bond;
   if (staged) {
-    CK(TIMED("build_count", launch_cell_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, c->cell_start,
+    CK(TIMED("build_count", launch_cell_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, B, c->cell_start,
                                               c->cell_sites, rl2, rb2, band, cand_cap, c->nb_cnt, c->bd_cnt,
                                               c->max_row, c->flags, st)));
   } else {
-    CK(TIMED("build_count", launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of,
+    CK(TIMED("build_count", launch_nbr_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, B, c->cell_of,
                                              c->cell_start, c->cell_sites, rl2, rb2, band, c->nb_cnt, c->bd_cnt,
                                              c->max_row, st)));
   }
@@ -410,11 +491,11 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   const int max_row = c->ints_h[0];
   if ((int64_t)max_row * 5 > 200 * 1024) return MXE_ERR_NBR_OVERFLOW;
   if (staged && max_row <= 256) {
-    CK(TIMED("build_fill", launch_cell_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, c->cell_start,
+    CK(TIMED("build_fill", launch_cell_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, B, c->cell_start,
                                             c->cell_sites, c->abs_cell, rl2, rb2, band, cand_cap, c->nb_off,
                                             c->nb_ent, c->bd_off, c->bd_idx, max_row, c->flags, st)));
   } else {
-    CK(TIMED("build_fill", launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, c->cell_of,
+    CK(TIMED("build_fill", launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, B, c->cell_of,
                                            c->cell_start, c->cell_sites, c->abs_cell, rl2, rb2, band, c->nb_off,
                                            c->nb_ent, c->bd_off, c->bd_idx, max_row, st)));
   }
@@ -427,6 +508,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   c->r_bond = r_bond;
   c->sigma_max_build = smax;
   c->have_list = true;
+  c->list_gen += 1;
   return MXE_OK;
 }
 
@@ -445,7 +527,7 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
     return MXE_OK;
   }
   const bool ffm = c->precision == MXE_FP32_FF;
-  CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->pos32, c->x32,
+  CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32,
                  ffm && want_mu ? c->pos32lo : nullptr, ffm && want_mu ? c->x32lo : nullptr, st)));
   if (!want_mu) {
     CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
@@ -460,6 +542,249 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
     PassArgs F = A;
     F.site_E = nullptr;  // energies already come from the accurate pass
     CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, F, st)));
+  }
+  return MXE_OK;
+}
+
+mxe_fire_params fire_params_or_default(const mxe_fire_params* fire) {
+  mxe_fire_params fp = {0.02, 0.1, 1.1, 0.5, 0.1, 0.99, 0.0, 5, 16};
+  if (fire) fp = *fire;
+  return fp;
+}
+
+// Control block at the start of a relaxation (or of a staggered run).
+void init_ctrl(mxe_ctx* c, Ctrl& H, const mxe_fire_params& fp, double ftol, int max_iter) {
+  std::memset(&H, 0, sizeof(Ctrl));
+  H.max_iter = max_iter;
+  H.dt = fp.dt0;
+  H.alpha = fp.alpha0;
+  H.ftol = ftol;
+  H.skin = c->skin;
+  H.sigma_max_build = c->sigma_max_build;
+  H.dt_max = fp.dt_max;
+  H.f_inc = fp.f_inc;
+  H.f_dec = fp.f_dec;
+  H.alpha0 = fp.alpha0;
+  H.f_alpha = fp.f_alpha;
+  H.n_min = fp.n_min;
+  H.sigma_lo = kSigmaMin;
+  H.sigma_hi = fp.sigma_max > 0.0 ? fp.sigma_max : INFINITY;
+}
+
+void relax_pass_args(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
+  fill_pass(c, s, A);
+  A.ctrl = c->ctrl;
+  A.check_skin = 1;
+  A.site_E = nullptr;
+  A.lean = 1;
+}
+
+// One FIRE iteration: the force passes, then the reduction, logic and update
+// (per system for a batch).
+mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->n;
+  CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
+  CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
+  float4* p32 = c->precision != MXE_FP64 ? c->pos32 : nullptr;
+  if (c->nsys) {
+    CK(TIMED("fire_reduce", launch_fire_seg_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->B, c->sf, c->ctrl, c->flags, st)));
+    CK(TIMED("fire_logic", launch_fire_seg_logic(c->sf, c->nsys, c->ctrl, c->flags, st)));
+    CK(TIMED("fire_update", launch_fire_seg_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n,
+                                                   c->grid, c->B, c->sf, p32, c->ctrl, st)));
+  } else {
+    CK(TIMED("fire_reduce", launch_fire_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->partials, c->ctrl, c->flags, st)));
+    CK(TIMED("fire_logic", launch_fire_logic(c->partials, n, c->ctrl, c->flags, st)));
+    CK(TIMED("fire_update", launch_fire_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n,
+                                               c->grid, c->B, p32, c->ctrl, st)));
+  }
+  return MXE_OK;
+}
+
+// FIRE iterations from the current device state (control block, velocities,
+// packed positions) until convergence, max_iter or an error; rebuilds the
+// lists when the skin criterion fails.  H receives the final control block.
+mxe_status fire_loop(mxe_ctx* c, mxe_state* s, int max_iter, int chunk, Ctrl& H) {
+  cudaStream_t st = c->stream;
+  PassArgs A;
+  relax_pass_args(c, s, A);
+  mxe_status result = MXE_OK;
+  int last_iter = -1, rebuilds = 0;
+  for (;;) {
+    // enqueue no more iterations than can still run: max_iter updates plus the
+    // final evaluation
+    const int left = max_iter + 1 - H.iter;
+    const int todo = std::max(1, std::min(chunk, left));
+    for (int it = 0; it < todo; ++it) {
+      mxe_status ms = enqueue_fire_iter(c, s, A);
+      if (ms != MXE_OK) return ms;
+    }
+    CK(cudaMemcpyAsync(&H, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (H.reason == kReasonNone) {
+      if (H.iter == last_iter) {  // no progress over a whole chunk: never expected
+        result = MXE_ERR_STATE;
+        break;
+      }
+      last_iter = H.iter;
+      continue;
+    }
+    last_iter = H.iter;
+    if (H.reason == kReasonConverged) {
+      result = MXE_OK;
+      break;
+    }
+    if (H.reason == kReasonMaxIter) {
+      result = MXE_ERR_NO_CONVERGE;
+      break;
+    }
+    if (H.reason == kReasonAllDone) {  // batches: every system converged or hit max_iter
+      CK(cudaMemcpyAsync(c->sf_h, c->sf, sizeof(SysFire) * c->nsys, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      result = MXE_OK;
+      for (int b = 0; b < c->nsys; ++b)
+        if (c->sf_h[b].reason != kReasonConverged) result = MXE_ERR_NO_CONVERGE;
+      break;
+    }
+    if (H.reason == kReasonError) {
+      result = mxe_sync_status(c);
+      if (result == MXE_OK) result = MXE_ERR_NONFINITE;
+      break;
+    }
+    // rebuild: the skin criterion failed before the next evaluation
+    if (++rebuilds > max_iter + 16) {
+      result = MXE_ERR_STATE;
+      break;
+    }
+    mxe_status ms = build_lists(c, s, c->skin, c->r_bond);
+    if (ms != MXE_OK) {
+      result = ms;
+      break;
+    }
+    H.halted = 0;
+    H.reason = kReasonNone;
+    H.disp2_bits = 0ull;
+    H.smax_bits = 0ull;
+    H.sigma_max_build = c->sigma_max_build;
+    CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    if (c->precision != MXE_FP64)
+      CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32, nullptr, nullptr, st)));
+    // the rebuild may have reallocated the lists: take the current pointers
+    relax_pass_args(c, s, A);
+  }
+  return result;
+}
+
+// Per-system outcome of the last relaxation; for a batch H.fmax becomes the
+// largest fmax.
+mxe_status record_relax_info(mxe_ctx* c, Ctrl& H) {
+  if (c->nsys) {
+    CK(cudaMemcpyAsync(c->sf_h, c->sf, sizeof(SysFire) * c->nsys, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double fm = 0.0;
+    for (int b = 0; b < c->nsys; ++b) {
+      c->last_iters[b] = c->sf_h[b].iter;
+      c->last_fmax[b] = c->sf_h[b].fmax;
+      c->last_reason[b] = c->sf_h[b].reason;
+      fm = std::max(fm, c->sf_h[b].fmax);
+    }
+    H.fmax = fm;
+  } else {
+    c->last_iters[0] = H.iter;
+    c->last_fmax[0] = H.fmax;
+    c->last_reason[0] = H.reason;
+  }
+  return MXE_OK;
+}
+
+// One step of the staggered scheme (Sec. 4): excess chemical potentials, one
+// Euler step of x, then max_iter + 1 FIRE evaluations (kernels after
+// convergence return at once).  Every kernel obeys the control block, so the
+// sequence can be captured once and replayed.
+mxe_status enqueue_staggered_step(mxe_ctx* c, mxe_state* s, const StepKey& k) {
+  cudaStream_t st = c->stream;
+  CK(launch_step_begin(c->ctrl, k.dt0, k.alpha0, st));
+  PassArgs M;
+  fill_pass(c, s, M);
+  M.site_E = nullptr;
+  M.gq = nullptr;
+  M.gs = nullptr;
+  M.ctrl = c->ctrl;
+  M.check_skin = 1;
+  mxe_status ms = enqueue_passes(c, s, M, true);
+  if (ms != MXE_OK) return ms;
+  CK(cudaMemsetAsync(c->step_flags, 0, sizeof(int), st));
+  CK(launch_flux_res(s->x, s->T, c->mu_ex, c->bd_off, c->bd_idx, c->n, c->S, k.dt, k.nu0, k.Qm, c->flux_tmp,
+                     c->x_new, c->step_flags, c->fix_x_mask, c->fix_x_value, c->fix_mu_mask, c->fix_mu_value,
+                     c->mu_eff, c->nsys ? c->dt_sys : nullptr, c->nsys ? c->sys_of : nullptr, c->ctrl, st));
+  CK(launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, c->ctrl, st));
+  if (c->precision != MXE_FP64)
+    CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32, nullptr, nullptr, st));
+  CK(launch_fire_zero_v(c->vq, c->vs, c->n, c->ctrl, st));
+  if (c->nsys) CK(launch_fire_seg_init(c->sf, c->nsys, k.dt0, k.alpha0, c->ctrl, st));
+  PassArgs A;
+  relax_pass_args(c, s, A);
+  for (int it = 0; it <= k.max_iter; ++it) {
+    ms = enqueue_fire_iter(c, s, A);
+    if (ms != MXE_OK) return ms;
+  }
+  CK(launch_step_end(c->ctrl, st));
+  return MXE_OK;
+}
+
+// Capture one staggered step on a private stream (the caller's stream may be
+// the legacy default stream, which cannot be captured) and instantiate it;
+// kept while the key (state pointers, step parameters, list generation, pass
+// shape) is unchanged.
+mxe_status ensure_step_graph(mxe_ctx* c, mxe_state* s, StepKey key) {
+  key.list_gen = c->list_gen;
+  if (c->step_exec && same_key(key, c->step_key)) return MXE_OK;
+  if (c->step_exec) {
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  const bool timing = c->timing;
+  c->stream = c->cap_stream;
+  c->timing = false;
+  mxe_status ms = MXE_OK;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    ms = enqueue_staggered_step(c, s, key);
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+  }
+  c->stream = user;
+  c->timing = timing;
+  if (e == cudaSuccess && ms == MXE_OK) e = cudaGraphInstantiate(&c->step_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (ms != MXE_OK) return ms;
+  if (e != cudaSuccess) {
+    c->step_exec = nullptr;
+    return map_cuda(e);
+  }
+  c->step_key = key;
+  return MXE_OK;
+}
+
+// Work timed by the autotuner: the chemical-potential passes and two FIRE
+// force evaluations, as in one staggered step.
+mxe_status enqueue_tune_work(mxe_ctx* c, const mxe_state* s) {
+  PassArgs M;
+  fill_pass(c, s, M);
+  M.site_E = nullptr;
+  M.gq = nullptr;
+  M.gs = nullptr;
+  mxe_status ms = enqueue_passes(c, s, M, true);
+  if (ms != MXE_OK) return ms;
+  PassArgs A;
+  fill_pass(c, s, A);
+  A.site_E = nullptr;
+  A.lean = 1;
+  for (int r = 0; r < 2; ++r) {
+    CK(launch_density(c->precision, c->nl, c->dp, c->grid, A, c->stream));
+    CK(launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, c->stream));
   }
   return MXE_OK;
 }
@@ -487,7 +812,23 @@ const char* mxe_status_string(mxe_status s) {
 
 mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* pot, int64_t n,
                       mxe_precision precision, void* cuda_stream) {
+  return mxe_create_batch(out, 0, box, nullptr, pot, n, precision, cuda_stream);
+}
+
+mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* boxes, const int64_t* offsets,
+                            const mxe_potential* pot, int64_t n, mxe_precision precision, void* cuda_stream) {
   if (!out) return MXE_ERR_ARG;
+  *out = nullptr;
+  if (n_systems < 0 || n_systems > kMaxSystems || !boxes) return MXE_ERR_ARG;
+  if (n_systems > 0) {
+    if (!offsets || offsets[0] != 0 || offsets[n_systems] != n) return MXE_ERR_ARG;
+    for (int b = 0; b < n_systems; ++b) {
+      if (offsets[b + 1] < offsets[b]) return MXE_ERR_ARG;
+      for (int a = 0; a < 3; ++a)
+        if (!(boxes[b].L[a] > 0.0) || !std::isfinite(boxes[b].L[a])) return MXE_ERR_ARG;
+    }
+  }
+  const mxe_box* box = boxes;
   *out = nullptr;
   if (!box || !pot || n < 0 || n >= (int64_t)kIdxMask) return MXE_ERR_ARG;
   if (precision != MXE_FP64 && precision != MXE_FP32_MIXED && precision != MXE_FP32_FF) return MXE_ERR_ARG;
@@ -568,6 +909,37 @@ mxe_status mxe_create(mxe_ctx** out, const mxe_box* box, const mxe_potential* po
   A(cudaMallocHost((void**)&c->totals_h, sizeof(long long) * 4));
   A(cudaMallocHost((void**)&c->ints_h, sizeof(int) * 4));
   A(cudaMallocHost((void**)&c->bits_h, sizeof(unsigned long long) * 2));
+  const int nsys = n_systems;
+  c->last_iters.assign(std::max(nsys, 1), 0);
+  c->last_fmax.assign(std::max(nsys, 1), 0.0);
+  c->last_reason.assign(std::max(nsys, 1), 0);
+  if (nsys > 0) {
+    c->nsys = nsys;
+    c->boxes.assign(boxes, boxes + nsys);
+    c->sys_off_h.assign(offsets, offsets + nsys + 1);
+    A(dalloc(&c->sys_of, n));
+    A(dalloc(&c->sys_off, nsys + 1));
+    A(dalloc(&c->grids, nsys));
+    A(dalloc(&c->cell_base, nsys + 1));
+    A(dalloc(&c->sf, nsys));
+    A(dalloc(&c->dt_sys, nsys));
+    A(cudaMallocHost((void**)&c->grids_h, sizeof(DevGrid) * nsys));
+    A(cudaMallocHost((void**)&c->cell_base_h, sizeof(int) * (nsys + 1)));
+    A(cudaMallocHost((void**)&c->sf_h, sizeof(SysFire) * nsys));
+    if (e == cudaSuccess) {
+      std::vector<int> off32(offsets, offsets + nsys + 1);
+      std::vector<double> ones(nsys, 1.0);
+      e = cudaMemcpy(c->sys_off, off32.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c->dt_sys, ones.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = launch_segment_ids(c->sys_off, nsys, n, c->sys_of, c->stream);
+    }
+    c->B.nsys = nsys;
+    c->B.sys_of = c->sys_of;
+    c->B.grids = c->grids;
+    c->B.cell_base = c->cell_base;
+    c->B.cell_sys = nullptr;  // set with the cell arrays
+    c->B.sys_off = c->sys_off;
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -588,6 +960,8 @@ mxe_status mxe_destroy(mxe_ctx* c) {
     cudaEventDestroy(t.e1);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   dfree(c->cell_of);
   dfree(c->cell_slot);
   dfree(c->abs_cell);
@@ -633,6 +1007,16 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->flags);
   dfree(c->step_flags);
   dfree(c->ctrl);
+  dfree(c->sys_of);
+  dfree(c->sys_off);
+  dfree(c->grids);
+  dfree(c->cell_base);
+  dfree(c->cell_sys);
+  dfree(c->sf);
+  dfree(c->dt_sys);
+  if (c->grids_h) cudaFreeHost(c->grids_h);
+  if (c->cell_base_h) cudaFreeHost(c->cell_base_h);
+  if (c->sf_h) cudaFreeHost(c->sf_h);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
   if (c->totals_h) cudaFreeHost(c->totals_h);
   if (c->ints_h) cudaFreeHost(c->ints_h);
@@ -682,6 +1066,33 @@ mxe_status mxe_set_reservoirs(mxe_ctx* c, const uint8_t* fix_x_mask_dev, const d
   c->fix_x_value = fix_x_value_dev;
   c->fix_mu_mask = fix_mu_mask_dev;
   c->fix_mu_value = fix_mu_value_dev;
+  return MXE_OK;
+}
+
+mxe_status mxe_set_dt_scale(mxe_ctx* c, const double* scale) {
+  if (!c || c->nsys == 0) return MXE_ERR_ARG;
+  std::vector<double> v(c->nsys, 1.0);
+  if (scale) {
+    for (int b = 0; b < c->nsys; ++b) {
+      if (!(scale[b] >= 0.0) || !std::isfinite(scale[b])) return MXE_ERR_ARG;
+      v[b] = scale[b];
+    }
+  }
+  Guard gd(c->device);
+  CK(cudaMemcpyAsync(c->dt_sys, v.data(), sizeof(double) * c->nsys, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MXE_OK;
+}
+
+mxe_status mxe_relax_info(mxe_ctx* c, int32_t n_entries, int32_t* iters, double* fmax, int32_t* converged) {
+  if (!c) return MXE_ERR_ARG;
+  const int m = std::max(c->nsys, 1);
+  if (n_entries != m) return MXE_ERR_ARG;
+  for (int b = 0; b < m; ++b) {
+    if (iters) iters[b] = c->last_iters[b];
+    if (fmax) fmax[b] = c->last_fmax[b];
+    if (converged) converged[b] = c->last_reason[b] == kReasonConverged ? 1 : 0;
+  }
   return MXE_OK;
 }
 
@@ -750,7 +1161,8 @@ mxe_status mxe_free_energy_grad_async(mxe_ctx* c, const mxe_state* s, double* F4
   if (!want_mu) A.mu_ex = nullptr;
   mxe_status ms = enqueue_passes(c, s, A, want_mu);
   if (ms != MXE_OK) return ms;
-  CK(TIMED("energy_reduce", launch_energy_reduce(c->site_E, c->n, c->partials, F4_dev, c->stream)));
+  if (c->nsys) CK(TIMED("energy_reduce", launch_energy_seg(c->site_E, c->n, c->B, F4_dev, c->stream)));
+  else CK(TIMED("energy_reduce", launch_energy_reduce(c->site_E, c->n, c->partials, F4_dev, c->stream)));
   return MXE_OK;
 }
 
@@ -766,9 +1178,7 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
   if (!c || !state_ok(c, s) || !(ftol >= 0.0) || max_iter < 0) return MXE_ERR_ARG;
   if (!c->have_list) return MXE_ERR_STATE;
   Guard gd(c->device);
-  mxe_fire_params fp = {0.02, 0.1, 1.1, 0.5, 0.1, 0.99, 0.0, 5, 16};
-  if (fire) fp = *fire;
-  const int chunk = fp.check_every > 0 ? fp.check_every : 16;
+  const mxe_fire_params fp = fire_params_or_default(fire);
   const int64_t n = c->n;
   cudaStream_t st = c->stream;
   // clear stale device errors from earlier asynchronous calls into this call's result
@@ -781,94 +1191,14 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
     CK(cudaMemsetAsync(c->vs, 0, sizeof(double) * n, st));
   }
   Ctrl& H = *c->ctrl_h;
-  std::memset(&H, 0, sizeof(Ctrl));
-  H.max_iter = max_iter;
-  H.dt = fp.dt0;
-  H.alpha = fp.alpha0;
-  H.ftol = ftol;
-  H.skin = c->skin;
-  H.sigma_max_build = c->sigma_max_build;
-  H.dt_max = fp.dt_max;
-  H.f_inc = fp.f_inc;
-  H.f_dec = fp.f_dec;
-  H.alpha0 = fp.alpha0;
-  H.f_alpha = fp.f_alpha;
-  H.n_min = fp.n_min;
-  H.sigma_lo = kSigmaMin;
-  H.sigma_hi = fp.sigma_max > 0.0 ? fp.sigma_max : INFINITY;
+  init_ctrl(c, H, fp, ftol, max_iter);
   CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  if (c->nsys) CK(launch_fire_seg_init(c->sf, c->nsys, fp.dt0, fp.alpha0, nullptr, st));
   if (c->precision != MXE_FP64)
-    CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, nullptr, nullptr, st)));
-  PassArgs A;
-  fill_pass(c, s, A);
-  A.ctrl = c->ctrl;
-  A.check_skin = 1;
-  A.site_E = nullptr;
-  A.lean = 1;
-  mxe_status result = MXE_OK;
-  int last_iter = -1, rebuilds = 0;
-  for (;;) {
-    // enqueue no more iterations than can still run: max_iter updates plus the
-    // final evaluation
-    const int left = max_iter + 1 - H.iter;
-    const int todo = std::max(1, std::min(chunk, left));
-    for (int it = 0; it < todo; ++it) {
-      CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
-      CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
-      CK(TIMED("fire_reduce", launch_fire_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->partials, c->ctrl, c->flags, st)));
-      CK(TIMED("fire_logic", launch_fire_logic(c->partials, n, c->ctrl, c->flags, st)));
-      CK(TIMED("fire_update", launch_fire_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n, c->grid,
-                            c->precision != MXE_FP64 ? c->pos32 : nullptr, c->ctrl, st)));
-    }
-    CK(cudaMemcpyAsync(&H, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (H.reason == kReasonNone) {
-      if (H.iter == last_iter) {  // no progress over a whole chunk: never expected
-        result = MXE_ERR_STATE;
-        break;
-      }
-      last_iter = H.iter;
-      continue;
-    }
-    last_iter = H.iter;
-    if (H.reason == kReasonConverged) {
-      result = MXE_OK;
-      break;
-    }
-    if (H.reason == kReasonMaxIter) {
-      result = MXE_ERR_NO_CONVERGE;
-      break;
-    }
-    if (H.reason == kReasonError) {
-      result = mxe_sync_status(c);
-      if (result == MXE_OK) result = MXE_ERR_NONFINITE;
-      break;
-    }
-    // rebuild: the skin criterion failed before the next evaluation
-    if (++rebuilds > max_iter + 16) {
-      result = MXE_ERR_STATE;
-      break;
-    }
-    mxe_status ms = build_lists(c, s, c->skin, c->r_bond);
-    if (ms != MXE_OK) {
-      result = ms;
-      break;
-    }
-    H.halted = 0;
-    H.reason = kReasonNone;
-    H.disp2_bits = 0ull;
-    H.smax_bits = 0ull;
-    H.sigma_max_build = c->sigma_max_build;
-    CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-    if (c->precision != MXE_FP64)
-      CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->pos32, c->x32, nullptr, nullptr, st)));
-    // the rebuild may have reallocated the lists: take the current pointers
-    fill_pass(c, s, A);
-    A.ctrl = c->ctrl;
-    A.check_skin = 1;
-    A.site_E = nullptr;
-    A.lean = 1;
-  }
+    CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, n, c->S, c->grid, c->B, c->pos32, c->x32, nullptr, nullptr, st)));
+  mxe_status result = fire_loop(c, s, max_iter, fp.check_every > 0 ? fp.check_every : 16, H);
+  mxe_status info = record_relax_info(c, H);
+  if (info != MXE_OK && result == MXE_OK) result = info;
   if (iters_out) *iters_out = H.iter;
   if (fmax_out) *fmax_out = H.fmax;
   if (result != MXE_OK && result != MXE_ERR_NO_CONVERGE) {
@@ -880,6 +1210,143 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
     else c->have_list = false;
   }
   return result;
+}
+
+mxe_status mxe_run_staggered(mxe_ctx* c, mxe_state* s, int32_t n_steps, double dt, double nu0, double Qm,
+                             double ftol, int32_t max_iter, const mxe_fire_params* fire, int32_t* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!c || !state_ok(c, s) || n_steps < 0 || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm) ||
+      !(ftol >= 0.0) || max_iter < 0 || max_iter > 100000)
+    return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  if (n_steps == 0 || c->n == 0) {
+    if (steps_done) *steps_done = n_steps;
+    return MXE_OK;
+  }
+  Guard gd(c->device);
+  const mxe_fire_params fp = fire_params_or_default(fire);
+  const int chunk = fp.check_every > 0 ? fp.check_every : 16;
+  cudaStream_t st = c->stream;
+  mxe_status pre = mxe_sync_status(c);
+  if (pre != MXE_OK) return pre;
+  Ctrl& H = *c->ctrl_h;
+  init_ctrl(c, H, fp, ftol, max_iter);
+  CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  const StepKey key{s->q, s->sigma, s->x, s->T, s->sublattice, s->mobile_mask, dt, nu0, Qm, max_iter,
+                    fp.dt0, fp.alpha0, 0, c->nl, c->tpb};
+  mxe_status result = MXE_OK;
+  int done = 0, stops = 0;
+  while (done < n_steps) {
+    mxe_status ms = ensure_step_graph(c, s, key);
+    if (ms != MXE_OK) return ms;
+    for (int k = done; k < n_steps; ++k) CK(cudaGraphLaunch(c->step_exec, st));
+    CK(cudaMemcpyAsync(&H, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    done = H.steps;
+    if (H.reason == kReasonError) {
+      result = mxe_sync_status(c);
+      if (result == MXE_OK) result = MXE_ERR_NONFINITE;
+      break;
+    }
+    if (!(H.halted && H.reason == kReasonRebuild)) {
+      if (done != n_steps) result = MXE_ERR_STATE;  // every launched step must have completed
+      break;
+    }
+    // the skin criterion failed: rebuild, then finish the interrupted step
+    if (++stops > n_steps * (max_iter + 2) + 16) {
+      result = MXE_ERR_STATE;
+      break;
+    }
+    ms = build_lists(c, s, c->skin, c->r_bond);
+    if (ms != MXE_OK) {
+      result = ms;
+      break;
+    }
+    H.halted = 0;
+    H.reason = kReasonNone;
+    H.disp2_bits = 0ull;
+    H.smax_bits = 0ull;
+    H.sigma_max_build = c->sigma_max_build;
+    if (H.phase == 1) {
+      // the Euler step of this step is committed: continue its relaxation
+      // (velocities, dt and alpha kept) outside the graph
+      CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+      if (c->precision != MXE_FP64)
+        CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32, nullptr, nullptr, st)));
+      ms = fire_loop(c, s, max_iter, chunk, H);
+      if (ms != MXE_OK && ms != MXE_ERR_NO_CONVERGE) {
+        result = ms;
+        break;
+      }
+      done += 1;
+      H.steps = done;
+      H.phase = 0;
+    }
+    // phase 0: the step had not changed x; the graph runs it again from its start
+    CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  }
+  mxe_status info = record_relax_info(c, H);
+  if (info != MXE_OK && result == MXE_OK) result = info;
+  if (steps_done) *steps_done = done;
+  return result;
+}
+
+mxe_status mxe_autotune(mxe_ctx* c, const mxe_state* s, int32_t* lanes_out, int32_t* threads_out) {
+  if (!c || !state_ok(c, s)) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  mxe_status pre = mxe_sync_status(c);
+  if (pre != MXE_OK) return pre;
+  cudaStream_t st = c->stream;
+  const bool timing = c->timing;
+  c->timing = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  mxe_status result = MXE_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) result = MXE_ERR_CUDA;
+  const int lanes[3] = {4, 8, 16}, threads[2] = {128, 256};
+  int best_nl = c->nl, best_tpb = c->tpb;
+  float best = INFINITY;
+  for (int a = 0; a < 3 && result == MXE_OK; ++a)
+    for (int b = 0; b < 2 && result == MXE_OK; ++b) {
+      c->nl = lanes[a];
+      c->tpb = threads[b];
+      float total = 0.f;
+      for (int rep = 0; rep < 3 && result == MXE_OK; ++rep) {  // rep 0 warms up
+        if (cudaEventRecord(e0, st) != cudaSuccess) result = MXE_ERR_CUDA;
+        if (result == MXE_OK) result = enqueue_tune_work(c, s);
+        if (result == MXE_OK && cudaEventRecord(e1, st) != cudaSuccess) result = MXE_ERR_CUDA;
+        float ms = 0.f;
+        if (result == MXE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          result = MXE_ERR_CUDA;
+        if (rep > 0) total += ms;
+      }
+      if (result == MXE_OK && total < best) {
+        best = total;
+        best_nl = lanes[a];
+        best_tpb = threads[b];
+      }
+    }
+  c->nl = best_nl;
+  c->tpb = best_tpb;
+  c->timing = timing;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (result != MXE_OK) {
+    cudaGetLastError();
+    return result;
+  }
+  mxe_status fl = mxe_sync_status(c);
+  if (fl != MXE_OK) return fl;
+  if (lanes_out) *lanes_out = c->nl;
+  if (threads_out) *threads_out = c->tpb;
+  return MXE_OK;
+}
+
+mxe_status mxe_set_pass_shape(mxe_ctx* c, int32_t lanes, int32_t threads) {
+  if (!c || (lanes != 4 && lanes != 8 && lanes != 16) || (threads != 128 && threads != 256)) return MXE_ERR_ARG;
+  c->nl = lanes;
+  c->tpb = threads;
+  return MXE_OK;
 }
 
 mxe_status mxe_diffuse_step_async(mxe_ctx* c, mxe_state* s, const double* mu_ex_dev, double dt, double nu0,
@@ -902,8 +1369,9 @@ mxe_status mxe_diffuse_step_async(mxe_ctx* c, mxe_state* s, const double* mu_ex_
   CK(cudaMemsetAsync(c->step_flags, 0, sizeof(int), st));
   CK(TIMED("flux", launch_flux_res(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, c->flux_tmp,
                                    c->x_new, c->step_flags, c->fix_x_mask, c->fix_x_value, c->fix_mu_mask,
-                                   c->fix_mu_value, c->mu_eff, st)));
-  CK(TIMED("commit", launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, st)));
+                                   c->fix_mu_value, c->mu_eff, c->nsys ? c->dt_sys : nullptr,
+                                   c->nsys ? c->sys_of : nullptr, nullptr, st)));
+  CK(TIMED("commit", launch_commit_x(s->x, c->x_new, (int64_t)c->S * c->n, c->step_flags, c->flags, nullptr, st)));
   return MXE_OK;
 }
 

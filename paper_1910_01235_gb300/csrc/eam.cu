@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
   }
   int bad = 0;
   if (active) {
+    const DevGrid gs = site_grid(g, A.batch, i);
     SiteData<PREC, S> si;
     load_site(A, i, si);
     const R s_i = sqrt6<R>() * si.sig;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
       SiteData<PREC, S> sj;
       load_site(A, j, sj);
       R d[3];
-      separation(g, si, sj, ent >> kCodeShift, d);
+      separation(gs, si, sj, ent >> kCodeShift, d);
       const R s_j = sqrt6<R>() * sj.sig;
       const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       R fst[NF], fav[NF];
@@ -544,6 +545,7 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
 #pragma unroll
   for (int k = 0; k < S; ++k) mu[k].zero();
   if (active) {
+    const DevGrid gs = site_grid(g, A.batch, i);
     SiteData<PREC, S> si;
     load_site(A, i, si);
     R ai[S], bi[S];
@@ -558,7 +560,7 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
       R aj[S], bj[S];
       load_ab(A, j, aj, bj, (SiteData<PREC, S>*)nullptr);
       R d[3];
-      separation(g, si, sj, ent >> kCodeShift, d);
+      separation(gs, si, sj, ent >> kCodeShift, d);
       const R s_j = sqrt6<R>() * sj.sig;
       const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       // pair weights of the distinct radial terms
@@ -773,10 +775,12 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
 
 // ---------------------------------------------------------------- K7: pack
 __global__ void k_pack(const double* __restrict__ q, const double* __restrict__ sigma, const double* __restrict__ x,
-                       const int* __restrict__ abs_cell, int64_t n, int S, DevGrid g, float4* __restrict__ pos32,
-                       float4* __restrict__ x32, float4* __restrict__ pos32lo, float4* __restrict__ x32lo) {
+                       const int* __restrict__ abs_cell, int64_t n, int S, DevGrid g0, Batch B,
+                       float4* __restrict__ pos32, float4* __restrict__ x32, float4* __restrict__ pos32lo,
+                       float4* __restrict__ x32lo) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const DevGrid g = site_grid(g0, B, i);
   double pd[4];
 #pragma unroll
   for (int a = 0; a < 3; ++a) pd[a] = q[a * n + i] - (double)abs_cell[a * n + i] * g.h[a];
@@ -864,16 +868,44 @@ __global__ void k_energy_final(const double* __restrict__ partials, int64_t ngro
   }
 }
 
+// Batches: one block per system sums its own sites with a fixed stride and
+// tree, F4 laid out [nsys][4].
+__global__ void __launch_bounds__(256) k_energy_seg(const double* __restrict__ site_E, int64_t n,
+                                                    const int* __restrict__ sys_off, double* __restrict__ F4) {
+  __shared__ double sh[3][256];
+  const int sys = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t beg = sys_off[sys], end = sys_off[sys + 1];
+  for (int c = 0; c < 3; ++c) {
+    double v = 0.0;
+    for (int64_t i = beg + tid; i < end; i += 256) v += site_E[c * n + i];
+    sh[c][tid] = v;
+  }
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double* o = F4 + 4 * (int64_t)sys;
+    o[0] = sh[0][0];
+    o[1] = sh[1][0];
+    o[2] = sh[2][0];
+    o[3] = (sh[0][0] + sh[1][0]) + sh[2][0];
+  }
+}
+
 template <int PREC, int S, int NL>
 cudaError_t launch_density_t(const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
-  const int threads = 256;
+  const int threads = a.tpb > 0 ? a.tpb : 256;
   const int64_t work = a.n * NL;
   k_density<PREC, S, NL><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(P, g, a);
   return cudaGetLastError();
 }
 template <int PREC, int S, int NL>
 cudaError_t launch_gradient_t(int mode, const DevPot& P, const DevGrid& g, const PassArgs& a, cudaStream_t s) {
-  const int threads = 256;
+  const int threads = a.tpb > 0 ? a.tpb : 256;
   const int64_t work = a.n * NL;
   const unsigned blocks = (unsigned)((work + threads - 1) / threads);
   if constexpr (PREC == 3) {  // float-float: chemical potentials and energies only
@@ -923,6 +955,7 @@ cudaError_t dispatch_s(int mode, int nl, const DevPot& P, const DevGrid& g, cons
 cudaError_t dispatch(int mode, int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                      cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
+  if (a.tpb < 0 || a.tpb > 256 || a.tpb % 32 != 0) return cudaErrorInvalidValue;
   switch (precision) {
     case 0: return dispatch_s<0>(mode, nl, P, g, a, s);
     case 1: return dispatch_s<1>(mode, nl, P, g, a, s);
@@ -935,10 +968,10 @@ cudaError_t dispatch(int mode, int precision, int nl, const DevPot& P, const Dev
 }  // namespace
 
 cudaError_t launch_pack(const double* q, const double* sigma, const double* x, const int* abs_cell, int64_t n,
-                        int S, const DevGrid& g, float4* pos32, float4* x32, float4* pos32lo, float4* x32lo,
-                        cudaStream_t s) {
+                        int S, const DevGrid& g, const Batch& B, float4* pos32, float4* x32, float4* pos32lo,
+                        float4* x32lo, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, sigma, x, abs_cell, n, S, g, pos32, x32, pos32lo, x32lo);
+  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, sigma, x, abs_cell, n, S, g, B, pos32, x32, pos32lo, x32lo);
   return cudaGetLastError();
 }
 
@@ -963,6 +996,12 @@ cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partia
   if (ng < 1) ng = 1;
   k_energy_partials<<<(unsigned)ng, kReduceGroup / 4, 0, s>>>(site_E, n, ng, partials);
   k_energy_final<<<1, 256, 0, s>>>(partials, ng, F4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, double* F4, cudaStream_t s) {
+  if (B.nsys <= 0) return cudaSuccess;
+  k_energy_seg<<<(unsigned)B.nsys, 256, 0, s>>>(site_E, n, B.sys_off, F4);
   return cudaGetLastError();
 }
 

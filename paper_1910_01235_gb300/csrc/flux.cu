@@ -37,6 +37,10 @@ struct Reservoirs {
   const uint8_t* fix_mu_mask;
   const double* fix_mu_value;
   double* mu_eff;  // [S][n] scratch: mu with the held values (when fix_mu_mask is set)
+  // batches: the step of site i is dt * dt_sys[sys_of[i]] (both null: dt)
+  const double* dt_sys;
+  const int* sys_of;
+  const Ctrl* gate;  // optional: nothing runs while gate->halted
 };
 
 template <int S>
@@ -44,7 +48,7 @@ __global__ void __launch_bounds__(256) k_flux_prep(const double* __restrict__ x,
                                                    const double* __restrict__ mu, int64_t n, double nu0, double Qm,
                                                    double* __restrict__ fl, Reservoirs res) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (res.gate && res.gate->halted)) return;
   const bool held = res.fix_mu_mask && res.fix_mu_mask[i];
   const double beta = 1.0 / (kKB * T[i]);
   double xv = 1.0;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(256) k_flux(const double* __restrict__ x, cons
                                               int64_t n, double dt, double* __restrict__ x_new,
                                               int* __restrict__ flags, Reservoirs res) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (res.gate && res.gate->halted)) return;
   const double* __restrict__ mu = res.mu_eff ? res.mu_eff : mu_in;
   Site si[S];
 #pragma unroll
@@ -119,9 +123,10 @@ __global__ void __launch_bounds__(256) k_flux(const double* __restrict__ x, cons
   double tot = 0.0;
   bool ok = true;
   const bool held_x = res.fix_x_mask && res.fix_x_mask[i];
+  const double dti = res.dt_sys ? __dmul_rn(dt, res.dt_sys[res.sys_of[i]]) : dt;
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const double v = held_x ? res.fix_x_value[k * n + i] : __dadd_rn(si[k].x, __dmul_rn(dt, rate[k]));
+    const double v = held_x ? res.fix_x_value[k * n + i] : __dadd_rn(si[k].x, __dmul_rn(dti, rate[k]));
     x_new[k * n + i] = v;
     tot += v;
     ok = ok && (v >= -kXTol);
@@ -131,12 +136,21 @@ __global__ void __launch_bounds__(256) k_flux(const double* __restrict__ x, cons
 }
 
 __global__ void k_commit(double* __restrict__ x, const double* __restrict__ x_new, int64_t count,
-                         const int* __restrict__ step_flags, int* __restrict__ flags) {
+                         const int* __restrict__ step_flags, int* __restrict__ flags, Ctrl* __restrict__ gate) {
+  if (gate && gate->halted) return;
   const int sf = *step_flags;
-  if (sf && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, sf);  // keep the error for the status call
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if (sf && lead) {
+    atomicOr(flags, sf);  // keep the error for the status call
+    if (gate && (sf & kFlagXRange)) {
+      gate->reason = kReasonError;
+      gate->halted = 1;
+    }
+  }
   if (sf & kFlagXRange) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < count) x[t] = x_new[t];
+  if (gate && lead) gate->phase = 1;
 }
 
 }  // namespace
@@ -157,10 +171,11 @@ cudaError_t launch_flux_res(const double* x, const double* T, const double* mu_e
                             const int* bd_idx, int64_t n, int S, double dt, double nu0, double Qm, double* scratch,
                             double* x_new, int* flags, const uint8_t* fix_x_mask, const double* fix_x_value,
                             const uint8_t* fix_mu_mask, const double* fix_mu_value, double* mu_eff,
-                            cudaStream_t s) {
+                            const double* dt_sys, const int* sys_of, Ctrl* gate, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if ((dt_sys == nullptr) != (sys_of == nullptr)) return cudaErrorInvalidValue;
   const unsigned blocks = (unsigned)((n + 255) / 256);
-  Reservoirs res{fix_x_mask, fix_x_value, fix_mu_mask, fix_mu_value, fix_mu_mask ? mu_eff : nullptr};
+  Reservoirs res{fix_x_mask, fix_x_value, fix_mu_mask, fix_mu_value, fix_mu_mask ? mu_eff : nullptr, dt_sys, sys_of, gate};
   switch (S) {
     case 1: flux_kernels<1>(blocks, x, T, mu_ex, bd_off, bd_idx, n, dt, nu0, Qm, scratch, x_new, flags, res, s); break;
     case 2: flux_kernels<2>(blocks, x, T, mu_ex, bd_off, bd_idx, n, dt, nu0, Qm, scratch, x_new, flags, res, s); break;
@@ -173,13 +188,13 @@ cudaError_t launch_flux(const double* x, const double* T, const double* mu_ex, c
                         int64_t n, int S, double dt, double nu0, double Qm, double* scratch, double* x_new,
                         int* flags, cudaStream_t s) {
   return launch_flux_res(x, T, mu_ex, bd_off, bd_idx, n, S, dt, nu0, Qm, scratch, x_new, flags, nullptr, nullptr,
-                         nullptr, nullptr, nullptr, s);
+                         nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, s);
 }
 
 cudaError_t launch_commit_x(double* x, const double* x_new, int64_t count, const int* step_flags, int* flags,
-                            cudaStream_t s) {
+                            Ctrl* gate, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  k_commit<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(x, x_new, count, step_flags, flags);
+  k_commit<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(x, x_new, count, step_flags, flags, gate);
   return cudaGetLastError();
 }
 

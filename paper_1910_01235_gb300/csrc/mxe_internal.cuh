@@ -65,6 +65,24 @@ struct DevGrid {
   int nc[3];
 };
 
+// Several independent periodic systems in one context (sites of system s are
+// the contiguous range [sys_off[s], sys_off[s+1])).  nsys == 0: one system,
+// every kernel uses the DevGrid it receives by value.
+constexpr int kMaxSystems = 1 << 20;
+
+struct Batch {
+  int nsys;
+  const int* sys_of;      // [n] system of each site
+  const DevGrid* grids;   // [nsys] box and cell grid of each system
+  const int* cell_base;   // [nsys + 1] first global cell of each system
+  const int* cell_sys;    // [ncell] system of each global cell
+  const int* sys_off;     // [nsys + 1] first site of each system
+};
+
+__device__ __forceinline__ DevGrid site_grid(const DevGrid& g, const Batch& B, int64_t i) {
+  return B.nsys ? B.grids[B.sys_of[i]] : g;
+}
+
 // FIRE / relaxation control block living in device memory.
 struct Ctrl {
   int flags;          // kFlag* bits
@@ -86,34 +104,49 @@ struct Ctrl {
   double dt_max, f_inc, f_dec, alpha0, f_alpha;
   double sigma_lo, sigma_hi;      // box of the widths
   int n_min;
+  // staggered runs captured in a graph
+  int phase;          // 0: before the Euler step of the current step, 1: after it
+  int steps;          // completed steps
   int pad;
 };
 
-enum { kReasonNone = 0, kReasonConverged = 1, kReasonMaxIter = 2, kReasonRebuild = 3, kReasonError = 4 };
+enum { kReasonNone = 0, kReasonConverged = 1, kReasonMaxIter = 2, kReasonRebuild = 3, kReasonError = 4,
+       kReasonAllDone = 5 };
+
+// FIRE state of one system of a batch (the global Ctrl keeps the constants,
+// the skin maxima and the global halt).
+struct SysFire {
+  int halted, reason, iter, n_pos;
+  double dt, alpha, keep, mix, one_minus_alpha, fmax;
+  double P, vv, ff;
+};
 
 // ---------------------------------------------------------------- launchers
 // neighbours.cu
-cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, int* cell_of, int* cell_slot,
-                               int* cell_count, int* abs_cell, float4* qf, cudaStream_t s);
+cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, const Batch& B, int* cell_of,
+                               int* cell_slot, int* cell_count, int* abs_cell, float4* qf, cudaStream_t s);
 cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slot, const int* cell_start,
                               int* cell_sites, cudaStream_t s);
 cudaError_t launch_nbr_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                             const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                             const DevGrid& g, const Batch& B, const int* cell_of, const int* cell_start, const int* cell_sites,
                              double rl2, double rb2, float band, int* nb_cnt, int* bd_cnt, int* max_row,
                              cudaStream_t s);
 cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                            const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                            const DevGrid& g, const Batch& B, const int* cell_of, const int* cell_start, const int* cell_sites,
                             const int* abs_cell, double rl2, double rb2, float band, const int* nb_off,
                             uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row, cudaStream_t s);
 // cell-staged variants (one block per cell, candidates staged in shared memory)
-cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const int* cell_start, int* out, cudaStream_t s);
+cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start, int* out,
+                            cudaStream_t s);
 size_t cell_stage_bytes(int cand_cap, int max_row, bool fill);
+// out[t] = the last segment s with base[s] <= t, for t < count (base: nseg + 1 nondecreasing starts)
+cudaError_t launch_segment_ids(const int* base, int nseg, int64_t count, int* out, cudaStream_t s);
 cudaError_t launch_cell_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                              int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                              int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start, const int* cell_sites,
                               double rl2, double rb2, float band, int cand_cap, int* nb_cnt, int* bd_cnt,
                               int* max_row, int* flags, cudaStream_t s);
 cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                             int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                             int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start, const int* cell_sites,
                              const int* abs_cell, double rl2, double rb2, float band, int cand_cap,
                              const int* nb_off, uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row,
                              int* flags, cudaStream_t s);
@@ -128,8 +161,8 @@ cudaError_t launch_site_max(const double* sigma, const double* q, int64_t n, uns
 // eam.cu
 // pos32/x32: FP32 records; pos32lo/x32lo (optional): the float-pair remainders
 cudaError_t launch_pack(const double* q, const double* sigma, const double* x, const int* abs_cell, int64_t n,
-                        int S, const DevGrid& g, float4* pos32, float4* x32, float4* pos32lo, float4* x32lo,
-                        cudaStream_t s);
+                        int S, const DevGrid& g, const Batch& B, float4* pos32, float4* x32, float4* pos32lo,
+                        float4* x32lo, cudaStream_t s);
 cudaError_t init_ff_exp_table();
 struct PassArgs {
   const double* q;
@@ -161,6 +194,8 @@ struct PassArgs {
   int* flags;
   int check_skin;   // pass 1 checks the rebuild criterion in ctrl first
   int lean;         // FP32 density pass of the relaxation: write only the packed (a, b)
+  Batch batch;      // several systems (nsys > 0): per-site box and cell grid
+  int tpb;  // threads per block of the density and gradient passes (0: 256)
 };
 cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                            cudaStream_t s);
@@ -169,6 +204,8 @@ cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, co
                             cudaStream_t s);
 cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s);
+// batches: F4 [nsys][4], one block per system in a fixed order
+cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, double* F4, cudaStream_t s);
 
 // relax.cu
 cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
@@ -176,7 +213,22 @@ cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double*
 cudaError_t launch_fire_logic(const double* partials, int64_t n, Ctrl* ctrl, int* flags, cudaStream_t s);
 cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
                                const double* gs, const double* q_build, const int* abs_cell, int64_t n,
-                               const DevGrid& g, float4* pos32, Ctrl* ctrl, cudaStream_t s);
+                               const DevGrid& g, const Batch& B, float4* pos32, Ctrl* ctrl, cudaStream_t s);
+// batches: one block per system reduces, one block runs every system's FIRE logic
+cudaError_t launch_fire_seg_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
+                                   const double* vs, int64_t n, const Batch& B, SysFire* sf, Ctrl* ctrl, int* flags,
+                                   cudaStream_t s);
+cudaError_t launch_fire_seg_logic(SysFire* sf, int nsys, Ctrl* ctrl, const int* flags, cudaStream_t s);
+cudaError_t launch_fire_seg_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
+                                   const double* gs, const double* q_build, const int* abs_cell, int64_t n,
+                                   const DevGrid& g, const Batch& B, const SysFire* sf, float4* pos32, Ctrl* ctrl,
+                                   cudaStream_t s);
+cudaError_t launch_fire_seg_init(SysFire* sf, int nsys, double dt0, double alpha0, const Ctrl* gate, cudaStream_t s);
+// staggered steps captured in a graph: per-step bookkeeping (a stop for a
+// rebuild or an error is kept until the host clears it)
+cudaError_t launch_step_begin(Ctrl* ctrl, double dt0, double alpha0, cudaStream_t s);
+cudaError_t launch_step_end(Ctrl* ctrl, cudaStream_t s);
+cudaError_t launch_fire_zero_v(double* vq, double* vs, int64_t n, const Ctrl* gate, cudaStream_t s);
 
 // flux.cu
 int64_t flux_scratch_len(int64_t n, int S);
@@ -185,11 +237,13 @@ cudaError_t launch_flux_res(const double* x, const double* T, const double* mu_e
                             const int* bd_idx, int64_t n, int S, double dt, double nu0, double Qm, double* scratch,
                             double* x_new, int* flags, const uint8_t* fix_x_mask, const double* fix_x_value,
                             const uint8_t* fix_mu_mask, const double* fix_mu_value, double* mu_eff,
-                            cudaStream_t s);
+                            const double* dt_sys, const int* sys_of, Ctrl* gate, cudaStream_t s);
 cudaError_t launch_flux(const double* x, const double* T, const double* mu_ex, const int* bd_off, const int* bd_idx,
                         int64_t n, int S, double dt, double nu0, double Qm, double* scratch, double* x_new,
                         int* flags, cudaStream_t s);
+// gate (optional): nothing runs while gate->halted; a range error stops the
+// run (gate->reason = error), a commit sets gate->phase = 1
 cudaError_t launch_commit_x(double* x, const double* x_new, int64_t count, const int* step_flags, int* flags,
-                            cudaStream_t s);
+                            Ctrl* gate, cudaStream_t s);
 
 }  // namespace mxe

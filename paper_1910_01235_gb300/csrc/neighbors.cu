@@ -21,11 +21,13 @@
 namespace mxe {
 namespace {
 
-__global__ void k_cell_assign(const double* __restrict__ q, int64_t n, DevGrid g, int* __restrict__ cell_of,
+__global__ void k_cell_assign(const double* __restrict__ q, int64_t n, DevGrid g0, Batch B, int* __restrict__ cell_of,
                               int* __restrict__ cell_slot, int* __restrict__ cell_count, int* __restrict__ abs_cell,
                               float4* __restrict__ qf) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const DevGrid g = site_grid(g0, B, i);
+  const int base = B.nsys ? B.cell_base[B.sys_of[i]] : 0;
   qf[i] = make_float4((float)q[i], (float)q[n + i], (float)q[2 * n + i], 0.f);
   int c3[3];
 #pragma unroll
@@ -37,7 +39,7 @@ __global__ void k_cell_assign(const double* __restrict__ q, int64_t n, DevGrid g
     c3[a] = c;
     abs_cell[a * n + i] = (int)w * g.nc[a] + c;
   }
-  int cell = (c3[0] * g.nc[1] + c3[1]) * g.nc[2] + c3[2];
+  int cell = base + (c3[0] * g.nc[1] + c3[1]) * g.nc[2] + c3[2];
   cell_of[i] = cell;
   cell_slot[i] = atomicAdd(&cell_count[cell], 1);
 }
@@ -125,7 +127,7 @@ __device__ __forceinline__ int decide_f(float r2f, float cut2f, float band) {
 }
 
 __global__ void k_nbr_count(const double* __restrict__ q, const float4* __restrict__ qf,
-                            const uint8_t* __restrict__ sub, uint32_t mobile_mask, int64_t n, DevGrid g,
+                            const uint8_t* __restrict__ sub, uint32_t mobile_mask, int64_t n, DevGrid g0, Batch B,
                             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                             const int* __restrict__ cell_sites, double rl2, double rb2, float band,
                             int* __restrict__ nb_cnt, int* __restrict__ bd_cnt, int* __restrict__ max_row) {
@@ -137,12 +139,14 @@ __global__ void k_nbr_count(const double* __restrict__ q, const float4* __restri
   const float rl2f = (float)rl2, rb2f = (float)rb2;
   int si = sub ? sub[i] : 0;
   bool mob = (mobile_mask >> si) & 1u;
-  Stencil st = make_stencil(cell_of[i], g);
+  const DevGrid g = site_grid(g0, B, i);
+  const int base = B.nsys ? B.cell_base[B.sys_of[i]] : 0;
+  Stencil st = make_stencil(cell_of[i] - base, g);
   int cnt = 0, bcnt = 0;
   for (int ax = 0; ax < st.cnt[0]; ++ax)
     for (int ay = 0; ay < st.cnt[1]; ++ay)
       for (int az = 0; az < st.cnt[2]; ++az) {
-        int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+        int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
         int beg = cell_start[c], end = cell_start[c + 1];
         for (int t0 = beg; t0 < end; t0 += 32) {
           int t = t0 + lane;
@@ -175,7 +179,7 @@ __global__ void k_nbr_count(const double* __restrict__ q, const float4* __restri
 }
 
 __global__ void k_nbr_fill(const double* __restrict__ q, const float4* __restrict__ qf,
-                           const uint8_t* __restrict__ sub, uint32_t mobile_mask, int64_t n, DevGrid g,
+                           const uint8_t* __restrict__ sub, uint32_t mobile_mask, int64_t n, DevGrid g0, Batch B,
                            const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                            const int* __restrict__ cell_sites, const int* __restrict__ abs_cell, double rl2,
                            double rb2, float band, const int* __restrict__ nb_off, uint32_t* __restrict__ nb_ent,
@@ -194,12 +198,14 @@ __global__ void k_nbr_fill(const double* __restrict__ q, const float4* __restric
   int Ai[3] = {abs_cell[i], abs_cell[n + i], abs_cell[2 * n + i]};
   int si = sub ? sub[i] : 0;
   bool mob = (mobile_mask >> si) & 1u;
-  Stencil st = make_stencil(cell_of[i], g);
+  const DevGrid g = site_grid(g0, B, i);
+  const int base = B.nsys ? B.cell_base[B.sys_of[i]] : 0;
+  Stencil st = make_stencil(cell_of[i] - base, g);
   int m = 0;
   for (int ax = 0; ax < st.cnt[0]; ++ax)
     for (int ay = 0; ay < st.cnt[1]; ++ay)
       for (int az = 0; az < st.cnt[2]; ++az) {
-        int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+        int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
         int beg = cell_start[c], end = cell_start[c + 1];
         for (int t0 = beg; t0 < end; t0 += 32) {
           int t = t0 + lane;
@@ -276,17 +282,17 @@ struct CellStage {
   int ncand;
 };
 
-__device__ __forceinline__ CellStage stage_cell(int cell, const DevGrid& g, const int* __restrict__ cell_start,
+__device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGrid& g, const int* __restrict__ cell_start,
                                                 const int* __restrict__ cell_sites, const float4* __restrict__ qf,
                                                 float4* cq, int* cj, int* s_off, int* s_beg, int cand_cap,
                                                 int* __restrict__ flags) {
   if (threadIdx.x == 0) {
-    const Stencil st = make_stencil(cell, g);
+    const Stencil st = make_stencil(cell - base, g);
     int k = 0, tot = 0;
     for (int ax = 0; ax < st.cnt[0]; ++ax)
       for (int ay = 0; ay < st.cnt[1]; ++ay)
         for (int az = 0; az < st.cnt[2]; ++az) {
-          const int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+          const int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
           s_beg[k] = cell_start[c];
           s_off[k] = tot;
           tot += cell_start[c + 1] - cell_start[c];
@@ -348,7 +354,7 @@ __device__ __forceinline__ CandResult test_cand(int64_t i, const double qi[3], c
 
 __global__ void __launch_bounds__(kCellThreads) k_cell_count(
     const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
-    int64_t n, DevGrid g, const int* __restrict__ cell_start, const int* __restrict__ cell_sites, double rl2,
+    int64_t n, DevGrid g0, Batch B, const int* __restrict__ cell_start, const int* __restrict__ cell_sites, double rl2,
     double rb2, float band, int cand_cap, int* __restrict__ nb_cnt, int* __restrict__ bd_cnt,
     int* __restrict__ max_row, int* __restrict__ flags) {
   extern __shared__ unsigned char smem[];
@@ -358,7 +364,10 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
   const int cell = blockIdx.x;
   const int hbeg = cell_start[cell], hend = cell_start[cell + 1];
   if (hbeg == hend) return;  // uniform over the block
-  const CellStage cs = stage_cell(cell, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
+  const int sys = B.nsys ? B.cell_sys[cell] : 0;
+  const DevGrid g = B.nsys ? B.grids[sys] : g0;
+  const int base = B.nsys ? B.cell_base[sys] : 0;
+  const CellStage cs = stage_cell(cell, base, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float rl2f = (float)rl2, rb2f = (float)rb2;
   for (int h = hbeg + warp; h < hend; h += nwarps) {
@@ -385,7 +394,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
 
 __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
-    int64_t n, DevGrid g, const int* __restrict__ cell_start, const int* __restrict__ cell_sites,
+    int64_t n, DevGrid g0, Batch B, const int* __restrict__ cell_start, const int* __restrict__ cell_sites,
     const int* __restrict__ abs_cell, double rl2, double rb2, float band, int cand_cap,
     const int* __restrict__ nb_off, uint32_t* __restrict__ nb_ent, const int* __restrict__ bd_off,
     int* __restrict__ bd_idx, int max_row, int* __restrict__ flags) {
@@ -396,7 +405,10 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   const int cell = blockIdx.x;
   const int hbeg = cell_start[cell], hend = cell_start[cell + 1];
   if (hbeg == hend) return;
-  const CellStage cs = stage_cell(cell, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
+  const int sys = B.nsys ? B.cell_sys[cell] : 0;
+  const DevGrid g = B.nsys ? B.grids[sys] : g0;
+  const int base = B.nsys ? B.cell_base[sys] : 0;
+  const CellStage cs = stage_cell(cell, base, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint32_t* buf = reinterpret_cast<uint32_t*>(cj + cand_cap) + (size_t)warp * max_row;
   uint8_t* isb = reinterpret_cast<uint8_t*>(reinterpret_cast<uint32_t*>(cj + cand_cap) + (size_t)nwarps * max_row) +
@@ -458,15 +470,19 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
 }
 
 // Largest number of candidates of any cell's stencil.
-__global__ void k_cand_max(int64_t ncell, DevGrid g, const int* __restrict__ cell_start, int* __restrict__ out) {
+__global__ void k_cand_max(int64_t ncell, DevGrid g0, Batch B, const int* __restrict__ cell_start,
+                           int* __restrict__ out) {
   const int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c0 >= ncell) return;
-  const Stencil st = make_stencil((int)c0, g);
+  const int sys = B.nsys ? B.cell_sys[c0] : 0;
+  const DevGrid g = B.nsys ? B.grids[sys] : g0;
+  const int base = B.nsys ? B.cell_base[sys] : 0;
+  const Stencil st = make_stencil((int)c0 - base, g);
   int tot = 0;
   for (int ax = 0; ax < st.cnt[0]; ++ax)
     for (int ay = 0; ay < st.cnt[1]; ++ay)
       for (int az = 0; az < st.cnt[2]; ++az) {
-        const int c = (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+        const int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
         tot += cell_start[c + 1] - cell_start[c];
       }
   atomicMax(out, tot);
@@ -559,12 +575,26 @@ __global__ void k_site_max(const double* __restrict__ sigma, const double* __res
 
 inline unsigned grid_for(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
 
+// segment of each index by binary search over the segment starts (empty
+// segments share their start with the next one and are skipped)
+__global__ void k_segment_ids(const int* __restrict__ base, int nseg, int64_t count, int* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int lo = 0, hi = nseg - 1;  // invariant: base[lo] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)base[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  out[t] = lo;
+}
+
 }  // namespace
 
-cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, int* cell_of, int* cell_slot,
-                               int* cell_count, int* abs_cell, float4* qf, cudaStream_t s) {
+cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, const Batch& B, int* cell_of,
+                               int* cell_slot, int* cell_count, int* abs_cell, float4* qf, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_cell_assign<<<grid_for(n, 256), 256, 0, s>>>(q, n, g, cell_of, cell_slot, cell_count, abs_cell, qf);
+  k_cell_assign<<<grid_for(n, 256), 256, 0, s>>>(q, n, g, B, cell_of, cell_slot, cell_count, abs_cell, qf);
   return cudaGetLastError();
 }
 
@@ -576,17 +606,17 @@ cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slo
 }
 
 cudaError_t launch_nbr_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                             const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                             const DevGrid& g, const Batch& B, const int* cell_of, const int* cell_start, const int* cell_sites,
                              double rl2, double rb2, float band, int* nb_cnt, int* bd_cnt, int* max_row,
                              cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_nbr_count<<<grid_for(n * 32, 256), 256, 0, s>>>(q, qf, sub, mobile_mask, n, g, cell_of, cell_start, cell_sites,
+  k_nbr_count<<<grid_for(n * 32, 256), 256, 0, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_of, cell_start, cell_sites,
                                                     rl2, rb2, band, nb_cnt, bd_cnt, max_row);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                            const DevGrid& g, const int* cell_of, const int* cell_start, const int* cell_sites,
+                            const DevGrid& g, const Batch& B, const int* cell_of, const int* cell_start, const int* cell_sites,
                             const int* abs_cell, double rl2, double rb2, float band, const int* nb_off,
                             uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
@@ -599,15 +629,16 @@ cudaError_t launch_nbr_fill(const double* q, const float4* qf, const uint8_t* su
   cudaError_t e = cudaFuncSetAttribute(k_nbr_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
   int threads = warps * 32;
-  k_nbr_fill<<<grid_for(n * 32, threads), threads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_of, cell_start,
+  k_nbr_fill<<<grid_for(n * 32, threads), threads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_of, cell_start,
                                                              cell_sites, abs_cell, rl2, rb2, band, nb_off, nb_ent,
                                                              bd_off, bd_idx, max_row);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const int* cell_start, int* out, cudaStream_t s) {
+cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start, int* out,
+                            cudaStream_t s) {
   if (ncell == 0) return cudaSuccess;
-  k_cand_max<<<grid_for(ncell, 256), 256, 0, s>>>(ncell, g, cell_start, out);
+  k_cand_max<<<grid_for(ncell, 256), 256, 0, s>>>(ncell, g, B, cell_start, out);
   return cudaGetLastError();
 }
 
@@ -618,20 +649,20 @@ size_t cell_stage_bytes(int cand_cap, int max_row, bool fill) {
 }
 
 cudaError_t launch_cell_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                              int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                              int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start, const int* cell_sites,
                               double rl2, double rb2, float band, int cand_cap, int* nb_cnt, int* bd_cnt,
                               int* max_row, int* flags, cudaStream_t s) {
   if (n == 0 || ncell == 0) return cudaSuccess;
   const size_t shm = cell_stage_bytes(cand_cap, 0, false);
   cudaError_t e = cudaFuncSetAttribute(k_cell_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
-  k_cell_count<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_start, cell_sites, rl2,
+  k_cell_count<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start, cell_sites, rl2,
                                                           rb2, band, cand_cap, nb_cnt, bd_cnt, max_row, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
-                             int64_t ncell, const DevGrid& g, const int* cell_start, const int* cell_sites,
+                             int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start, const int* cell_sites,
                              const int* abs_cell, double rl2, double rb2, float band, int cand_cap,
                              const int* nb_off, uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row,
                              int* flags, cudaStream_t s) {
@@ -640,7 +671,7 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
   const size_t shm = cell_stage_bytes(cand_cap, max_row, true);
   cudaError_t e = cudaFuncSetAttribute(k_cell_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
-  k_cell_fill<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, cell_start, cell_sites,
+  k_cell_fill<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start, cell_sites,
                                                          abs_cell, rl2, rb2, band, cand_cap, nb_off, nb_ent, bd_off,
                                                          bd_idx, max_row, flags);
   return cudaGetLastError();
@@ -670,6 +701,13 @@ cudaError_t launch_site_max(const double* sigma, const double* q, int64_t n, uns
                             cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_site_max<<<grid_for(n, 256), 256, 0, s>>>(sigma, q, n, out_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_ids(const int* base, int nseg, int64_t count, int* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (nseg <= 0) return cudaErrorInvalidValue;
+  k_segment_ids<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(base, nseg, count, out);
   return cudaGetLastError();
 }
 

@@ -80,7 +80,7 @@ extern "C" MXE_API mxe_status mxe_diffuse_step_noalloc(int64_t n, int32_t n_spec
   if (e == cudaSuccess)
     e = launch_flux(x_dev, T_dev, mu_ex_dev, bond_offsets_dev, bond_idx_dev, n, n_species, dt, nu0, Qm, factors,
                     x_new, step_flags, st);
-  if (e == cudaSuccess) e = launch_commit_x(x_dev, x_new, (int64_t)n_species * n, step_flags, sticky, st);
+  if (e == cudaSuccess) e = launch_commit_x(x_dev, x_new, (int64_t)n_species * n, step_flags, sticky, nullptr, st);
   int flags_h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags_h, step_flags, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

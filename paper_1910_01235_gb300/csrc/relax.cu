@@ -148,48 +148,275 @@ __global__ void __launch_bounds__(256) k_fire_logic(const double* __restrict__ p
   C.smax_bits = 0ull;
 }
 
+// One FIRE update of site i with the given scalars; returns |q - q_build|^2 and sigma.
+__device__ __forceinline__ void fire_site(double* __restrict__ q, double* __restrict__ sigma, double* __restrict__ vq,
+                                          double* __restrict__ vs, const double* __restrict__ gq,
+                                          const double* __restrict__ gs, const double* __restrict__ q_build,
+                                          const int* __restrict__ abs_cell, int64_t n, int64_t i, const DevGrid& g,
+                                          float4* __restrict__ pos32, double dt, double keep, double mix, double oma,
+                                          double lo, double hi, double& disp2, double& sg) {
+  double p[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double f = -gq[c * n + i];
+    double v = keep * vq[c * n + i] + dt * f;
+    v = oma * v + mix * f;
+    vq[c * n + i] = v;
+    const double qn = q[c * n + i] + dt * v;
+    q[c * n + i] = qn;
+    const double dq = qn - q_build[c * n + i];
+    disp2 += dq * dq;
+    p[c] = (float)(qn - (double)abs_cell[c * n + i] * g.h[c]);
+  }
+  const double f = proj_fsig(gs[i], sigma[i], lo, hi);
+  double v = keep * vs[i] + dt * f;
+  v = oma * v + mix * f;
+  sg = sigma[i] + dt * v;
+  if (sg < lo || sg > hi) {
+    sg = sg < lo ? lo : hi;
+    v = 0.0;
+  }
+  vs[i] = v;
+  sigma[i] = sg;
+  if (pos32) pos32[i] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)sg);
+}
+
 __global__ void __launch_bounds__(256) k_fire_update(double* __restrict__ q, double* __restrict__ sigma,
                                                      double* __restrict__ vq, double* __restrict__ vs,
                                                      const double* __restrict__ gq, const double* __restrict__ gs,
                                                      const double* __restrict__ q_build,
-                                                     const int* __restrict__ abs_cell, int64_t n, DevGrid g,
-                                                     float4* __restrict__ pos32, Ctrl* __restrict__ ctrl) {
+                                                     const int* __restrict__ abs_cell, int64_t n, DevGrid g0,
+                                                     Batch B, float4* __restrict__ pos32, Ctrl* __restrict__ ctrl) {
   if (ctrl->halted) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double dt = ctrl->dt, keep = ctrl->keep, mix = ctrl->mix, oma = ctrl->one_minus_alpha;
   double disp2 = 0.0, sg = 0.0;
   if (i < n) {
-    double p[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double f = -gq[c * n + i];
-      double v = keep * vq[c * n + i] + dt * f;
-      v = oma * v + mix * f;
-      vq[c * n + i] = v;
-      const double qn = q[c * n + i] + dt * v;
-      q[c * n + i] = qn;
-      const double dq = qn - q_build[c * n + i];
-      disp2 += dq * dq;
-      p[c] = (float)(qn - (double)abs_cell[c * n + i] * g.h[c]);
-    }
-    const double lo = ctrl->sigma_lo, hi = ctrl->sigma_hi;
-    const double f = proj_fsig(gs[i], sigma[i], lo, hi);
-    double v = keep * vs[i] + dt * f;
-    v = oma * v + mix * f;
-    sg = sigma[i] + dt * v;
-    if (sg < lo || sg > hi) {
-      sg = sg < lo ? lo : hi;
-      v = 0.0;
-    }
-    vs[i] = v;
-    sigma[i] = sg;
-    if (pos32) pos32[i] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)sg);
+    const DevGrid g = site_grid(g0, B, i);
+    fire_site(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, i, g, pos32, dt, keep, mix, oma, ctrl->sigma_lo,
+              ctrl->sigma_hi, disp2, sg);
   }
   atomic_max_nonneg(&ctrl->disp2_bits, disp2);
   atomic_max_nonneg(&ctrl->smax_bits, sg);
 }
 
+// ---------------------------------------------------------------- batches
+__global__ void __launch_bounds__(256) k_fire_seg_reduce(const double* __restrict__ gq,
+                                                         const double* __restrict__ gs,
+                                                         const double* __restrict__ sigma,
+                                                         const double* __restrict__ vq,
+                                                         const double* __restrict__ vs, int64_t n, Batch B,
+                                                         SysFire* __restrict__ sf, Ctrl* __restrict__ ctrl,
+                                                         int* __restrict__ flags) {
+  if (ctrl->halted) return;
+  const int sys = blockIdx.x;
+  if (sf[sys].halted) return;
+  __shared__ double sh[4][256];
+  const int tid = threadIdx.x;
+  const double lo = ctrl->sigma_lo, hi = ctrl->sigma_hi;
+  double P = 0.0, vv = 0.0, ff = 0.0, fm = 0.0;
+  bool finite = true;
+  for (int64_t i = B.sys_off[sys] + tid; i < B.sys_off[sys + 1]; i += 256) {
+    const double g0 = gq[i], g1 = gq[n + i], g2 = gq[2 * n + i];
+    const double f3 = proj_fsig(gs[i], sigma[i], lo, hi);
+    const double v0 = vq[i], v1 = vq[n + i], v2 = vq[2 * n + i], v3 = vs[i];
+    P += -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
+    vv += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
+    ff += g0 * g0 + g1 * g1 + g2 * g2 + f3 * f3;
+    fm = fmax(fm, fmax(sqrt(g0 * g0 + g1 * g1 + g2 * g2), fabs(f3)));
+    finite = finite && isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs[i]);
+  }
+  if (!finite) atomicOr(flags, kFlagNonfinite);
+  sh[0][tid] = P;
+  sh[1][tid] = vv;
+  sh[2][tid] = ff;
+  sh[3][tid] = fm;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) {
+      for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
+      sh[3][tid] = fmax(sh[3][tid], sh[3][tid + w]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    sf[sys].P = sh[0][0];
+    sf[sys].vv = sh[1][0];
+    sf[sys].ff = sh[2][0];
+    sf[sys].fmax = sh[3][0];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fire_seg_logic(SysFire* __restrict__ sf, int nsys, Ctrl* __restrict__ ctrl,
+                                                        const int* __restrict__ flags) {
+  if (ctrl->halted) return;
+  __shared__ int active[256];
+  const Ctrl& C = *ctrl;
+  if (*flags & (kFlagGeometry | kFlagNonfinite)) {
+    if (threadIdx.x == 0) {
+      ctrl->halted = 1;
+      ctrl->reason = kReasonError;
+    }
+    return;
+  }
+  int act = 0;
+  for (int s = threadIdx.x; s < nsys; s += 256) {
+    SysFire& F = sf[s];
+    if (F.halted) continue;
+    if (F.fmax <= C.ftol) {
+      F.halted = 1;
+      F.reason = kReasonConverged;
+      continue;
+    }
+    if (F.iter >= C.max_iter) {
+      F.halted = 1;
+      F.reason = kReasonMaxIter;
+      continue;
+    }
+    double keep = 1.0;
+    if (F.iter > 0) {
+      if (F.P > 0.0) {
+        F.n_pos += 1;
+        if (F.n_pos > C.n_min) {
+          F.dt = fmin(F.dt * C.f_inc, C.dt_max);
+          F.alpha = F.alpha * C.f_alpha;
+        }
+      } else {
+        F.n_pos = 0;
+        F.dt = F.dt * C.f_dec;
+        F.alpha = C.alpha0;
+        keep = 0.0;
+      }
+    }
+    const double dt = F.dt;
+    const double v2 = keep * (F.vv + 2.0 * dt * F.P) + dt * dt * F.ff;
+    const double fnorm = sqrt(F.ff);
+    F.keep = keep;
+    F.mix = fnorm > 0.0 ? F.alpha * sqrt(fmax(v2, 0.0)) / fnorm : 0.0;
+    F.one_minus_alpha = 1.0 - F.alpha;
+    F.iter += 1;
+    act += 1;
+  }
+  active[threadIdx.x] = act;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) active[threadIdx.x] += active[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Ctrl& G = *ctrl;
+    if (active[0] == 0) {
+      G.halted = 1;  // the maxima of the last update stay for the skin test
+      G.reason = kReasonAllDone;
+    } else {
+      G.iter += 1;  // updates of the longest-running system
+      G.disp2_bits = 0ull;
+      G.smax_bits = 0ull;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fire_seg_update(double* __restrict__ q, double* __restrict__ sigma,
+                                                         double* __restrict__ vq, double* __restrict__ vs,
+                                                         const double* __restrict__ gq,
+                                                         const double* __restrict__ gs,
+                                                         const double* __restrict__ q_build,
+                                                         const int* __restrict__ abs_cell, int64_t n, DevGrid g0,
+                                                         Batch B, const SysFire* __restrict__ sf,
+                                                         float4* __restrict__ pos32, Ctrl* __restrict__ ctrl) {
+  if (ctrl->halted) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double disp2 = 0.0, sg = 0.0;
+  if (i < n) {
+    const SysFire& F = sf[B.sys_of[i]];
+    if (!F.halted) {
+      const DevGrid g = site_grid(g0, B, i);
+      fire_site(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, i, g, pos32, F.dt, F.keep, F.mix, F.one_minus_alpha,
+                ctrl->sigma_lo, ctrl->sigma_hi, disp2, sg);
+    } else {  // a stopped system still counts in the skin test
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double dq = q[c * n + i] - q_build[c * n + i];
+        disp2 += dq * dq;
+      }
+      sg = sigma[i];
+    }
+  }
+  atomic_max_nonneg(&ctrl->disp2_bits, disp2);
+  atomic_max_nonneg(&ctrl->smax_bits, sg);
+}
+
+__global__ void k_fire_seg_init(SysFire* __restrict__ sf, int nsys, double dt0, double alpha0,
+                                const Ctrl* __restrict__ gate) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || (gate && gate->halted)) return;
+  SysFire F;
+  F.halted = 0;
+  F.reason = kReasonNone;
+  F.iter = 0;
+  F.n_pos = 0;
+  F.dt = dt0;
+  F.alpha = alpha0;
+  F.keep = F.mix = F.one_minus_alpha = F.fmax = 0.0;
+  F.P = F.vv = F.ff = 0.0;
+  sf[s] = F;
+}
+
+// ------------------------------------------------------- staggered steps in a graph
+// A stop for a rebuild or an error stays until the host clears it: every
+// later kernel of the captured steps then returns at once.
+__device__ __forceinline__ bool run_stopped(const Ctrl& C) {
+  return C.halted && (C.reason == kReasonRebuild || C.reason == kReasonError);
+}
+
+__global__ void k_step_begin(Ctrl* __restrict__ ctrl, double dt0, double alpha0) {
+  Ctrl& C = *ctrl;
+  if (run_stopped(C)) return;
+  C.halted = 0;
+  C.reason = kReasonNone;
+  C.iter = 0;
+  C.n_pos = 0;
+  C.dt = dt0;
+  C.alpha = alpha0;
+  C.fmax_bits = 0ull;
+  C.phase = 0;
+}
+
+__global__ void k_step_end(Ctrl* __restrict__ ctrl) {
+  Ctrl& C = *ctrl;
+  if (run_stopped(C)) return;
+  C.steps += 1;
+  C.phase = 0;
+}
+
+__global__ void __launch_bounds__(256) k_fire_zero_v(double* __restrict__ vq, double* __restrict__ vs, int64_t n,
+                                                     const Ctrl* __restrict__ gate) {
+  if (gate->halted) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  vq[i] = 0.0;
+  vq[n + i] = 0.0;
+  vq[2 * n + i] = 0.0;
+  vs[i] = 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_step_begin(Ctrl* ctrl, double dt0, double alpha0, cudaStream_t s) {
+  k_step_begin<<<1, 1, 0, s>>>(ctrl, dt0, alpha0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_end(Ctrl* ctrl, cudaStream_t s) {
+  k_step_end<<<1, 1, 0, s>>>(ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fire_zero_v(double* vq, double* vs, int64_t n, const Ctrl* gate, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_fire_zero_v<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vq, vs, n, gate);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
                                const double* vs, int64_t n, double* partials, Ctrl* ctrl, int* flags, cudaStream_t s) {
@@ -208,10 +435,39 @@ cudaError_t launch_fire_logic(const double* partials, int64_t n, Ctrl* ctrl, int
 
 cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
                                const double* gs, const double* q_build, const int* abs_cell, int64_t n,
-                               const DevGrid& g, float4* pos32, Ctrl* ctrl, cudaStream_t s) {
+                               const DevGrid& g, const Batch& B, float4* pos32, Ctrl* ctrl, cudaStream_t s) {
   unsigned blocks = (unsigned)((n + 255) / 256);
   if (blocks == 0) blocks = 1;
-  k_fire_update<<<blocks, 256, 0, s>>>(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, g, pos32, ctrl);
+  k_fire_update<<<blocks, 256, 0, s>>>(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, g, B, pos32, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fire_seg_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
+                                   const double* vs, int64_t n, const Batch& B, SysFire* sf, Ctrl* ctrl, int* flags,
+                                   cudaStream_t s) {
+  if (B.nsys <= 0) return cudaErrorInvalidValue;
+  k_fire_seg_reduce<<<(unsigned)B.nsys, 256, 0, s>>>(gq, gs, sigma, vq, vs, n, B, sf, ctrl, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fire_seg_logic(SysFire* sf, int nsys, Ctrl* ctrl, const int* flags, cudaStream_t s) {
+  k_fire_seg_logic<<<1, 256, 0, s>>>(sf, nsys, ctrl, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fire_seg_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
+                                   const double* gs, const double* q_build, const int* abs_cell, int64_t n,
+                                   const DevGrid& g, const Batch& B, const SysFire* sf, float4* pos32, Ctrl* ctrl,
+                                   cudaStream_t s) {
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (blocks == 0) blocks = 1;
+  k_fire_seg_update<<<blocks, 256, 0, s>>>(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, g, B, sf, pos32, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fire_seg_init(SysFire* sf, int nsys, double dt0, double alpha0, const Ctrl* gate, cudaStream_t s) {
+  if (nsys <= 0) return cudaSuccess;
+  k_fire_seg_init<<<(unsigned)((nsys + 255) / 256), 256, 0, s>>>(sf, nsys, dt0, alpha0, gate);
   return cudaGetLastError();
 }
 

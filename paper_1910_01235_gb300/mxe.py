@@ -52,10 +52,11 @@ class mxe_fire_params(C.Structure):
                 ("sigma_max", C.c_double), ("n_min", C.c_int32), ("check_every", C.c_int32)]
 
 
-EXPORTS = ["mxe_status_string", "mxe_create", "mxe_destroy", "mxe_build_neighbors", "mxe_export_neighbors",
-           "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async", "mxe_sync_status",
-           "mxe_relax", "mxe_diffuse_step", "mxe_diffuse_step_async", "mxe_diffuse_step_noalloc",
-           "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs"]
+EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy", "mxe_build_neighbors",
+           "mxe_export_neighbors", "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async",
+           "mxe_sync_status", "mxe_relax", "mxe_relax_info", "mxe_diffuse_step", "mxe_diffuse_step_async",
+           "mxe_diffuse_step_noalloc", "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs",
+           "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape"]
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
 
@@ -82,6 +83,12 @@ def lib():
             L.mxe_status_string.restype = C.c_char_p
             L.mxe_status_string.argtypes = [C.c_int]
             L.mxe_create.argtypes = [C.POINTER(C.c_void_p), p, p, i64, C.c_int, p]
+            L.mxe_create_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, p, p, p, i64, C.c_int, p]
+            L.mxe_set_dt_scale.argtypes = [p, p]
+            L.mxe_relax_info.argtypes = [p, C.c_int32, p, p, p]
+            L.mxe_run_staggered.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.POINTER(C.c_int32)]
+            L.mxe_autotune.argtypes = [p, p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+            L.mxe_set_pass_shape.argtypes = [p, C.c_int32, C.c_int32]
             L.mxe_destroy.argtypes = [p]
             L.mxe_build_neighbors.argtypes = [p, p, d, d, C.POINTER(i64), C.POINTER(d)]
             L.mxe_export_neighbors.argtypes = [p, p, p]
@@ -114,8 +121,53 @@ def mxe_create(box: mxe_box, pot: mxe_potential, n: int, precision: int, stream:
     return st, ctx
 
 
+def mxe_create_batch(boxes, offsets, pot: mxe_potential, precision: int, stream: int):
+    """boxes: sequence of 3-vectors; offsets: n_systems + 1 site offsets."""
+    m = len(boxes)
+    barr = (mxe_box * max(m, 1))()
+    for b, L in enumerate(boxes):
+        barr[b] = mxe_box((C.c_double * 3)(*[float(v) for v in L]))
+    off = (C.c_int64 * (m + 1))(*[int(v) for v in offsets])
+    ctx = C.c_void_p()
+    st = lib().mxe_create_batch(C.byref(ctx), m, barr, off, C.byref(pot), int(offsets[-1]), int(precision),
+                                C.c_void_p(stream))
+    return st, ctx
+
+
 def mxe_destroy(ctx):
     return lib().mxe_destroy(ctx)
+
+
+def mxe_set_dt_scale(ctx, scale=None):
+    if scale is None:
+        return lib().mxe_set_dt_scale(ctx, None)
+    arr = (C.c_double * len(scale))(*[float(v) for v in scale])
+    return lib().mxe_set_dt_scale(ctx, arr)
+
+
+def mxe_relax_info(ctx, m):
+    it = (C.c_int32 * m)()
+    fm = (C.c_double * m)()
+    cv = (C.c_int32 * m)()
+    st = lib().mxe_relax_info(ctx, m, it, fm, cv)
+    return st, np.array(it[:], np.int32), np.array(fm[:]), np.array(cv[:], bool)
+
+
+def mxe_run_staggered(ctx, state, n_steps, dt, nu0, Qm, ftol, max_iter, fire: mxe_fire_params | None = None):
+    done = C.c_int32(0)
+    st = lib().mxe_run_staggered(ctx, C.byref(state), int(n_steps), float(dt), float(nu0), float(Qm), float(ftol),
+                                 int(max_iter), C.byref(fire) if fire is not None else None, C.byref(done))
+    return st, done.value
+
+
+def mxe_autotune(ctx, state):
+    lanes, threads = C.c_int32(0), C.c_int32(0)
+    st = lib().mxe_autotune(ctx, C.byref(state), C.byref(lanes), C.byref(threads))
+    return st, lanes.value, threads.value
+
+
+def mxe_set_pass_shape(ctx, lanes, threads):
+    return lib().mxe_set_pass_shape(ctx, int(lanes), int(threads))
 
 
 def mxe_build_neighbors(ctx, state: mxe_state, skin: float, r_bond: float):
@@ -236,17 +288,20 @@ class MxeSystem:
         self.mu_ex = torch.zeros((self.S, self.n), dtype=torch.float64, device=dev)
         self.mu = torch.zeros((self.S, self.n), dtype=torch.float64, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
-        self.box = mxe_box((C.c_double * 3)(*[float(v) for v in sys.L]))
         self.pot = make_potential(sys.pot)
         with torch.cuda.device(dev):
-            st, self.ctx = mxe_create(self.box, self.pot, self.n, self.precision, self.stream.cuda_stream)
-        if st != OK:
-            raise MxeError(st, "mxe_create")
+            self._create()
         self.skin = skin
         # bonds: nearest neighbours of the FCC sublattice (a/sqrt2), cut halfway to the second shell (a)
         self.r_bond = r_bond if r_bond is not None else 0.5 * (sys.a / np.sqrt(2.0) + sys.a)
         self.state = mxe_state()
         self._refresh_state()
+
+    def _create(self):
+        self.box = mxe_box((C.c_double * 3)(*[float(v) for v in self.sys.L]))
+        st, self.ctx = mxe_create(self.box, self.pot, self.n, self.precision, self.stream.cuda_stream)
+        if st != OK:
+            raise MxeError(st, "mxe_create")
 
     def _refresh_state(self):
         s = self.state
@@ -329,12 +384,80 @@ class MxeSystem:
             ptrs += [_ptr(m), _ptr(v)]
         self._check(mxe_set_reservoirs(self.ctx, *ptrs), "mxe_set_reservoirs")
 
+    def relax_info(self):
+        """Per-system (iterations, fmax, converged) of the last relaxation."""
+        st, it, fm, cv = mxe_relax_info(self.ctx, getattr(self, "n_systems", 1))
+        self._check(st, "mxe_relax_info")
+        return it, fm, cv
+
+    def run_staggered(self, n_steps, dt, ftol, max_iter, fire=None, nu0=None, Qm=None, allow=()):
+        """n_steps staggered steps replayed from one captured CUDA graph."""
+        st, done = mxe_run_staggered(self.ctx, self.state, n_steps, dt, self.sys.nu0 if nu0 is None else nu0,
+                                     self.sys.Qm if Qm is None else Qm, ftol, max_iter, fire)
+        self._check(st, "mxe_run_staggered", allow)
+        return st, done
+
+    def autotune(self):
+        st, lanes, threads = mxe_autotune(self.ctx, self.state)
+        self._check(st, "mxe_autotune")
+        return lanes, threads
+
+    def set_pass_shape(self, lanes, threads):
+        self._check(mxe_set_pass_shape(self.ctx, lanes, threads), "mxe_set_pass_shape")
+
     def staggered_step(self, dt, ftol, max_iter, fire=None):
         """One step of the staggered scheme (Sec. 4): excess chemical potentials,
         one Euler step of x, then relaxation of (q, sigma) at fixed x."""
         self.free_energy_grad(with_mu=False)
         self.diffuse_step(dt, mu_ex=self.mu_ex)
         return self.relax(ftol, max_iter, fire)
+
+
+def concatenate(systems):
+    """One System holding `systems` site block after site block, plus the
+    site offsets (argument marshalling for a batched context).  The systems
+    must share the potential, the mobile sublattice mask, the lattice
+    parameter and nu0, Qm."""
+    first = systems[0]
+    for t in systems[1:]:
+        if (t.S != first.S or t.mobile_mask != first.mobile_mask or t.a != first.a or t.nu0 != first.nu0
+                or t.Qm != first.Qm):
+            raise ValueError("systems of one batch must share S, mobile_mask, a, nu0 and Qm")
+    offsets = np.zeros(len(systems) + 1, np.int64)
+    offsets[1:] = np.cumsum([t.n for t in systems])
+    merged = first.copy()
+    merged.name = f"batch_{len(systems)}"
+    merged.q = np.concatenate([t.q for t in systems], axis=1)
+    merged.sigma = np.concatenate([t.sigma for t in systems])
+    merged.x = np.concatenate([t.x for t in systems], axis=1)
+    merged.T = np.concatenate([t.T for t in systems])
+    merged.sublattice = np.concatenate([t.sublattice for t in systems])
+    return merged, offsets
+
+
+class MxeBatch(MxeSystem):
+    """A batched context: many independent systems in one set of device
+    arrays (sites concatenated; see mxe_create_batch).  F4 is [n_systems, 4];
+    `part(t, b)` slices a per-site tensor to system b."""
+
+    def __init__(self, systems, precision="fp64", device="cuda:0", stream=None, skin=0.2, r_bond=None):
+        self.systems = list(systems)
+        self.n_systems = len(self.systems)
+        merged, self.offsets = concatenate(self.systems)
+        super().__init__(merged, precision, device, stream, skin, r_bond)
+        self.F4 = self.torch.zeros((self.n_systems, 4), dtype=self.torch.float64, device=self.device)
+
+    def _create(self):
+        boxes = [t.L for t in self.systems]
+        st, self.ctx = mxe_create_batch(boxes, self.offsets, self.pot, self.precision, self.stream.cuda_stream)
+        if st != OK:
+            raise MxeError(st, "mxe_create_batch")
+
+    def part(self, t, b):
+        return t[..., int(self.offsets[b]):int(self.offsets[b + 1])]
+
+    def set_dt_scale(self, scale=None):
+        self._check(mxe_set_dt_scale(self.ctx, scale), "mxe_set_dt_scale")
 
 
 def _autograd_function():

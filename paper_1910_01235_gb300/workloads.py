@@ -259,6 +259,27 @@ def random_fractions(sys: System, lo=0.0, hi=1.0, vac_min=0.0, seed=SEED + 2) ->
     return s
 
 
+def config_ensemble(n_systems=512, cmin=4, cmax=16, a=3.6, sigma0=0.1, seed=SEED, pot=None) -> List[System]:
+    """Independent periodic single-species lattices: cells per side ~ U{cmin..cmax},
+    T ~ U(300, 1200) K, vacancy fraction c_v ~ U(1e-4, 1e-2) per system; per
+    site x_v = c_v * 2 u, u ~ U(0, 1), so the fluxes are non-trivial.
+    Draw order: all cell counts, all T, all c_v, then each system's u."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    cells = rng.integers(cmin, cmax + 1, n_systems)
+    Ts = rng.uniform(300.0, 1200.0, n_systems)
+    cvs = rng.uniform(1e-4, 1e-2, n_systems)
+    out = []
+    for s_ in range(n_systems):
+        c = int(cells[s_])
+        q = fcc_positions(c, c, c, a)
+        n = q.shape[1]
+        xv = cvs[s_] * 2.0 * rng.uniform(0.0, 1.0, n)
+        out.append(System(f"ensemble_{s_}_{c}c", np.full(3, c * a), q, np.full(n, sigma0), (1.0 - xv)[None, :].copy(),
+                          np.full(n, Ts[s_]), np.zeros(n, np.uint8), 1,
+                          pot if pot is not None else potential_single(), a, 1e13, 0.69))
+    return out
+
+
 CONFIGS = {
     "vacancy_500": lambda: config_vacancy_lattice(),
     "binary_256k": lambda: config_binary_alloy(),

@@ -41,3 +41,30 @@ def test_workloads_do_not_load_cuda():
             "print('mxe' in ' '.join(sys.modules))") % ROOT
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True).stdout
     assert out.strip() == "False"
+
+
+def test_create_batch_rejects_bad_arguments_before_touching_a_device():
+    """Argument checks of mxe_create_batch run on the host: every rejected
+    case returns MXE_ERR_ARG without a CUDA call (so this runs without a GPU)."""
+    import ctypes as C
+    from paper_1910_01235_gb300 import mxe, workloads as W
+    L = mxe.lib()
+    pot = mxe.make_potential(W.potential_single())
+    boxes = (mxe.mxe_box * 2)(mxe.mxe_box((C.c_double * 3)(20.0, 20.0, 20.0)),
+                              mxe.mxe_box((C.c_double * 3)(20.0, 20.0, 20.0)))
+    ctx = C.c_void_p()
+
+    def create(m, offsets, n, prec=mxe.FP64, bx=boxes):
+        off = (C.c_int64 * len(offsets))(*offsets)
+        return L.mxe_create_batch(C.byref(ctx), m, bx, off, C.byref(pot), n, prec, None)
+
+    assert create(2, [1, 2, 4], 4) == mxe.ERR_ARG       # first offset not 0
+    assert create(2, [0, 3, 2], 2) == mxe.ERR_ARG       # decreasing
+    assert create(2, [0, 2, 4], 5) == mxe.ERR_ARG       # last offset != n
+    assert create(-1, [0], 0) == mxe.ERR_ARG
+    assert create((1 << 20) + 1, [0, 0], 0) == mxe.ERR_ARG
+    assert create(2, [0, 2, 4], 4, prec=7) == mxe.ERR_ARG
+    bad = (mxe.mxe_box * 2)(mxe.mxe_box((C.c_double * 3)(20.0, 20.0, 20.0)),
+                            mxe.mxe_box((C.c_double * 3)(20.0, -1.0, 20.0)))
+    assert create(2, [0, 2, 4], 4, bx=bad) == mxe.ERR_ARG
+    assert ctx.value is None
