@@ -18,6 +18,17 @@ beside it.  Timed with CUDA events on the library's stream, L2 flushed
 --impl reference times the CPU oracle on the host cores (one neighbour build,
 one free-energy/gradient evaluation and one Euler step of the same state per
 step; value in the same unit).
+
+--workload ensemble measures the batched ensemble instead: 512 independent
+periodic single-species lattices (4..16 cells per side, 2.85 M sites in
+all, T ~ U(300, 1200) K, vacancy fraction ~ U(1e-4, 1e-2) per system) in one
+batched context, with the stable variant of the single-species potential
+(pair exponent 5, density exponent 3: the literal one collapses the lattice
+within ~40 steps of 10 FIRE iterations at fixed box, and its sigma has no
+minimum), relax+diffuse loop replayed from one captured CUDA graph
+(mxe_run_staggered), per-system Euler step = the system's stable step, pass
+shape chosen by the autotuner.  The working set (~1 GB) exceeds L2, so no
+flush is needed between steps.
 """
 from __future__ import annotations
 
@@ -152,6 +163,23 @@ def peak_fp32_ops(clock_mhz=2070.0):
     return 152 * 128 * clock_mhz * 1e6
 
 
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of this
+    workload, or None when the kernel sources changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_binary_alloy_256k.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256()
+    for f in d["source_files"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    k = d["kernels"].get(kernel)
+    if k is None or h.hexdigest()[:16] != d["source_digest"]:
+        return None
+    return k["dram_read"] + k["dram_write"]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -178,11 +206,21 @@ def run_ours(args):
     dt = sys0.dt_default()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
+    def set_shape(g):
+        """Pass shape: the autotuner's choice, or --pass-shape (lanes,threads)."""
+        if args.pass_shape:
+            lanes, threads = (int(v) for v in args.pass_shape.split(","))
+            g.set_pass_shape(lanes, threads)
+            return lanes, threads
+        return g.autotune()
+
     def timed_arm(prec, steps, warmup, launches_out=None, kernel_events=False):
         stream = torch.cuda.Stream(dev)
         with torch.cuda.stream(stream):
             g = M.MxeSystem(sys0, prec, device=dev, stream=stream)
         q0, s0, x0 = g.q.clone(), g.sigma.clone(), g.x.clone()
+        g.build_neighbors()
+        shape = set_shape(g)
         total_ms = 0.0
 
         def one_step():
@@ -225,7 +263,7 @@ def run_ours(args):
             M.mxe_timing_enable(g.ctx, False)
         npairs = g.n_pairs
         g.close()
-        return total_ms, kern, npairs
+        return total_ms, kern, npairs, shape
 
     main_prec = args.precision
     precs = [main_prec] + [p for p in ("fp64", "mixed", "ff") if p != main_prec and not args.quick]
@@ -237,10 +275,10 @@ def run_ours(args):
         sampler = ClockSampler(local) if p == main_prec else None
         if sampler:
             sampler.start()
-        ms, kern, npairs = timed_arm(p, steps, warm, kernel_events=True)
+        ms, kern, npairs, shape = timed_arm(p, steps, warm, kernel_events=True)
         if sampler:
             clocks = sampler.stop()
-        results[p] = (max_over_ranks(ms / steps, dist, dev), steps, warm, npairs, kern)
+        results[p] = (max_over_ranks(ms / steps, dist, dev), steps, warm, npairs, kern, shape)
 
     # e2e through the public API with host buffers
     def e2e(prec, steps):
@@ -252,6 +290,8 @@ def run_ours(args):
         out_F = torch.empty(4, dtype=torch.float64).pin_memory()
         with torch.cuda.stream(stream):
             g = M.MxeSystem(sys0, prec, device=dev, stream=stream)
+        g.build_neighbors()
+        set_shape(g)
         h2d = sum(t.numel() * t.element_size() for t in host.values()) + host_sub.numel()
         d2h = out_x.numel() * 8 + 32
         tot = 0.0
@@ -293,7 +333,7 @@ def run_ours(args):
         return
 
     evals_per_step = n * (K + 2)
-    ms, steps, warm, npairs, kern = results[main_prec]
+    ms, steps, warm, npairs, kern, shape = results[main_prec]
     value = aggregate_rate(evals_per_step, ms, world)
     dp = sys0.pot
     n_phi = 3 if dp.cross_geomean else 2
@@ -326,16 +366,20 @@ def run_ours(args):
         "data": "synthetic (seeded FCC binary alloy, random-init composition)",
         "config": {"workload": WORKLOAD, "sites": n, "species": 2, "fire_iters_per_step": K,
                    "evals_per_step": K + 2, "neighbor_pairs": npairs, "parallelism": f"replicas{world}",
-                   "l2": "flushed between steps (256 MB write)", "precision": main_prec},
+                   "l2": "flushed between steps (256 MB write)", "precision": main_prec,
+                   "pass_shape": {"lanes_per_site": shape[0], "threads_per_block": shape[1],
+                                  "chosen_by": "--pass-shape" if args.pass_shape else "autotuner"}},
         "diffusion_steps_per_s": world * 1e3 / ms,
         "precisions": {p: {"ms_per_step": r[0], "site_evals_per_s": aggregate_rate(evals_per_step, r[0], world),
-                           "steps": r[1]} for p, r in results.items()},
+                           "steps": r[1], "pass_shape": list(r[5])} for p, r in results.items()},
         "kernels": shares,
         "e2e": {"value": aggregate_rate(evals_per_step, e2e_ms, world), "unit": "site-evals/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 pipe)", "frac": (achieved / (peak_ops / 1e12)) if achieved else None,
-                     "traffic": None, "kernel_avg_ms": shares[dom]["avg_ms"] if dom else None,
+                     "traffic": ncu_traffic(dom) if (dom and main_prec == "ff" and world >= 1) else None,
+                     "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)",
+                     "kernel_avg_ms": shares[dom]["avg_ms"] if dom else None,
                      "ops_per_launch": ops_launch,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"},
         "clocks": clocks,
@@ -364,6 +408,88 @@ def cpu_baseline(sys0, max_seconds=30.0):
     return {"value": sys0.n / (t2 - t0), "unit": "site-evals/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"one neighbour build ({t1 - t0:.2f} s) + one free-energy/gradient evaluation "
                       f"({t2 - t1:.2f} s) of the full {sys0.n}-site state"}
+
+
+# ---------------------------------------------------------------- batched ensemble
+ENSEMBLE_STEPS = 50
+
+
+def run_ensemble(args):
+    import torch
+
+    from paper_1910_01235_gb300 import mxe as M
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    systems = W.config_ensemble(seed=W.SEED + rank, pot=W.potential_variant_s())
+    n = sum(t.n for t in systems)
+    K = args.fire_iters
+    steps_per_run = args.ensemble_steps
+    prec = args.precision
+    fire = M.make_fire(check_every=K + 1)
+    dts = np.array([t.dt_default() for t in systems])
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        g = M.MxeBatch(systems, prec, device=dev, stream=stream)
+    g.build_neighbors()
+    g.set_dt_scale(list(dts))
+    if args.pass_shape:
+        lanes, threads = (int(v) for v in args.pass_shape.split(","))
+        g.set_pass_shape(lanes, threads)
+    else:
+        lanes, threads = g.autotune()
+    q0, s0, x0 = g.q.clone(), g.sigma.clone(), g.x.clone()
+
+    def restore():
+        with torch.cuda.stream(stream):
+            g.q.copy_(q0)
+            g.sigma.copy_(s0)
+            g.x.copy_(x0)
+        stream.synchronize()
+        g.build_neighbors()
+
+    # warm-up: capture and replay
+    for _ in range(args.warmup):
+        restore()
+        st, done = g.run_staggered(2, 1.0, 0.0, K, fire)
+    times = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(max(1, args.steps // steps_per_run) if args.steps >= steps_per_run else 1):
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, done = g.run_staggered(steps_per_run, 1.0, 0.0, K, fire)
+        e1.record(stream)
+        stream.synchronize()
+        assert st == M.OK and done == steps_per_run, (st, done)
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    ms_run = float(np.median(times))
+    ms_step = ms_run / steps_per_run
+    moved = (g.x - x0).abs().max().item()
+    g.close()
+    evals_per_step = n * (K + 2)
+    line = {
+        "metric": METRIC, "value": aggregate_rate(evals_per_step, ms_step, world), "unit": "site-evals/s",
+        "n_gpus": world, "steps": steps_per_run * len(times), "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32 (f64 sums, f64 mu)", "ff": "f32 (float-float sums and mu)"}[prec],
+        "data": "synthetic (seeded ensemble of FCC single-species lattices with vacancies)",
+        "config": {"workload": "ensemble_512_systems", "systems": len(systems), "sites": n,
+                   "fire_iters_per_step": K, "evals_per_step": K + 2, "steps_per_graph_run": steps_per_run,
+                   "pass_shape": {"lanes_per_site": lanes, "threads_per_block": threads},
+                   "potential": "single species, variant with pair exponent 5 and density exponent 3",
+                   "precision": prec,
+                   "l2": "working set ~1 GB > L2, not flushed", "parallelism": f"replicas{world}"},
+        "diffusion_steps_per_s": world * 1e3 / ms_step,
+        "max_abs_dx": moved,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- reference arm
@@ -409,11 +535,16 @@ def main():
     ap.add_argument("--fire-iters", type=int, default=FIRE_ITERS)
     ap.add_argument("--quick", action="store_true", help="main precision only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="binary", choices=["binary", "ensemble"])
+    ap.add_argument("--ensemble-steps", type=int, default=ENSEMBLE_STEPS)
+    ap.add_argument("--pass-shape", default="", help="lanes,threads of the passes (default: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
 
