@@ -304,6 +304,75 @@ MXE_API mxe_status mxe_run_staggered(mxe_ctx *ctx, mxe_state *state, int32_t n_s
 MXE_API mxe_status mxe_autotune(mxe_ctx *ctx, const mxe_state *state, int32_t *lanes_out, int32_t *threads_out);
 MXE_API mxe_status mxe_set_pass_shape(mxe_ctx *ctx, int32_t lanes, int32_t threads);
 
+/* ---------------------------------------------------------------------------
+ * Derivatives of the staggered scheme (second order).
+ *
+ * Every pair and density function of the potential is a radial term
+ * A exp(kappa - lambda r) S(r) (App. B.2 analytic forms with the cut-off
+ * switch).  The context holds the distinct terms: the pair terms first, then
+ * the density terms.  mxe_potential_terms returns their count, (A, kappa,
+ * lambda) for each (host array [3 (n_phi + n_f)]), and which term each species
+ * pair uses (phi_of, f_of: host [MXE_MAXS][MXE_MAXS], -1 = none; f_of indices
+ * count from n_phi).  Parameter sensitivities are reported per term with
+ * respect to c = ln A + kappa and lambda (dF/dc = F, dF/dlambda = -r F); a
+ * caller maps them to its own parameters by the chain rule.                 */
+MXE_API mxe_status mxe_potential_terms(mxe_ctx *ctx, int32_t *n_phi, int32_t *n_f, double *terms,
+                                       int32_t *phi_of, int32_t *f_of);
+
+/* Forward-mode pass (FP64 in every precision mode): the gradients of the
+ * free energy and their directional derivatives along a tangent (dq [3][n],
+ * dsigma [n], dx [S][n]; each may be NULL = zero) of the state:
+ *   dFdq, dFdsigma, mu_ex                 values (as mxe_free_energy_grad)
+ *   dFdq_t, dFdsigma_t, mu_ex_t           H v: the Hessian of F (of E_V for
+ *                                         mu_ex) in (q, sigma, x) times the tangent
+ *   dterm [4 T] (T = n_phi + n_f)         dE_V/dc_u, dE_V/dlambda_u (2 T values),
+ *                                         then their directional derivatives (2 T)
+ * Every output is a caller-owned device array and may be NULL.  Because the
+ * Hessian is symmetric these products are also the vector-Jacobian products
+ * of the gradients.  Requires a neighbour list.  Syncs.                      */
+MXE_API mxe_status mxe_tangent(mxe_ctx *ctx, const mxe_state *state, const double *dq_dev, const double *dsigma_dev,
+                               const double *dx_dev, double *dFdq_dev, double *dFdsigma_dev, double *mu_ex_dev,
+                               double *dFdq_t_dev, double *dFdsigma_t_dev, double *mu_ex_t_dev, double *dterm_dev);
+
+/* Vector-Jacobian product of the Euler step x' = x + dt R(x, mu) of
+ * mxe_diffuse_step (Sec. 3.1): given the cotangent xbar_next [S][n] of x',
+ * writes xbar = xbar_next + (dt dR/dx)^T xbar_next and mubar = (dt dR/dmu)^T
+ * xbar_next (device [S][n] each), at the state's x and the given mu_ex.
+ * Per-system step multipliers of a batch apply; reservoir groups are not
+ * differentiated (MXE_ERR_ARG while any is set).  Syncs.                     */
+MXE_API mxe_status mxe_flux_vjp(mxe_ctx *ctx, const mxe_state *state, const double *mu_ex_dev, double dt, double nu0,
+                                double Qm, const double *xbar_next_dev, double *xbar_dev, double *mubar_dev);
+
+typedef struct {
+    int32_t relax_iters_total;  /* FIRE updates of every relaxation, forward and recomputed */
+    int32_t recomputed_steps;   /* relaxations repeated from checkpoints */
+    int32_t cg_iters_total;
+    int32_t cg_iters_max;
+    double cg_resid_max;        /* largest final |r| / |rhs| */
+} mxe_grad_info;
+
+/* Gradient of L = sum_ik w_ik x_ik(n_steps) after n_steps staggered steps
+ * (Sec. 4) with respect to the radial-term parameters and the initial x.
+ * Forward: y_0 = relax(x_0); per step mu_t = mu_ex(y_t, x_t), x_{t+1} =
+ * x_t + dt R(x_t, mu_t), y_{t+1} = relax(x_{t+1}) from y_t, where y = (q,
+ * sigma) and relax = mxe_relax(ftol, max_iter, fire), which must converge
+ * (else MXE_ERR_NO_CONVERGE).  Each relaxed state is differentiated as the
+ * implicit function grad_y F(y, x) = 0: the reverse sweep solves
+ * H_yy lam = H_yx mubar by conjugate gradients (to |r| <= cg_tol |rhs|,
+ * at most cg_max iterations, else MXE_ERR_NO_CONVERGE), with the Hessian
+ * products of mxe_tangent, and accumulates
+ *   xbar_t = xbar_{t+1} + (dt dR/dx)^T xbar_{t+1} + H_xx mubar - H_xy lam,
+ *   thetabar += H_theta,x mubar - H_theta,y lam.
+ * (q, sigma) are kept every `checkpoint_every` steps and recomputed inside a
+ * segment on the way back; x is kept for every step.  Outputs: dterm_host
+ * [2 T] (dL/dc_u, then dL/dlambda_u, host), dx0_dev [S][n] (dL/dx_0, device,
+ * may be NULL), info (host, may be NULL); the state is left at the end of the
+ * run.  FP64 contexts only, no reservoir groups.  Syncs.                     */
+MXE_API mxe_status mxe_unrolled_grad(mxe_ctx *ctx, mxe_state *state, int32_t n_steps, double dt, double nu0,
+                                     double Qm, double ftol, int32_t max_iter, const mxe_fire_params *fire,
+                                     int32_t checkpoint_every, const double *w_dev, double cg_tol, int32_t cg_max,
+                                     double *dterm_host, double *dx0_dev, mxe_grad_info *info);
+
 /* Reservoir groups of the Euler step (Sec. 4: fix setatomicfraction, fix
  * setchemicalpotential; Algorithm 1: applied after the mass-transport step and
  * after the force computation).  fix_mu_mask [n] (nonzero: the site is in the

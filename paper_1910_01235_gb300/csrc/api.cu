@@ -119,6 +119,13 @@ struct mxe_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t step_exec = nullptr;
   StepKey step_key{};
+  // second-order passes (allocated on first use)
+  double* tan_buf = nullptr;   // a, b, e values and tangents: 6 [S][n]
+  double* th_buf = nullptr;    // per-site term sensitivities, values and tangents: 2 x [2 T][n]
+  double* th_sum = nullptr;    // [4 T]: sums of the values, then of the tangents
+  double* dot_part = nullptr;  // partial sums of dot products
+  double* dot_out = nullptr;   // [2]
+  double* dot_h = nullptr;     // pinned [2]
   // result of the last relaxation, per system (one entry without a batch)
   std::vector<int32_t> last_iters, last_reason;
   std::vector<double> last_fmax;
@@ -789,6 +796,115 @@ mxe_status enqueue_tune_work(mxe_ctx* c, const mxe_state* s) {
   return MXE_OK;
 }
 
+// ---------------------------------------------------------------- second order
+int n_terms(const mxe_ctx* c) { return c->dp.n_phi + c->dp.n_f; }
+
+mxe_status ensure_tangent(mxe_ctx* c) {
+  if (c->tan_buf) return MXE_OK;
+  const int64_t n = c->n, S = c->S, T = n_terms(c);
+  CK(dalloc(&c->tan_buf, 6 * S * n));
+  CK(dalloc(&c->th_buf, 2 * 2 * T * n));
+  CK(dalloc(&c->th_sum, 4 * T));
+  CK(dalloc(&c->dot_part, dot_partials_len(4 * n + 1)));
+  CK(dalloc(&c->dot_out, 2));
+  CK(cudaMallocHost((void**)&c->dot_h, 2 * sizeof(double)));
+  return MXE_OK;
+}
+
+// One forward-mode pass: values and tangents of dF/dq, dF/dsigma, mu^ex and
+// (when th_out) the summed term sensitivities [values 2T | tangents 2T].
+mxe_status enqueue_tangent(mxe_ctx* c, const mxe_state* s, const double* dq, const double* dsig, const double* dx,
+                           double* gq_v, double* gs_v, double* mu_v, double* gq_t, double* gs_t, double* mu_t,
+                           double* th_out) {
+  const int64_t n = c->n, S = c->S, T = n_terms(c);
+  TanArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.q = s->q;
+  A.sigma = s->sigma;
+  A.x = s->x;
+  A.T = s->T;
+  A.dq = dq;
+  A.dsigma = dsig;
+  A.dx = dx;
+  A.nb_off = c->nb_off;
+  A.nb_ent = c->nb_ent;
+  A.n = n;
+  double* b = c->tan_buf;
+  A.a_v = b;
+  A.a_t = b + S * n;
+  A.b_v = b + 2 * S * n;
+  A.b_t = b + 3 * S * n;
+  A.e_v = b + 4 * S * n;
+  A.e_t = b + 5 * S * n;
+  A.gq_v = gq_v;
+  A.gs_v = gs_v;
+  A.mu_v = mu_v;
+  A.gq_t = gq_t;
+  A.gs_t = gs_t;
+  A.mu_t = mu_t;
+  if (th_out) {
+    A.th_v = c->th_buf;
+    A.th_t = c->th_buf + 2 * T * n;
+  }
+  A.flags = c->flags;
+  A.batch = c->B;
+  CK(TIMED("tangent", launch_tangent(c->dp, c->grid, A, c->stream)));
+  if (th_out && T > 0) {
+    CK(launch_col_sum(A.th_v, (int)(2 * T), n, th_out, c->stream));
+    CK(launch_col_sum(A.th_t, (int)(2 * T), n, th_out + 2 * T, c->stream));
+  }
+  return MXE_OK;
+}
+
+// <a, b> over len doubles, returned on the host (syncs)
+mxe_status dot_host(mxe_ctx* c, const double* a, const double* b, int64_t len, double& out) {
+  CK(launch_dot(a, b, len, c->dot_part, c->dot_out, c->stream));
+  CK(cudaMemcpyAsync(c->dot_h, c->dot_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  out = c->dot_h[0];
+  return MXE_OK;
+}
+
+// Conjugate gradients on H lam = rhs, H the Hessian of F in y = (q [3n],
+// sigma [n]) at fixed x, applied by the forward-mode pass.  lam, r, p, Hp:
+// 4n device vectors.  Stops at |r| <= tol |rhs| or max_it iterations.
+mxe_status cg_solve(mxe_ctx* c, const mxe_state* s, const double* rhs, double* lam, double* r, double* p,
+                    double* Hp, double tol, int max_it, int& iters, double& rel) {
+  const int64_t n = c->n, m = 4 * n;
+  cudaStream_t st = c->stream;
+  iters = 0;
+  rel = 0.0;
+  if (m > 0) CK(cudaMemsetAsync(lam, 0, sizeof(double) * m, st));
+  CK(copy_d2d(r, rhs, sizeof(double) * m, st));
+  CK(copy_d2d(p, rhs, sizeof(double) * m, st));
+  double rr = 0.0;
+  mxe_status ms = dot_host(c, r, r, m, rr);
+  if (ms != MXE_OK) return ms;
+  const double rr0 = rr;
+  if (!(rr0 > 0.0)) return MXE_OK;
+  while (iters < max_it) {
+    ms = enqueue_tangent(c, s, p, p + 3 * n, nullptr, nullptr, nullptr, nullptr, Hp, Hp + 3 * n, nullptr, nullptr);
+    if (ms != MXE_OK) return ms;
+    double pHp = 0.0;
+    ms = dot_host(c, p, Hp, m, pHp);
+    if (ms != MXE_OK) return ms;
+    if (!(pHp > 0.0)) return MXE_ERR_NONFINITE;  // not a minimum: no implicit function
+    const double alpha = rr / pHp;
+    CK(launch_axpby(lam, p, alpha, 1.0, m, st));
+    CK(launch_axpby(r, Hp, -alpha, 1.0, m, st));
+    double rr1 = 0.0;
+    ms = dot_host(c, r, r, m, rr1);
+    if (ms != MXE_OK) return ms;
+    ++iters;
+    rel = std::sqrt(rr1 / rr0);
+    if (!std::isfinite(rel)) return MXE_ERR_NONFINITE;
+    if (rel <= tol) break;
+    CK(launch_axpby(p, r, 1.0, rr1 / rr, m, st));  // p = r + beta p
+    rr = rr1;
+  }
+  return MXE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -961,6 +1077,12 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  dfree(c->tan_buf);
+  dfree(c->th_buf);
+  dfree(c->th_sum);
+  dfree(c->dot_part);
+  dfree(c->dot_out);
+  if (c->dot_h) cudaFreeHost(c->dot_h);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   dfree(c->cell_of);
   dfree(c->cell_slot);
@@ -1093,6 +1215,210 @@ mxe_status mxe_relax_info(mxe_ctx* c, int32_t n_entries, int32_t* iters, double*
     if (fmax) fmax[b] = c->last_fmax[b];
     if (converged) converged[b] = c->last_reason[b] == kReasonConverged ? 1 : 0;
   }
+  return MXE_OK;
+}
+
+mxe_status mxe_potential_terms(mxe_ctx* c, int32_t* n_phi, int32_t* n_f, double* terms, int32_t* phi_of,
+                               int32_t* f_of) {
+  if (!c) return MXE_ERR_ARG;
+  const DevPot& P = c->dp;
+  if (n_phi) *n_phi = P.n_phi;
+  if (n_f) *n_f = P.n_f;
+  if (terms) {
+    int k = 0;
+    for (int u = 0; u < P.n_phi; ++u, ++k) {
+      terms[3 * k] = P.phi[u].A;
+      terms[3 * k + 1] = P.phi[u].kappa;
+      terms[3 * k + 2] = P.phi[u].lambda;
+    }
+    for (int v = 0; v < P.n_f; ++v, ++k) {
+      terms[3 * k] = P.f[v].A;
+      terms[3 * k + 1] = P.f[v].kappa;
+      terms[3 * k + 2] = P.f[v].lambda;
+    }
+  }
+  for (int k = 0; k < MXE_MAXS; ++k)
+    for (int l = 0; l < MXE_MAXS; ++l) {
+      const bool in = k < P.S && l < P.S;
+      if (phi_of) phi_of[k * MXE_MAXS + l] = in ? P.phi_of[k][l] : -1;
+      if (f_of) f_of[k * MXE_MAXS + l] = in && P.f_of[k][l] >= 0 ? P.n_phi + P.f_of[k][l] : -1;
+    }
+  return MXE_OK;
+}
+
+mxe_status mxe_tangent(mxe_ctx* c, const mxe_state* s, const double* dq_dev, const double* dsigma_dev,
+                       const double* dx_dev, double* dFdq_dev, double* dFdsigma_dev, double* mu_ex_dev,
+                       double* dFdq_t_dev, double* dFdsigma_t_dev, double* mu_ex_t_dev, double* dterm_dev) {
+  if (!c || !state_ok(c, s)) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  mxe_status ms = ensure_tangent(c);
+  if (ms != MXE_OK) return ms;
+  ms = enqueue_tangent(c, s, dq_dev, dsigma_dev, dx_dev, dFdq_dev, dFdsigma_dev, mu_ex_dev, dFdq_t_dev,
+                       dFdsigma_t_dev, mu_ex_t_dev, dterm_dev);
+  if (ms != MXE_OK) return ms;
+  return mxe_sync_status(c);
+}
+
+mxe_status mxe_flux_vjp(mxe_ctx* c, const mxe_state* s, const double* mu_ex_dev, double dt, double nu0, double Qm,
+                        const double* xbar_next_dev, double* xbar_dev, double* mubar_dev) {
+  if (!c || !state_ok(c, s) || !mu_ex_dev || !xbar_next_dev || !xbar_dev || !mubar_dev) return MXE_ERR_ARG;
+  if (!(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm)) return MXE_ERR_ARG;
+  if (c->fix_x_mask || c->fix_mu_mask) return MXE_ERR_ARG;  // reservoir groups are not differentiated
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  CK(launch_flux_vjp(s->x, s->T, mu_ex_dev, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm,
+                     c->nsys ? c->dt_sys : nullptr, c->nsys ? c->sys_of : nullptr, xbar_next_dev, xbar_dev,
+                     mubar_dev, c->stream));
+  return mxe_sync_status(c);
+}
+
+mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double dt, double nu0, double Qm,
+                             double ftol, int32_t max_iter, const mxe_fire_params* fire, int32_t every,
+                             const double* w_dev, double cg_tol, int32_t cg_max, double* dterm_host,
+                             double* dx0_dev, mxe_grad_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!c || !state_ok(c, s) || n_steps < 0 || every < 1 || !w_dev || !dterm_host || !(cg_tol > 0.0) ||
+      cg_max < 1 || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm) || !(ftol >= 0.0) || max_iter < 0)
+    return MXE_ERR_ARG;
+  if (c->precision != MXE_FP64 || c->fix_x_mask || c->fix_mu_mask) return MXE_ERR_ARG;
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  mxe_status ms = ensure_tangent(c);
+  if (ms != MXE_OK) return ms;
+  const int64_t n = c->n, S = c->S, T = n_terms(c), ny = 4 * n, nx = S * n;
+  const int nck = n_steps / every + 1;
+  cudaStream_t st = c->stream;
+  // work arrays (freed on return)
+  std::vector<double*> owned;
+  auto alloc = [&](int64_t len) -> double* {
+    double* p = nullptr;
+    if (dalloc(&p, len) != cudaSuccess) return nullptr;
+    owned.push_back(p);
+    return p;
+  };
+  struct Free {
+    std::vector<double*>& v;
+    ~Free() {
+      for (double* p : v) cudaFree(p);
+    }
+  } fr{owned};
+  double* X = alloc((int64_t)(n_steps + 1) * nx);    // x_t, every step
+  double* Y = alloc((int64_t)nck * ny);              // (q, sigma) every `every` steps
+  double* seg = alloc((int64_t)every * ny);          // (q, sigma) recomputed inside a segment
+  double* yT = alloc(ny);                            // final state
+  double* mu = alloc(nx);
+  double* xbar = alloc(nx);
+  double* xdir = alloc(nx);
+  double* mubar = alloc(nx);
+  double* rhs = alloc(ny);
+  double* lam = alloc(ny);
+  double* r = alloc(ny);
+  double* p = alloc(ny);
+  double* Hp = alloc(ny);
+  double* th = alloc(4 * T);
+  double* mut = alloc(nx);
+  if (!X || !Y || !seg || !yT || !mu || !xbar || !xdir || !mubar || !rhs || !lam || !r || !p || !Hp || !th || !mut)
+    return MXE_ERR_OOM;
+  auto save_y = [&](double* dst) -> mxe_status {
+    CK(copy_d2d(dst, s->q, sizeof(double) * 3 * n, st));
+    CK(copy_d2d(dst + 3 * n, s->sigma, sizeof(double) * n, st));
+    return MXE_OK;
+  };
+  auto load_y = [&](const double* src) -> mxe_status {
+    CK(copy_d2d(s->q, src, sizeof(double) * 3 * n, st));
+    CK(copy_d2d(s->sigma, src + 3 * n, sizeof(double) * n, st));
+    return MXE_OK;
+  };
+  auto relax = [&]() -> mxe_status {
+    int32_t it = 0;
+    double fm = 0.0;
+    mxe_status r2 = mxe_relax(c, s, ftol, max_iter, fire, &it, &fm);
+    if (info) info->relax_iters_total += it;
+    return r2;
+  };
+  auto mu_pass = [&]() -> mxe_status {  // mu^ex at the current state into `mu`
+    PassArgs A;
+    fill_pass(c, s, A);
+    A.site_E = nullptr;
+    A.gq = nullptr;
+    A.gs = nullptr;
+    A.mu_ex = mu;
+    mxe_status r2 = enqueue_passes(c, s, A, true);
+    if (r2 != MXE_OK) return r2;
+    return mxe_sync_status(c);
+  };
+#define RUN(expr)                      \
+  do {                                 \
+    mxe_status _m = (expr);            \
+    if (_m != MXE_OK) return _m;       \
+  } while (0)
+  // ---- forward: y_0 = relax(x_0); per step mu, Euler, relax
+  RUN(relax());
+  CK(copy_d2d(X, s->x, sizeof(double) * nx, st));
+  RUN(save_y(Y));
+  for (int t = 0; t < n_steps; ++t) {
+    RUN(mu_pass());
+    RUN(mxe_diffuse_step(c, s, mu, dt, nu0, Qm));
+    RUN(relax());
+    CK(copy_d2d(X + (int64_t)(t + 1) * nx, s->x, sizeof(double) * nx, st));
+    if ((t + 1) % every == 0) RUN(save_y(Y + (int64_t)((t + 1) / every) * ny));
+  }
+  RUN(save_y(yT));
+  // ---- reverse sweep
+  std::vector<double> acc(2 * T, 0.0), hth(4 * T, 0.0);
+  CK(copy_d2d(xbar, w_dev, sizeof(double) * nx, st));
+  for (int c0 = ((n_steps - 1) / every) * every; n_steps > 0 && c0 >= 0; c0 -= every) {
+    const int c1 = std::min(c0 + every, n_steps);
+    // recompute the relaxed states of the segment from its checkpoint
+    RUN(load_y(Y + (int64_t)(c0 / every) * ny));
+    RUN(save_y(seg));
+    for (int t = c0 + 1; t < c1; ++t) {
+      CK(copy_d2d(s->x, X + (int64_t)t * nx, sizeof(double) * nx, st));
+      RUN(build_lists(c, s, c->skin, c->r_bond));
+      RUN(relax());
+      RUN(save_y(seg + (int64_t)(t - c0) * ny));
+      if (info) info->recomputed_steps += 1;
+    }
+    for (int t = c1 - 1; t >= c0; --t) {
+      RUN(load_y(seg + (int64_t)(t - c0) * ny));
+      CK(copy_d2d(s->x, X + (int64_t)t * nx, sizeof(double) * nx, st));
+      RUN(build_lists(c, s, c->skin, c->r_bond));
+      RUN(mu_pass());
+      // Euler step: xbar_t (direct part) and mubar from xbar_{t+1}
+      CK(launch_flux_vjp(s->x, s->T, mu, c->bd_off, c->bd_idx, n, (int)S, dt, nu0, Qm,
+                         c->nsys ? c->dt_sys : nullptr, c->nsys ? c->sys_of : nullptr, xbar, xdir, mubar, st));
+      // relaxed state as an implicit function of x: H lam = H_yx mubar
+      RUN(enqueue_tangent(c, s, nullptr, nullptr, mubar, nullptr, nullptr, nullptr, rhs, rhs + 3 * n, nullptr,
+                          nullptr));
+      int iters = 0;
+      double rel = 0.0;
+      RUN(cg_solve(c, s, rhs, lam, r, p, Hp, cg_tol, cg_max, iters, rel));
+      if (info) {
+        info->cg_iters_total += iters;
+        info->cg_iters_max = std::max(info->cg_iters_max, iters);
+        info->cg_resid_max = std::max(info->cg_resid_max, rel);
+      }
+      if (rel > cg_tol && iters >= cg_max) return MXE_ERR_NO_CONVERGE;
+      // xbar_t = xdir + H_xx mubar - H_xy lam; thetabar += H_tx mubar - H_ty lam
+      CK(launch_axpby(lam, lam, 0.0, -1.0, ny, st));
+      RUN(enqueue_tangent(c, s, lam, lam + 3 * n, mubar, nullptr, nullptr, nullptr, nullptr, nullptr, mut, th));
+      CK(launch_axpby(xdir, mut, 1.0, 1.0, nx, st));
+      CK(copy_d2d(xbar, xdir, sizeof(double) * nx, st));
+      CK(cudaMemcpyAsync(hth.data(), th, sizeof(double) * 4 * T, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int u = 0; u < 2 * T; ++u) acc[u] += hth[2 * T + u];
+      RUN(mxe_sync_status(c));
+    }
+  }
+  for (int u = 0; u < 2 * T; ++u) dterm_host[u] = acc[u];
+  if (dx0_dev) CK(copy_d2d(dx0_dev, xbar, sizeof(double) * nx, st));
+  // leave the state at the end of the run
+  RUN(load_y(yT));
+  CK(copy_d2d(s->x, X + (int64_t)n_steps * nx, sizeof(double) * nx, st));
+  RUN(build_lists(c, s, c->skin, c->r_bond));
+#undef RUN
+  CK(cudaStreamSynchronize(st));
   return MXE_OK;
 }
 

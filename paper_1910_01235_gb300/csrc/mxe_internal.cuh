@@ -230,6 +230,29 @@ cudaError_t launch_step_begin(Ctrl* ctrl, double dt0, double alpha0, cudaStream_
 cudaError_t launch_step_end(Ctrl* ctrl, cudaStream_t s);
 cudaError_t launch_fire_zero_v(double* vq, double* vs, int64_t n, const Ctrl* gate, cudaStream_t s);
 
+// deriv.cu: forward-mode (dual-number) density and gradient passes
+struct TanArgs {
+  const double *q, *sigma, *x, *T;           // state
+  const double *dq, *dsigma, *dx;            // tangents ([3][n], [n], [S][n]; null: zero)
+  const int* nb_off;
+  const uint32_t* nb_ent;
+  int64_t n;
+  double *a_v, *a_t, *b_v, *b_t, *e_v, *e_t;  // [S][n] embedding terms (written by the density pass)
+  double *gq_v, *gq_t, *gs_v, *gs_t, *mu_v, *mu_t;  // outputs, any may be null
+  double *th_v, *th_t;                       // [2 T][n] per-site term sensitivities (null: skip)
+  int* flags;
+  Batch batch;
+};
+cudaError_t launch_tangent(const DevPot& P, const DevGrid& g, const TanArgs& A, cudaStream_t s);
+cudaError_t launch_col_sum(const double* col, int ncol, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_flux_vjp(const double* x, const double* T, const double* mu, const int* bd_off, const int* bd_idx,
+                            int64_t n, int S, double dt, double nu0, double Qm, const double* dt_sys,
+                            const int* sys_of, const double* xbar1, double* xbar0, double* mubar, cudaStream_t s);
+int64_t dot_partials_len(int64_t len);
+cudaError_t launch_dot(const double* a, const double* b, int64_t len, double* part, double* out, cudaStream_t s);
+// y = alpha x + beta y
+cudaError_t launch_axpby(double* y, const double* x, double alpha, double beta, int64_t len, cudaStream_t s);
+
 // flux.cu
 int64_t flux_scratch_len(int64_t n, int S);
 // with reservoir groups (any pointer may be null); mu_eff: [S][n] scratch

@@ -46,6 +46,11 @@ class mxe_state(C.Structure):
                 ("pad", C.c_uint32)]
 
 
+class mxe_grad_info(C.Structure):
+    _fields_ = [("relax_iters_total", C.c_int32), ("recomputed_steps", C.c_int32),
+                ("cg_iters_total", C.c_int32), ("cg_iters_max", C.c_int32), ("cg_resid_max", C.c_double)]
+
+
 class mxe_fire_params(C.Structure):
     _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("f_inc", C.c_double),
                 ("f_dec", C.c_double), ("alpha0", C.c_double), ("f_alpha", C.c_double),
@@ -56,7 +61,8 @@ EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy",
            "mxe_export_neighbors", "mxe_export_bonds", "mxe_free_energy_grad", "mxe_free_energy_grad_async",
            "mxe_sync_status", "mxe_relax", "mxe_relax_info", "mxe_diffuse_step", "mxe_diffuse_step_async",
            "mxe_diffuse_step_noalloc", "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs",
-           "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape"]
+           "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape",
+           "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad"]
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
 
@@ -89,6 +95,12 @@ def lib():
             L.mxe_run_staggered.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.POINTER(C.c_int32)]
             L.mxe_autotune.argtypes = [p, p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
             L.mxe_set_pass_shape.argtypes = [p, C.c_int32, C.c_int32]
+            i32p = C.POINTER(C.c_int32)
+            L.mxe_potential_terms.argtypes = [p, i32p, i32p, p, p, p]
+            L.mxe_tangent.argtypes = [p, p] + [p] * 10
+            L.mxe_flux_vjp.argtypes = [p, p, p, d, d, d, p, p, p]
+            L.mxe_unrolled_grad.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.c_int32, p, d, C.c_int32,
+                                            p, p, p]
             L.mxe_destroy.argtypes = [p]
             L.mxe_build_neighbors.argtypes = [p, p, d, d, C.POINTER(i64), C.POINTER(d)]
             L.mxe_export_neighbors.argtypes = [p, p, p]
@@ -168,6 +180,40 @@ def mxe_autotune(ctx, state):
 
 def mxe_set_pass_shape(ctx, lanes, threads):
     return lib().mxe_set_pass_shape(ctx, int(lanes), int(threads))
+
+
+def mxe_potential_terms(ctx):
+    """(n_phi, n_f, terms [T, 3] = (A, kappa, lambda), phi_of [4, 4], f_of [4, 4])."""
+    nphi, nf = C.c_int32(0), C.c_int32(0)
+    terms = (C.c_double * (3 * (MAXS * (MAXS + 1) // 2 + MAXS * MAXS)))()
+    phi_of = (C.c_int32 * (MAXS * MAXS))()
+    f_of = (C.c_int32 * (MAXS * MAXS))()
+    st = lib().mxe_potential_terms(ctx, C.byref(nphi), C.byref(nf), terms, phi_of, f_of)
+    T = nphi.value + nf.value
+    return (st, nphi.value, nf.value, np.array(terms[:3 * T]).reshape(T, 3),
+            np.array(phi_of[:]).reshape(MAXS, MAXS), np.array(f_of[:]).reshape(MAXS, MAXS))
+
+
+def mxe_tangent(ctx, state, dq, dsigma, dx, gq, gs, mu, gq_t, gs_t, mu_t, dterm):
+    """All arguments after the state are device pointers (0 = none)."""
+    return lib().mxe_tangent(ctx, C.byref(state), *[C.c_void_p(v or 0) for v in
+                                                    (dq, dsigma, dx, gq, gs, mu, gq_t, gs_t, mu_t, dterm)])
+
+
+def mxe_flux_vjp(ctx, state, mu_ex, dt, nu0, Qm, xbar_next, xbar, mubar):
+    return lib().mxe_flux_vjp(ctx, C.byref(state), C.c_void_p(mu_ex), float(dt), float(nu0), float(Qm),
+                              C.c_void_p(xbar_next), C.c_void_p(xbar), C.c_void_p(mubar))
+
+
+def mxe_unrolled_grad(ctx, state, n_steps, dt, nu0, Qm, ftol, max_iter, fire, every, w_ptr, cg_tol, cg_max,
+                      n_terms, dx0_ptr=0):
+    dterm = (C.c_double * max(2 * n_terms, 1))()
+    info = mxe_grad_info()
+    st = lib().mxe_unrolled_grad(ctx, C.byref(state), int(n_steps), float(dt), float(nu0), float(Qm), float(ftol),
+                                 int(max_iter), C.byref(fire) if fire is not None else None, int(every),
+                                 C.c_void_p(w_ptr), float(cg_tol), int(cg_max), dterm, C.c_void_p(dx0_ptr or 0),
+                                 C.byref(info))
+    return st, np.array(dterm[:2 * n_terms]), {nm: getattr(info, nm) for nm, _ in mxe_grad_info._fields_}
 
 
 def mxe_build_neighbors(ctx, state: mxe_state, skin: float, r_bond: float):
@@ -405,12 +451,103 @@ class MxeSystem:
     def set_pass_shape(self, lanes, threads):
         self._check(mxe_set_pass_shape(self.ctx, lanes, threads), "mxe_set_pass_shape")
 
+    # ---------------------------------------------------------- second order
+    def potential_terms(self):
+        st, nphi, nf, terms, phi_of, f_of = mxe_potential_terms(self.ctx)
+        self._check(st, "mxe_potential_terms")
+        return nphi, nf, terms, phi_of, f_of
+
+    def tangent(self, dq=None, dsigma=None, dx=None):
+        """Values and directional derivatives of (dF/dq, dF/dsigma, mu_ex) and
+        of the term sensitivities along (dq, dsigma, dx) (device tensors or None)."""
+        t = self.torch
+        nphi, nf, _, _, _ = self.potential_terms()
+        T = nphi + nf
+        z = lambda *shape: t.zeros(shape, dtype=t.float64, device=self.device)
+        out = dict(gq=z(3, self.n), gs=z(self.n), mu_ex=z(self.S, self.n), gq_t=z(3, self.n), gs_t=z(self.n),
+                   mu_ex_t=z(self.S, self.n), dterm=z(4 * T))
+        st = mxe_tangent(self.ctx, self.state, _ptr(dq), _ptr(dsigma), _ptr(dx), _ptr(out["gq"]), _ptr(out["gs"]),
+                         _ptr(out["mu_ex"]), _ptr(out["gq_t"]), _ptr(out["gs_t"]), _ptr(out["mu_ex_t"]),
+                         _ptr(out["dterm"]))
+        self._check(st, "mxe_tangent")
+        return out
+
+    def flux_vjp(self, mu_ex, dt, xbar_next, nu0=None, Qm=None):
+        t = self.torch
+        xbar = t.zeros_like(xbar_next)
+        mubar = t.zeros_like(xbar_next)
+        st = mxe_flux_vjp(self.ctx, self.state, _ptr(mu_ex), dt, self.sys.nu0 if nu0 is None else nu0,
+                          self.sys.Qm if Qm is None else Qm, _ptr(xbar_next), _ptr(xbar), _ptr(mubar))
+        self._check(st, "mxe_flux_vjp")
+        return xbar, mubar
+
+    def unrolled_grad(self, n_steps, dt, w, ftol=1e-10, max_iter=50000, every=5, cg_tol=1e-10, cg_max=5000,
+                      fire=None, nu0=None, Qm=None):
+        """dL/d(term parameters) and dL/dx_0 for L = sum w x after n_steps
+        staggered steps (mxe_unrolled_grad).  Returns (dterm [2 T], dx0, info)."""
+        nphi, nf, _, _, _ = self.potential_terms()
+        w = self.torch.as_tensor(w, dtype=self.torch.float64, device=self.device).contiguous()
+        dx0 = self.torch.zeros_like(w)
+        st, dterm, info = mxe_unrolled_grad(self.ctx, self.state, n_steps, dt, self.sys.nu0 if nu0 is None else nu0,
+                                            self.sys.Qm if Qm is None else Qm, ftol, max_iter, fire, every,
+                                            _ptr(w), cg_tol, cg_max, nphi + nf, _ptr(dx0))
+        self._check(st, "mxe_unrolled_grad")
+        return dterm, dx0, info
+
     def staggered_step(self, dt, ftol, max_iter, fire=None):
         """One step of the staggered scheme (Sec. 4): excess chemical potentials,
         one Euler step of x, then relaxation of (q, sigma) at fixed x."""
         self.free_energy_grad(with_mu=False)
         self.diffuse_step(dt, mu_ex=self.mu_ex)
         return self.relax(ftol, max_iter, fire)
+
+
+def term_parameters(pot, phi_of, f_of, n_phi, n_f):
+    """(c, lambda) of each of the library's radial terms computed from the
+    potential tables: c = ln A + exponent, lambda = exponent / length scale;
+    a geometric-mean cross pair averages the two like-pair terms (the form in
+    which the library evaluates it)."""
+    T = n_phi + n_f
+    c = np.zeros(T)
+    lam = np.zeros(T)
+    seen = np.zeros(T, bool)
+    S = pot.n_species
+    for k in range(S):
+        for l in range(S):
+            u = phi_of[k, l]
+            if u >= 0 and not seen[u]:
+                if pot.cross_geomean and k != l:
+                    c[u] = 0.5 * (np.log(pot.phi_A[k, k]) + pot.phi_p[k, k] + np.log(pot.phi_A[l, l]) + pot.phi_p[l, l])
+                    lam[u] = 0.5 * (pot.phi_p[k, k] / pot.phi_r0[k, k] + pot.phi_p[l, l] / pot.phi_r0[l, l])
+                else:
+                    c[u] = np.log(pot.phi_A[k, l]) + pot.phi_p[k, l]
+                    lam[u] = pot.phi_p[k, l] / pot.phi_r0[k, l]
+                seen[u] = True
+            v = f_of[k, l]
+            if v >= 0 and not seen[v]:
+                c[v] = np.log(pot.f_xi[k, l]) + pot.f_q[k, l]
+                lam[v] = pot.f_q[k, l] / pot.f_r0[k, l]
+                seen[v] = True
+    return c, lam
+
+
+def chain_to_parameters(dterm, make_pot, theta, phi_of, f_of, n_phi, n_f, rel_step=1e-6):
+    """dL/dtheta from the per-term sensitivities dterm = [dL/dc (T), dL/dlambda
+    (T)]: the chain rule through the host map theta -> potential -> (c,
+    lambda), whose Jacobian is taken by central differences of that map
+    (a few logarithms and ratios; error ~1e-12 relative)."""
+    T = n_phi + n_f
+    theta = np.asarray(theta, float)
+    out = np.zeros(theta.size)
+    for m in range(theta.size):
+        h = rel_step * max(abs(theta[m]), 1.0)
+        tp, tm = theta.copy(), theta.copy()
+        tp[m] += h
+        tm[m] -= h
+        cp, lp = term_parameters(make_pot(tp), phi_of, f_of, n_phi, n_f)
+        cm, lm = term_parameters(make_pot(tm), phi_of, f_of, n_phi, n_f)
+        out[m] = dterm[:T] @ ((cp - cm) / (2 * h)) + dterm[T:2 * T] @ ((lp - lm) / (2 * h))
+    return out
 
 
 def concatenate(systems):

@@ -103,6 +103,30 @@ def potential_binary_variant_s() -> Potential:
     return P
 
 
+# The eight parameters differentiated in the surface-alloy workload: for each
+# element e in (A, B): pair prefactor A_e, pair exponent p_e, density exponent
+# q_e and length scale r0_e (shared by the element's pair and density terms).
+THETA_NAMES = ("A_A", "p_A", "q_A", "r0_A", "A_B", "p_B", "q_B", "r0_B")
+
+
+def theta_of(pot: Potential) -> np.ndarray:
+    return np.array([pot.phi_A[0, 0], pot.phi_p[0, 0], pot.f_q[0, 0], pot.phi_r0[0, 0],
+                     pot.phi_A[1, 1], pot.phi_p[1, 1], pot.f_q[0, 1], pot.phi_r0[1, 1]])
+
+
+def binary_from_theta(theta, base: Potential = None) -> Potential:
+    """The binary tables with element e's (A_e, p_e, q_e, r0_e) replaced;
+    the density from an e-neighbour uses q_e and r0_e at every site."""
+    P = dataclasses.replace(base if base is not None else potential_binary())
+    P.phi_A, P.phi_p, P.phi_r0 = P.phi_A.copy(), P.phi_p.copy(), P.phi_r0.copy()
+    P.f_q, P.f_r0 = P.f_q.copy(), P.f_r0.copy()
+    for e in range(2):
+        A, p, q, r0 = (float(v) for v in theta[4 * e:4 * e + 4])
+        P.phi_A[e, e], P.phi_p[e, e], P.phi_r0[e, e] = A, p, r0
+        P.f_q[:, e], P.f_r0[:, e] = q, r0
+    return P
+
+
 def potential_host_solute() -> Potential:
     """Species 0 = host, 1 = interstitial solute.  Host-host as the single
     species potential; host-solute pair and density with prefactor 0.5 and
