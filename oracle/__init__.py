@@ -101,6 +101,8 @@ def lib():
             L.orc_diffuse_step_res.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double,
                                                C.c_double, p, p, p, p]
             L.orc_relax.argtypes = [p, p, p, p, C.c_double, C.c_double, C.c_int, p, p, p]
+            L.orc_transport_step.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_double, p]
             L.orc_num_threads.argtypes = []
             _lib = L
         return _lib
@@ -267,6 +269,21 @@ def diffuse_step(sys, mu_ex, bond_csr, dt, x=None, nu0=None, Qm=None, fix_x=None
                                     float(dt), float(sys.nu0 if nu0 is None else nu0),
                                     float(sys.Qm if Qm is None else Qm), _ptr(fxm), _ptr(fxv), _ptr(fmm), _ptr(fmv))
     return int(st), xx
+
+
+def transport_step(sys, mu_ex, bond_csr, dt, host=-1, tau=0.0, v=None, x=None, nu0=None, Qm=None):
+    """One step of the transport variants (host exchange, ballistic term;
+    definitions in the C source).  v: [S, n] rates for tau > 0 (in-out copy).
+    Returns (status, x_new, v_new)."""
+    xx = _f64(sys.x if x is None else x).copy()
+    vv = None if v is None else _f64(v).copy()
+    T = _f64(sys.T)
+    mu = _f64(mu_ex)
+    off, idx = bond_csr
+    st = lib().orc_transport_step(sys.n, xx.shape[0], _ptr(xx), _ptr(T), _ptr(mu), _ptr(off), _ptr(idx),
+                                  float(dt), float(sys.nu0 if nu0 is None else nu0),
+                                  float(sys.Qm if Qm is None else Qm), int(host), float(tau), _ptr(vv))
+    return int(st), xx, vv
 
 
 def relax(sys, ftol, max_iter, fire: FireParams | None = None, skin=0.2, q=None, sigma=None, x=None):

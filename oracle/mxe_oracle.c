@@ -691,6 +691,108 @@ int orc_diffuse_step(int64_t n, int S, double *x, const double *T, const double 
 }
 
 /* ------------------------------------------------------------------ */
+/* Variants of the transport step (Sec. 3, Eq. Transport and Eq. MassTransport).
+ *
+ * Host exchange (host >= 0): the exchange partner of every species k != host
+ * is the host species instead of the vacancy, as in a binary alloy without
+ * vacancies where x and 1 - x are the two species of Eq. MassTransport:
+ *   J^k_{i->j} = D_i x_ik x_j,host exp(beta_i (m_ik - m_jk)),
+ *   m_k = mu_k - mu_host (the chemical potential of exchanging a host atom
+ *   for a k atom), and every k atom leaving i is replaced by a host atom:
+ *   R_ik = sum_j (J^k_{j->i} - J^k_{i->j}),  R_i,host = -sum_{k != host} R_ik.
+ * host < 0 is the vacancy-mediated law of orc_diffuse_step.
+ *
+ * Ballistic term (tau > 0): tau d2x/dt2 + dx/dt = R.  Written as dx/dt = v,
+ * tau dv/dt = R - v, and integrated over one step with R held at its value
+ * at the start of the step (the analogue of the explicit Euler step):
+ *   v' = R + (v - R) e,    x' = x + dt R + tau (v - R)(1 - e),  e = exp(-dt/tau).
+ * tau = 0 is the Euler step x' = x + dt R (v, if given, becomes R).
+ * The range rule of orc_diffuse_step applies to x'; on failure x and v are
+ * unchanged.                                                              */
+/* ------------------------------------------------------------------ */
+int orc_transport_step(int64_t n, int S, double *x, const double *T, const double *mu_ex,
+                       const int32_t *b_off, const int32_t *b_idx, double dt, double nu0, double Qm,
+                       int host, double tau, double *v)
+{
+    if (host >= S) return ORC_ERR_ARG;
+    if (tau > 0.0 && !v) return ORC_ERR_ARG;
+    double *R = (double *)calloc((size_t)(S * n + 1), sizeof(double));
+    double *xn = (double *)malloc(sizeof(double) * (size_t)(S * n + 1));
+    double *vn = (double *)malloc(sizeof(double) * (size_t)(S * n + 1));
+    int bad = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const double beta_i = 1.0 / (ORC_KB * T[i]);
+        const double Di = nu0 * exp(-beta_i * Qm);
+        double part_i = 1.0;                      /* vacancy fraction, or the host's */
+        if (host < 0) {
+            for (int k = 0; k < S; ++k) part_i -= x[k * n + i];
+        } else {
+            part_i = x[host * n + i];
+        }
+        for (int k = 0; k < S; ++k) {
+            if (k == host) continue;
+            double rate = 0.0;
+            for (int32_t t = b_off[i]; t < b_off[i + 1]; ++t) {
+                const int64_t j = b_idx[t];
+                const double beta_j = 1.0 / (ORC_KB * T[j]);
+                const double Dj = nu0 * exp(-beta_j * Qm);
+                double part_j = 1.0;
+                if (host < 0) {
+                    for (int kk = 0; kk < S; ++kk) part_j -= x[kk * n + j];
+                } else {
+                    part_j = x[host * n + j];
+                }
+                double mi = mu_ex[k * n + i], mj = mu_ex[k * n + j];
+                if (host >= 0) {
+                    mi -= mu_ex[host * n + i];
+                    mj -= mu_ex[host * n + j];
+                }
+                const double out_ij = Di * x[k * n + i] * part_j * exp(beta_i * (mi - mj));
+                const double in_ji = Dj * x[k * n + j] * part_i * exp(beta_j * (mj - mi));
+                rate += in_ji - out_ij;
+            }
+            R[k * n + i] = rate;
+        }
+        if (host >= 0) {
+            double r = 0.0;
+            for (int k = 0; k < S; ++k)
+                if (k != host) r -= R[k * n + i];
+            R[host * n + i] = r;
+        }
+    }
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t i = 0; i < n; ++i) {
+        double tot = 0.0;
+        for (int k = 0; k < S; ++k) {
+            const int64_t a = k * n + i;
+            double xv, vv;
+            if (tau > 0.0) {
+                const double e = exp(-dt / tau);
+                xv = x[a] + dt * R[a] + tau * (v[a] - R[a]) * (1.0 - e);
+                vv = R[a] + (v[a] - R[a]) * e;
+            } else {
+                xv = x[a] + dt * R[a];
+                vv = R[a];
+            }
+            xn[a] = xv;
+            vn[a] = vv;
+            tot += xv;
+            if (!(xv >= -ORC_X_TOL)) bad = 1;
+        }
+        if (!(tot <= 1.0 + ORC_X_TOL)) bad = 1;
+    }
+    if (!bad) {
+        memcpy(x, xn, sizeof(double) * (size_t)(S * n));
+        if (v) memcpy(v, vn, sizeof(double) * (size_t)(S * n));
+    }
+    free(R);
+    free(xn);
+    free(vn);
+    return bad ? ORC_ERR_X_RANGE : ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* FIRE relaxation of (q, sigma) at fixed x (Bitzek et al. 2006), in the one
  * variant this project fixes for both implementations:
  *   y = (q, sigma), force f = -(dF/dq, dF/dsigma), unit masses, v = 0, dt = dt0,
