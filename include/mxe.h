@@ -373,6 +373,36 @@ MXE_API mxe_status mxe_unrolled_grad(mxe_ctx *ctx, mxe_state *state, int32_t n_s
                                      int32_t checkpoint_every, const double *w_dev, double cg_tol, int32_t cg_max,
                                      double *dterm_host, double *dx0_dev, mxe_grad_info *info);
 
+/* Variants of the transport step (Sec. 3: Eq. Transport, Eq. MassTransport).
+ *  host_species = -1: vacancy-mediated exchange, as mxe_diffuse_step.
+ *  host_species = h:  species h is the exchange partner of every other
+ *     species instead of the vacancy (a substitutional alloy whose two
+ *     species are the x and 1 - x of Eq. MassTransport):
+ *       J^k_{i->j} = D_i x_ik x_jh exp(beta_i (m_ik - m_jk)),  m_k = mu_k - mu_h,
+ *     every k atom leaving a site is replaced by an h atom (dx_h = -sum dx_k),
+ *     so each species and each site's occupied total are conserved.
+ *  tau_r > 0: the ballistic term of Eq. Transport, tau_r x'' + x' = R, as
+ *     x' = v, tau_r v' = R - v; over one step R is held at its start value and
+ *     v is integrated exactly:
+ *       v' = R + (v - R) e,  x' = x + dt R + tau_r (v - R)(1 - e),  e = exp(-dt/tau_r)
+ *     (tau_r -> 0 gives the Euler step).  v_dev [S][n] (caller-owned device
+ *     array, in-out) holds the rates; start it at zero (or at R).  With
+ *     tau_r = 0, v_dev may be NULL; if given it receives R.              */
+typedef struct {
+    int32_t host_species;  /* -1: vacancy-mediated */
+    int32_t pad;
+    double tau_r;          /* s; 0: purely diffusive */
+} mxe_transport;
+
+/* One step of the variants above.  opt NULL = vacancy-mediated, tau_r = 0.
+ * mu_ex_dev as in mxe_diffuse_step (NULL: computed first).  x (and v) are
+ * updated only if every x_ik' >= -1e-12 and sum_k x_ik' <= 1 + 1e-12, else
+ * MXE_ERR_X_RANGE and both are unchanged.  Per-system step multipliers of a
+ * batch apply.  Reservoir groups are not combined with the variants
+ * (MXE_ERR_ARG while any is set).  Syncs.                                  */
+MXE_API mxe_status mxe_transport_step(mxe_ctx *ctx, mxe_state *state, const mxe_transport *opt,
+                                      const double *mu_ex_dev, double *v_dev, double dt, double nu0, double Qm);
+
 /* Reservoir groups of the Euler step (Sec. 4: fix setatomicfraction, fix
  * setchemicalpotential; Algorithm 1: applied after the mass-transport step and
  * after the force computation).  fix_mu_mask [n] (nonzero: the site is in the

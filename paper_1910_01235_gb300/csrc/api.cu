@@ -126,6 +126,7 @@ struct mxe_ctx {
   double* dot_part = nullptr;  // partial sums of dot products
   double* dot_out = nullptr;   // [2]
   double* dot_h = nullptr;     // pinned [2]
+  double* v_new = nullptr;     // [S][n] rates after a ballistic transport step (allocated on first use)
   // result of the last relaxation, per system (one entry without a batch)
   std::vector<int32_t> last_iters, last_reason;
   std::vector<double> last_fmax;
@@ -1078,6 +1079,7 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   dfree(c->tan_buf);
+  dfree(c->v_new);
   dfree(c->th_buf);
   dfree(c->th_sum);
   dfree(c->dot_part);
@@ -1420,6 +1422,38 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
 #undef RUN
   CK(cudaStreamSynchronize(st));
   return MXE_OK;
+}
+
+mxe_status mxe_transport_step(mxe_ctx* c, mxe_state* s, const mxe_transport* opt, const double* mu_ex_dev,
+                              double* v_dev, double dt, double nu0, double Qm) {
+  if (!c || !state_ok(c, s) || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm)) return MXE_ERR_ARG;
+  const int host = opt ? opt->host_species : -1;
+  const double tau = opt ? opt->tau_r : 0.0;
+  if (host < -1 || host >= c->S || !(tau >= 0.0) || !std::isfinite(tau)) return MXE_ERR_ARG;
+  if (tau > 0.0 && !v_dev) return MXE_ERR_ARG;
+  if (c->fix_x_mask || c->fix_mu_mask) return MXE_ERR_ARG;  // reservoir groups belong to mxe_diffuse_step
+  if (!c->have_list) return MXE_ERR_STATE;
+  Guard gd(c->device);
+  cudaStream_t st = c->stream;
+  mxe_status pre = mxe_sync_status(c);
+  if (pre != MXE_OK) return pre;
+  const double* mu = mu_ex_dev;
+  if (!mu) {
+    PassArgs A;
+    fill_pass(c, s, A);
+    A.site_E = nullptr;
+    A.gq = nullptr;
+    A.gs = nullptr;
+    mxe_status ms = enqueue_passes(c, s, A, true);
+    if (ms != MXE_OK) return ms;
+    mu = c->mu_ex;
+  }
+  if (v_dev && !c->v_new) CK(dalloc(&c->v_new, (int64_t)c->S * c->n));
+  CK(cudaMemsetAsync(c->step_flags, 0, sizeof(int), st));
+  CK(TIMED("flux_ext", launch_transport_ext(s->x, s->T, mu, c->bd_off, c->bd_idx, c->n, c->S, dt, nu0, Qm, host, tau,
+                                            v_dev, c->v_new, c->x_new, c->step_flags, c->flags,
+                                            c->nsys ? c->dt_sys : nullptr, c->nsys ? c->sys_of : nullptr, st)));
+  return mxe_sync_status(c);
 }
 
 mxe_status mxe_timing_enable(mxe_ctx* c, int32_t enable) {

@@ -153,6 +153,120 @@ __global__ void k_commit(double* __restrict__ x, const double* __restrict__ x_ne
   if (gate && lead) gate->phase = 1;
 }
 
+// ---------------------------------------------------------------- transport variants
+// Host exchange (host >= 0): the exchange partner of species k != host is the
+// host species (a binary alloy without vacancies, where x and 1 - x of Eq.
+// MassTransport are two species): J^k_{a->b} = D_a x_ak x_b,host
+// exp(beta_a (m_ak - m_bk)), m_k = mu_k - mu_host, and R_host = -sum R_k.
+// Ballistic term (tau > 0, Eq. Transport): tau x'' + x' = R as x' = v,
+// tau v' = R - v, integrated over the step with R held:
+//   v' = R + (v - R) e,  x' = x + dt R + tau (v - R)(1 - e),  e = exp(-dt/tau);
+// tau = 0 is the Euler step (v' = R).  Each bond's net exchange is formed in
+// its canonical orientation with explicitly rounded operations, so the two
+// ends cancel exactly, as in k_flux.
+struct Ext {
+  int host;
+  double tau;
+  const double* v;   // [S][n] rates at the start of the step (tau > 0)
+  double* v_new;     // [S][n] (optional)
+  const double* dt_sys;
+  const int* sys_of;
+};
+
+__device__ __forceinline__ double ext_hop(double Da, double xak, double part_b, double beta_a, double ma, double mb) {
+  return __dmul_rn(__dmul_rn(__dmul_rn(Da, xak), part_b), exp(__dmul_rn(beta_a, __dsub_rn(ma, mb))));
+}
+
+template <int S>
+__device__ __forceinline__ double partner(const double* __restrict__ x, int64_t n, int64_t i, int host) {
+  if (host >= 0) return x[host * n + i];
+  double p = 1.0;
+#pragma unroll
+  for (int k = 0; k < S; ++k) p = __dsub_rn(p, x[k * n + i]);
+  return p;
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_flux_ext(const double* __restrict__ x, const double* __restrict__ T,
+                                                  const double* __restrict__ mu, const int* __restrict__ bd_off,
+                                                  const int* __restrict__ bd_idx, int64_t n, double dt, double nu0,
+                                                  double Qm, double* __restrict__ x_new, int* __restrict__ flags,
+                                                  Ext e) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double bi = 1.0 / (kKB * T[i]);
+  const double Di = nu0 * exp(-bi * Qm);
+  const double pi = partner<S>(x, n, i, e.host);
+  double m_i[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) m_i[k] = e.host >= 0 ? __dsub_rn(mu[k * n + i], mu[e.host * n + i]) : mu[k * n + i];
+  double R[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) R[k] = 0.0;
+  for (int t = bd_off[i]; t < bd_off[i + 1]; ++t) {
+    const int64_t j = bd_idx[t];
+    const double bj = 1.0 / (kKB * T[j]);
+    const double Dj = nu0 * exp(-bj * Qm);
+    const double pj = partner<S>(x, n, j, e.host);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      if (k == e.host) continue;
+      const double m_j = e.host >= 0 ? __dsub_rn(mu[k * n + j], mu[e.host * n + j]) : mu[k * n + j];
+      const double xi = x[k * n + i], xj = x[k * n + j];
+      if (i < j) {  // net exchange i -> j, canonical orientation
+        const double net = __dsub_rn(ext_hop(Di, xi, pj, bi, m_i[k], m_j), ext_hop(Dj, xj, pi, bj, m_j, m_i[k]));
+        R[k] = __dsub_rn(R[k], net);
+      } else {      // net exchange j -> i
+        const double net = __dsub_rn(ext_hop(Dj, xj, pi, bj, m_j, m_i[k]), ext_hop(Di, xi, pj, bi, m_i[k], m_j));
+        R[k] = __dadd_rn(R[k], net);
+      }
+    }
+  }
+  if (e.host >= 0) {
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < S; ++k)
+      if (k != e.host) r = __dsub_rn(r, R[k]);
+    R[e.host] = r;
+  }
+  const double dti = e.dt_sys ? dt * e.dt_sys[e.sys_of[i]] : dt;
+  const double ex = e.tau > 0.0 ? exp(-dti / e.tau) : 0.0;
+  double tot = 0.0;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const int64_t a = k * n + i;
+    double xv, vv;
+    if (e.tau > 0.0) {
+      const double dv = e.v[a] - R[k];
+      xv = x[a] + dti * R[k] + e.tau * dv * (1.0 - ex);
+      vv = R[k] + dv * ex;
+    } else {
+      xv = x[a] + dti * R[k];
+      vv = R[k];
+    }
+    x_new[a] = xv;
+    if (e.v_new) e.v_new[a] = vv;
+    tot += xv;
+    ok = ok && (xv >= -kXTol);
+  }
+  ok = ok && (tot <= 1.0 + kXTol);
+  if (!ok) atomicOr(flags, kFlagXRange);
+}
+
+// commit x (and the rates) unless the step failed its range check
+__global__ void k_commit_xv(double* __restrict__ x, const double* __restrict__ x_new, double* __restrict__ v,
+                            const double* __restrict__ v_new, int64_t count, const int* __restrict__ step_flags,
+                            int* __restrict__ flags) {
+  const int sf = *step_flags;
+  if (sf && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, sf);
+  if (sf & kFlagXRange) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  x[t] = x_new[t];
+  if (v) v[t] = v_new[t];
+}
+
 }  // namespace
 
 int64_t flux_scratch_len(int64_t n, int S) { return (3 + 2 * (int64_t)S) * n; }
@@ -195,6 +309,25 @@ cudaError_t launch_commit_x(double* x, const double* x_new, int64_t count, const
                             Ctrl* gate, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   k_commit<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(x, x_new, count, step_flags, flags, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport_ext(double* x, const double* T, const double* mu_ex, const int* bd_off,
+                                 const int* bd_idx, int64_t n, int S, double dt, double nu0, double Qm, int host,
+                                 double tau, double* v, double* v_new, double* x_new, int* step_flags, int* flags,
+                                 const double* dt_sys, const int* sys_of, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (host >= S || (tau > 0.0 && (!v || !v_new))) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  Ext e{host, tau, v, v ? v_new : nullptr, dt_sys, sys_of};
+  switch (S) {
+    case 1: k_flux_ext<1><<<blocks, 256, 0, s>>>(x, T, mu_ex, bd_off, bd_idx, n, dt, nu0, Qm, x_new, step_flags, e); break;
+    case 2: k_flux_ext<2><<<blocks, 256, 0, s>>>(x, T, mu_ex, bd_off, bd_idx, n, dt, nu0, Qm, x_new, step_flags, e); break;
+    default: return cudaErrorInvalidValue;
+  }
+  const int64_t count = (int64_t)S * n;
+  k_commit_xv<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(x, x_new, v, v ? v_new : nullptr,
+                                                             count, step_flags, flags);
   return cudaGetLastError();
 }
 

@@ -264,6 +264,12 @@ cudaError_t launch_flux_res(const double* x, const double* T, const double* mu_e
 cudaError_t launch_flux(const double* x, const double* T, const double* mu_ex, const int* bd_off, const int* bd_idx,
                         int64_t n, int S, double dt, double nu0, double Qm, double* scratch, double* x_new,
                         int* flags, cudaStream_t s);
+// transport variants (host exchange, ballistic term): flux into x_new / v_new
+// and a conditional commit of x and v (x is written through the commit only)
+cudaError_t launch_transport_ext(double* x, const double* T, const double* mu_ex, const int* bd_off,
+                                 const int* bd_idx, int64_t n, int S, double dt, double nu0, double Qm, int host,
+                                 double tau, double* v, double* v_new, double* x_new, int* step_flags, int* flags,
+                                 const double* dt_sys, const int* sys_of, cudaStream_t s);
 // gate (optional): nothing runs while gate->halted; a range error stops the
 // run (gate->reason = error), a commit sets gate->phase = 1
 cudaError_t launch_commit_x(double* x, const double* x_new, int64_t count, const int* step_flags, int* flags,

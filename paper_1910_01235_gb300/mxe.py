@@ -46,6 +46,10 @@ class mxe_state(C.Structure):
                 ("pad", C.c_uint32)]
 
 
+class mxe_transport(C.Structure):
+    _fields_ = [("host_species", C.c_int32), ("pad", C.c_int32), ("tau_r", C.c_double)]
+
+
 class mxe_grad_info(C.Structure):
     _fields_ = [("relax_iters_total", C.c_int32), ("recomputed_steps", C.c_int32),
                 ("cg_iters_total", C.c_int32), ("cg_iters_max", C.c_int32), ("cg_resid_max", C.c_double)]
@@ -62,7 +66,7 @@ EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy",
            "mxe_sync_status", "mxe_relax", "mxe_relax_info", "mxe_diffuse_step", "mxe_diffuse_step_async",
            "mxe_diffuse_step_noalloc", "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs",
            "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape",
-           "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad"]
+           "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad", "mxe_transport_step"]
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
 
@@ -99,6 +103,7 @@ def lib():
             L.mxe_potential_terms.argtypes = [p, i32p, i32p, p, p, p]
             L.mxe_tangent.argtypes = [p, p] + [p] * 10
             L.mxe_flux_vjp.argtypes = [p, p, p, d, d, d, p, p, p]
+            L.mxe_transport_step.argtypes = [p, p, p, p, p, d, d, d]
             L.mxe_unrolled_grad.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.c_int32, p, d, C.c_int32,
                                             p, p, p]
             L.mxe_destroy.argtypes = [p]
@@ -198,6 +203,12 @@ def mxe_tangent(ctx, state, dq, dsigma, dx, gq, gs, mu, gq_t, gs_t, mu_t, dterm)
     """All arguments after the state are device pointers (0 = none)."""
     return lib().mxe_tangent(ctx, C.byref(state), *[C.c_void_p(v or 0) for v in
                                                     (dq, dsigma, dx, gq, gs, mu, gq_t, gs_t, mu_t, dterm)])
+
+
+def mxe_transport_step(ctx, state, host, tau, mu_ex_ptr, v_ptr, dt, nu0, Qm):
+    opt = mxe_transport(int(host), 0, float(tau))
+    return lib().mxe_transport_step(ctx, C.byref(state), C.byref(opt), C.c_void_p(mu_ex_ptr or 0),
+                                    C.c_void_p(v_ptr or 0), float(dt), float(nu0), float(Qm))
 
 
 def mxe_flux_vjp(ctx, state, mu_ex, dt, nu0, Qm, xbar_next, xbar, mubar):
@@ -413,6 +424,13 @@ class MxeSystem:
                               self.sys.nu0 if nu0 is None else nu0, self.sys.Qm if Qm is None else Qm,
                               asynchronous)
         return self._check(st, "mxe_diffuse_step", allow)
+
+    def transport_step(self, dt, host=-1, tau=0.0, v=None, mu_ex=None, nu0=None, Qm=None, allow=()):
+        """One step of the transport variants (mxe_transport_step): exchange
+        with a host species and/or the ballistic term; v: [S, n] rates."""
+        st = mxe_transport_step(self.ctx, self.state, host, tau, _ptr(mu_ex), _ptr(v), dt,
+                                self.sys.nu0 if nu0 is None else nu0, self.sys.Qm if Qm is None else Qm)
+        return self._check(st, "mxe_transport_step", allow)
 
     def set_reservoirs(self, fix_x=None, fix_mu=None):
         """fix_x / fix_mu: (mask [n] bool, values [S, n]) numpy arrays or None
