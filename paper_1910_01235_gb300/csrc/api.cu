@@ -75,6 +75,11 @@ struct mxe_ctx {
   bool have_list = false;
   double r_list = 0, skin = 0.2, r_bond = 0, sigma_max_build = 0;
   double* q_build = nullptr;
+  // unordered-pair index and records of the half-list float-float passes
+  int *first_gt = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
+  int *pair_i = nullptr, *pair_t = nullptr, *pid = nullptr;           // [pairs], [pairs], [entries]
+  float2* pair_buf = nullptr;                                         // [pairs][pair_record_len]
+  int64_t pair_cap = 0, n_upairs = 0;
 
   // per-site work arrays
   double *rho_bar = nullptr, *rho_avg = nullptr, *a = nullptr, *b = nullptr, *e = nullptr;
@@ -490,6 +495,18 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     CK(dalloc(&c->nb_ent, cap));
     c->nb_cap = cap;
   }
+  if (c->precision == MXE_FP32_FF && (npairs > c->pair_cap || !c->pid)) {
+    dfree(c->pid);
+    dfree(c->pair_i);
+    dfree(c->pair_t);
+    dfree(c->pair_buf);
+    const int64_t cap = std::max<int64_t>(c->nb_cap, npairs);
+    CK(dalloc(&c->pid, cap));
+    CK(dalloc(&c->pair_i, cap / 2 + 64));
+    CK(dalloc(&c->pair_t, cap / 2 + 64));
+    CK(dalloc(&c->pair_buf, (cap / 2 + 64) * (int64_t)pair_record_len(c->dp)));
+    c->pair_cap = cap;
+  }
   if (nbonds > c->bd_cap) {
     dfree(c->bd_idx);
     int64_t cap = nbonds + nbonds / 8 + 64;
@@ -506,6 +523,14 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     CK(TIMED("build_fill", launch_nbr_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, g, B, c->cell_of,
                                            c->cell_start, c->cell_sites, c->abs_cell, rl2, rb2, band, c->nb_off,
                                            c->nb_ent, c->bd_off, c->bd_idx, max_row, st)));
+  }
+  if (c->precision == MXE_FP32_FF) {
+    if (npairs % 2) return MXE_ERR_NBR_OVERFLOW;  // a symmetric list has every pair twice
+    CK(TIMED("build_misc", launch_pair_count(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_cnt, st)));
+    CK(TIMED("build_misc", launch_scan(c->pair_cnt, c->pair_off, n, c->totals + 3, (int*)c->scan_tmp, c->scan_len, st)));
+    CK(TIMED("build_misc", launch_pair_fill(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_off, npairs / 2, c->pair_i,
+                                            c->pair_t, c->pid, c->flags, st)));
+    c->n_upairs = npairs / 2;
   }
   CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
   c->n_pairs = npairs;
@@ -542,9 +567,15 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
     CK(TIMED(cls_name("gradient", c->precision, kGradForce), launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st)));
     return MXE_OK;
   }
-  const int acc = ffm ? 3 : 0;  // precision of the chemical-potential passes
-  CK(TIMED(cls_name("density", acc), launch_density(acc, c->nl, c->dp, c->grid, A, st)));
-  CK(TIMED(cls_name("gradient", acc, kGradMu), launch_gradient(acc, kGradMu, c->nl, c->dp, c->grid, A, st)));
+  if (ffm) {
+    // float-float: pair averages once per unordered pair, then per-site gathers
+    CK(TIMED("pair_ff", launch_pair_ff(c->dp, c->grid, A, c->pair_i, c->pair_t, c->n_upairs, c->pair_buf, st)));
+    CK(TIMED("density_gather_ff", launch_pair_gather(false, c->nl, c->dp, A, c->pid, c->pair_buf, c->n_upairs, st)));
+    CK(TIMED("mu_gather_ff", launch_pair_gather(true, c->nl, c->dp, A, c->pid, c->pair_buf, c->n_upairs, st)));
+  } else {
+    CK(TIMED(cls_name("density", 0), launch_density(0, c->nl, c->dp, c->grid, A, st)));
+    CK(TIMED(cls_name("gradient", 0, kGradMu), launch_gradient(0, kGradMu, c->nl, c->dp, c->grid, A, st)));
+  }
   if (!ffm) CK(TIMED("pack_ab", launch_pack_ab(c->a, c->b, c->n, c->S, c->ab32, st)));  // the float-float pass packs them itself
   if (A.gq != nullptr || A.gs != nullptr) {
     PassArgs F = A;
@@ -1001,6 +1032,9 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
     A(dalloc(&c->ab32, 2 * n));
   }
   if (precision == MXE_FP32_FF) {
+    A(dalloc(&c->first_gt, n));
+    A(dalloc(&c->pair_cnt, n));
+    A(dalloc(&c->pair_off, n + 1));
     A(dalloc(&c->pos32lo, n));
     A(dalloc(&c->x32lo, n));
     A(dalloc(&c->ab32lo, 2 * n));
@@ -1079,6 +1113,13 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   dfree(c->tan_buf);
+  dfree(c->first_gt);
+  dfree(c->pair_cnt);
+  dfree(c->pair_off);
+  dfree(c->pair_i);
+  dfree(c->pair_t);
+  dfree(c->pid);
+  dfree(c->pair_buf);
   dfree(c->v_new);
   dfree(c->th_buf);
   dfree(c->th_sum);

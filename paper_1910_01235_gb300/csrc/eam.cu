@@ -773,6 +773,289 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
   if (flag) atomicOr(A.flags, flag);
 }
 
+// ---------------------------------------------------------------- half-list float-float passes
+// The averages <phi_u>_ij, <f_v>_ij and the static f_v(r_ij) of a pair depend
+// only on its geometry and are the same from both ends (the node set of
+// App. A is symmetric in i and j).  k_pair_ff evaluates them once per
+// unordered pair (one thread per pair) into a record of C float pairs:
+// [f_v static (n_f) | sum over the 12 nodes of f_v (n_f) | of phi_u (n_phi)];
+// k_pair_density / k_pair_mu gather the records over every site's full row
+// (entry t -> pair pid[t]) and finish exactly as the float-float density
+// and chemical-potential passes do.
+template <int S>
+__global__ void __launch_bounds__(128) k_pair_ff(DevPot P, DevGrid g0, PassArgs A, const int* __restrict__ pair_i,
+                                                 const int* __restrict__ pair_t, int64_t npair,
+                                                 float2* __restrict__ buf, int C) {
+  using R = ff;
+  constexpr int NF = S * S;
+  constexpr int NP = S * (S + 1) / 2;
+  if (chunk_halted(A)) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int64_t i = pair_i[p];
+  const int tp = pair_t[p];
+  if (i < 0 || i >= A.n || tp < A.nb_off[i] || tp >= A.nb_off[i + 1]) {  // index not built for this list
+    atomicOr(A.flags, kFlagOverflow);
+    return;
+  }
+  const uint32_t ent = A.nb_ent[tp];
+  const int64_t j = ent & kIdxMask;
+  const DevGrid gs = site_grid(g0, A.batch, i);
+  SiteData<3, S> si, sj;
+  load_site(A, i, si);
+  load_site(A, j, sj);
+  R d[3];
+  separation(gs, si, sj, ent >> kCodeShift, d);
+  const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
+  const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  int bad = D2 < (R)(kRMin * kRMin);
+  R fst[NF], fav[NF], aph[NP];
+  {
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+#pragma unroll
+    for (int v = 0; v < NF; ++v) {
+      fst[v] = v < P.n_f ? rad_raw(P.f[v], r) * Sw : (R)0;
+      fav[v] = (R)0;
+    }
+#pragma unroll
+    for (int u = 0; u < NP; ++u) aph[u] = (R)0;
+  }
+#pragma unroll 1
+  for (int site = 0; site < 2; ++site) {
+    const R s = site == 0 ? s_i : s_j;
+    const R base = D2 + s * s;
+#pragma unroll 1
+    for (int a = 0; a < 3; ++a) {
+      const R tw = (R)2 * s * d[a];
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        const R r2 = pm == 0 ? base + tw : base - tw;
+        R r, rinv, Sw, dS;
+        r_from_r2(r2, r, rinv);
+        bad |= r2 < (R)(kRMin * kRMin);
+        sw(P, r, Sw, dS);
+#pragma unroll
+        for (int u = 0; u < NP; ++u)
+          if (u < P.n_phi) aph[u] += rad_raw(P.phi[u], r) * Sw;
+#pragma unroll
+        for (int v = 0; v < NF; ++v)
+          if (v < P.n_f) fav[v] += rad_raw(P.f[v], r) * Sw;
+      }
+    }
+  }
+  float2* o = buf + p * (int64_t)C;
+#pragma unroll
+  for (int v = 0; v < NF; ++v)
+    if (v < P.n_f) {
+      o[v] = make_float2(fst[v].hi, fst[v].lo);
+      o[P.n_f + v] = make_float2(fav[v].hi, fav[v].lo);
+    }
+#pragma unroll
+  for (int u = 0; u < NP; ++u)
+    if (u < P.n_phi) o[2 * P.n_f + u] = make_float2(aph[u].hi, aph[u].lo);
+  if (bad) atomicOr(A.flags, kFlagGeometry);
+}
+
+__device__ __forceinline__ ff ld_ff(const float2* __restrict__ rec, int c) {
+  const float2 v = __ldg(&rec[c]);
+  return ff(v.x, v.y);
+}
+
+template <int S, int NL>
+__global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, const int* __restrict__ pid,
+                                                      const float2* __restrict__ buf, int C, int64_t npair) {
+  using R = ff;
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  AccD rb[S], ra[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    rb[k].zero();
+    ra[k].zero();
+  }
+  if (active) {
+    const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+    for (int t = beg + lane; t < end; t += NL) {
+      const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
+      const int pp = __ldg(&pid[t]);
+      if (pp < 0 || pp >= npair) {
+        atomicOr(A.flags, kFlagOverflow);
+        continue;
+      }
+      const float2* rec = buf + (int64_t)pp * C;
+      SiteData<3, S> sj;
+      const float4 X = __ldg(&A.x32[j]), Xl = __ldg(&A.x32lo[j]);
+      const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
+#pragma unroll
+      for (int k = 0; k < S; ++k) sj.x[k] = ff(xs[k], xl[k]);
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        R sb = (R)0, sa = (R)0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const int v = P.f_of[k][l];
+          if (v < 0) continue;
+          sb += sj.x[l] * ld_ff(rec, v);
+          sa += sj.x[l] * ld_ff(rec, P.n_f + v);
+        }
+        rb[k].add(sb);
+        ra[k].add(sa);
+      }
+    }
+  }
+  if (NL > 1) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      rb[k].team_reduce(NL);
+      ra[k].team_reduce(NL);
+    }
+  }
+  if (!active || lane != 0) return;
+  const int64_t n = A.n;
+  int flag = 0;
+  float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const double rbar = rb[k].get();
+    const double ravg = ra[k].get() * (1.0 / 12.0);
+    const double xk = A.x[k * n + i];
+    double e = 0.0, ak = 0.0, bk = 0.0;
+    if (rbar > kRhoMin) {
+      const double sq = sqrt(rbar);
+      const double F = -P.E[k] * sq;
+      const double dF = -P.E[k] / (2.0 * sq);
+      const double d2F = P.E[k] / (4.0 * rbar * sq);
+      e = F + dF * (ravg - rbar);
+      ak = xk * d2F * (ravg - rbar);
+      bk = xk * dF;
+    } else {
+      flag |= kFlagGeometry;
+    }
+    A.rho_bar[k * n + i] = rbar;
+    A.rho_avg[k * n + i] = ravg;
+    A.e[k * n + i] = e;
+    A.a[k * n + i] = ak;
+    A.b[k * n + i] = bk;
+    ab[2 * k] = (float)ak;
+    ab[2 * k + 1] = (float)bk;
+    if (k < 2) {
+      lo[2 * k] = (float)(ak - (double)ab[2 * k]);
+      lo[2 * k + 1] = (float)(bk - (double)ab[2 * k + 1]);
+    }
+  }
+  A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
+  A.ab32lo[2 * i] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+  if (flag) atomicOr(A.flags, flag);
+}
+
+template <int S, int NL>
+__global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int* __restrict__ pid,
+                                                 const float2* __restrict__ buf, int C, int64_t npair) {
+  using R = ff;
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  AccD mu[S], epair;
+  epair.zero();
+#pragma unroll
+  for (int k = 0; k < S; ++k) mu[k].zero();
+  if (active) {
+    SiteData<3, S> si;
+    {
+      const float4 X = __ldg(&A.x32[i]), Xl = __ldg(&A.x32lo[i]);
+      const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
+#pragma unroll
+      for (int k = 0; k < S; ++k) si.x[k] = ff(xs[k], xl[k]);
+    }
+    const R inv12 = (R)(1.0 / 12.0);
+    const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+    for (int t = beg + lane; t < end; t += NL) {
+      const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
+      const int pp = __ldg(&pid[t]);
+      if (pp < 0 || pp >= npair) {
+        atomicOr(A.flags, kFlagOverflow);
+        continue;
+      }
+      const float2* rec = buf + (int64_t)pp * C;
+      SiteData<3, S> sj;
+      {
+        const float4 X = __ldg(&A.x32[j]), Xl = __ldg(&A.x32lo[j]);
+        const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
+#pragma unroll
+        for (int k = 0; k < S; ++k) sj.x[k] = ff(xs[k], xl[k]);
+      }
+      R aj[S], bj[S];
+      load_ab(A, j, aj, bj, (SiteData<3, S>*)nullptr);
+      R ep = (R)0;
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        R m = (R)0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const int u = P.phi_of[k][l];
+          if (u >= 0) {
+            const R ph = ld_ff(rec, 2 * P.n_f + u);
+            m += sj.x[l] * ph * inv12;
+            ep += si.x[k] * sj.x[l] * ph;
+          }
+          // density at j of species l from this site holding species k: f_lk
+          const int v = P.f_of[l][k];
+          if (v >= 0) m += aj[l] * ld_ff(rec, v) + bj[l] * ld_ff(rec, P.n_f + v) * inv12;
+        }
+        mu[k].add(m);
+      }
+      epair.add((R)0.5 * inv12 * ep);
+    }
+  }
+  if (NL > 1) {
+    epair.team_reduce(NL);
+#pragma unroll
+    for (int k = 0; k < S; ++k) mu[k].team_reduce(NL);
+  }
+  if (!active || lane != 0) return;
+  const int64_t n = A.n;
+  const double kT = kKB * A.T[i];
+  const double sg = A.sigma[i];
+  bool finite = true;
+  double xv = 1.0;
+#pragma unroll
+  for (int k = 0; k < S; ++k) xv -= A.x[k * n + i];
+  const double lv = log(fmax(xv, kLogFloor));
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const double m = mu[k].get() + A.e[k * n + i];
+    finite = finite && isfinite(m);
+    if (A.mu_ex) A.mu_ex[k * n + i] = m;
+    if (A.mu) A.mu[k * n + i] = m + kT * (log(fmax(A.x[k * n + i], kLogFloor)) - lv);
+  }
+  if (A.site_E) {
+    double xr = 1.0, mix = 0.0, emb = 0.0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const double xk = A.x[k * n + i];
+      xr -= xk;
+      if (xk > 0.0) mix += xk * log(xk);
+      emb += xk * A.e[k * n + i];
+    }
+    if (xr > 0.0) mix += xr * log(xr);
+    const double EV = epair.get() + emb;
+    const double Fv = -3.0 * kT * log(sg);
+    const double Fm = kT * mix;
+    A.site_E[i] = EV;
+    A.site_E[n + i] = Fv;
+    A.site_E[2 * n + i] = Fm;
+    finite = finite && isfinite(EV) && isfinite(Fv) && isfinite(Fm);
+  }
+  if (!finite) atomicOr(A.flags, kFlagNonfinite);
+}
+
 // ---------------------------------------------------------------- K7: pack
 __global__ void k_pack(const double* __restrict__ q, const double* __restrict__ sigma, const double* __restrict__ x,
                        const int* __restrict__ abs_cell, int64_t n, int S, DevGrid g0, Batch B,
@@ -1003,6 +1286,54 @@ cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, d
   if (B.nsys <= 0) return cudaSuccess;
   k_energy_seg<<<(unsigned)B.nsys, 256, 0, s>>>(site_E, n, B.sys_off, F4);
   return cudaGetLastError();
+}
+
+int pair_record_len(const DevPot& P) { return (2 * P.n_f + P.n_phi + 3) & ~3; }
+
+cudaError_t launch_pair_ff(const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i, const int* pair_t,
+                           int64_t npair, float2* buf, cudaStream_t s) {
+  if (npair == 0) return cudaSuccess;
+  const int C = pair_record_len(P);
+  const unsigned blocks = (unsigned)((npair + 127) / 128);
+  switch (P.S) {
+    case 1: k_pair_ff<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, buf, C); break;
+    case 2: k_pair_ff<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, buf, C); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+template <int S, int NL>
+cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf, int C,
+                          int64_t npair, cudaStream_t s) {
+  const int threads = A.tpb > 0 ? A.tpb : 256;
+  const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
+  if (mu) k_pair_mu<S, NL><<<blocks, threads, 0, s>>>(P, A, pid, buf, C, npair);
+  else k_pair_density<S, NL><<<blocks, threads, 0, s>>>(P, A, pid, buf, C, npair);
+  return cudaGetLastError();
+}
+template <int S>
+cudaError_t pair_gather_s(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
+                          int C, int64_t npair, cudaStream_t s) {
+  switch (nl) {
+    case 4: return pair_gather_t<S, 4>(mu, P, A, pid, buf, C, npair, s);
+    case 8: return pair_gather_t<S, 8>(mu, P, A, pid, buf, C, npair, s);
+    case 16: return pair_gather_t<S, 16>(mu, P, A, pid, buf, C, npair, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
+                               int64_t npair, cudaStream_t s) {
+  if (A.n == 0) return cudaSuccess;
+  const int C = pair_record_len(P);
+  switch (P.S) {
+    case 1: return pair_gather_s<1>(mu, nl, P, A, pid, buf, C, npair, s);
+    case 2: return pair_gather_s<2>(mu, nl, P, A, pid, buf, C, npair, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace mxe

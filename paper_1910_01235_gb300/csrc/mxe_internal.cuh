@@ -150,6 +150,15 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
                              const int* abs_cell, double rl2, double rb2, float band, int cand_cap,
                              const int* nb_off, uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row,
                              int* flags, cudaStream_t s);
+// unordered-pair index of a symmetric list: first_gt[i] = first entry of row i
+// with j > i, cnt[i] = entries from there to the row's end; after a scan of
+// cnt into pair_off: pair p = (pair_i[p], entry pair_t[p]), and pid[t] = the
+// pair of every entry t (kFlagOverflow if the list is not symmetric)
+cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* first_gt, int* cnt,
+                              cudaStream_t s);
+cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
+                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pid, int* flags,
+                             cudaStream_t s);
 // exclusive scan of n int32 counts into out[0..n] (out[n] = total, int64 total in *total64)
 cudaError_t launch_scan(const int* in, int* out, int64_t n, long long* total64, int* tmp, int64_t tmp_len,
                         cudaStream_t s);
@@ -202,6 +211,13 @@ cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid
 enum { kGradAll = 0, kGradForce = 1, kGradMu = 2, kGradForceNoE = 3 };
 cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                             cudaStream_t s);
+// half-list float-float passes: records of pair_record_len(P) float pairs per
+// unordered pair, then the density (mu = false) or chemical-potential gather
+int pair_record_len(const DevPot& P);
+cudaError_t launch_pair_ff(const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i, const int* pair_t,
+                           int64_t npair, float2* buf, cudaStream_t s);
+cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
+                               int64_t npair, cudaStream_t s);
 cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s);
 // batches: F4 [nsys][4], one block per system in a fixed order

@@ -589,6 +589,63 @@ __global__ void k_segment_ids(const int* __restrict__ base, int nseg, int64_t co
   out[t] = lo;
 }
 
+// ---------------------------------------------------------------- pair index
+// Rows are sorted by j, so the entries of row i with j > i (each unordered
+// pair once, in the row of its lower-index site) are the tail of the row.
+__device__ __forceinline__ int first_above(const uint32_t* __restrict__ ent, int beg, int end, uint32_t i) {
+  int lo = beg, hi = end;  // first t in [beg, end) with (ent[t] & mask) > i
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((ent[mid] & kIdxMask) > i) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__global__ void k_pair_count(const int* __restrict__ nb_off, const uint32_t* __restrict__ nb_ent, int64_t n,
+                             int* __restrict__ first_gt, int* __restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int beg = nb_off[i], end = nb_off[i + 1];
+  const int fg = first_above(nb_ent, beg, end, (uint32_t)i);
+  first_gt[i] = fg;
+  cnt[i] = end - fg;
+}
+
+__global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __restrict__ nb_ent, int64_t n,
+                            const int* __restrict__ first_gt, const int* __restrict__ pair_off, int64_t npair,
+                            int* __restrict__ pair_i, int* __restrict__ pair_t, int* __restrict__ pid,
+                            int* __restrict__ flags) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0 && pair_off[n] != npair) atomicOr(flags, kFlagOverflow);  // lists must be symmetric
+  if (i >= n) return;
+  const int beg = nb_off[i], end = nb_off[i + 1], fg = first_gt[i];
+  for (int t = beg; t < end; ++t) {
+    const int64_t j = nb_ent[t] & kIdxMask;
+    if (t >= fg) {
+      const int p = pair_off[i] + (t - fg);
+      if (p < npair) {
+        pair_i[p] = (int)i;
+        pair_t[p] = t;
+        pid[t] = p;
+      } else {
+        pid[t] = 0;
+        atomicOr(flags, kFlagOverflow);
+      }
+    } else {
+      // the pair's owner entry: i in row j (j < i), in the tail of row j
+      const int jb = first_gt[j], je = nb_off[j + 1];
+      const int t2 = first_above(nb_ent, jb, je, (uint32_t)i) - 1;
+      if (t2 >= jb && (nb_ent[t2] & kIdxMask) == (uint32_t)i && pair_off[j] + (t2 - jb) < npair) {
+        pid[t] = pair_off[j] + (t2 - jb);
+      } else {
+        pid[t] = 0;
+        atomicOr(flags, kFlagOverflow);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, const Batch& B, int* cell_of,
@@ -708,6 +765,22 @@ cudaError_t launch_segment_ids(const int* base, int nseg, int64_t count, int* ou
   if (count <= 0) return cudaSuccess;
   if (nseg <= 0) return cudaErrorInvalidValue;
   k_segment_ids<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(base, nseg, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* first_gt, int* cnt,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_pair_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, first_gt, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
+                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pid, int* flags,
+                             cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_pair_fill<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(nb_off, nb_ent, n, first_gt, pair_off, npair, pair_i,
+                                                          pair_t, pid, flags);
   return cudaGetLastError();
 }
 
