@@ -155,7 +155,15 @@ def ops_per_pair(kernel, n_phi, n_f, S):
         return 13 * (node + term * n_f) + 300
     if kernel.startswith("gradient_ff"):
         return 12 * (node + term * (n_phi + n_f)) + (node + term * n_f) + 500
+    if kernel == "pair_ff":                 # once per unordered pair: 12 nodes x all terms + static f
+        return 12 * (node + term * (n_phi + n_f)) + (node + term * n_f) + 60
     return None
+
+
+def units_per_launch(kernel, entries):
+    """Units the ops count applies to: the half-list kernels evaluate each
+    unordered pair once, the full-list kernels each neighbour entry."""
+    return entries // 2 if kernel == "pair_ff" else entries
 
 
 def peak_fp32_ops(clock_mhz=2070.0):
@@ -347,7 +355,7 @@ def run_ours(args):
     opp = ops_per_pair(dom, n_phi, n_f, sys0.S) if dom else None
     peak_ops = peak_fp32_ops()
     if dom and opp:
-        ops_launch = npairs * opp
+        ops_launch = units_per_launch(dom, npairs) * opp
         achieved = ops_launch / (shares[dom]["avg_ms"] / 1e3) / 1e12
     else:
         ops_launch, achieved = None, None
@@ -381,6 +389,10 @@ def run_ours(args):
                      "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)",
                      "kernel_avg_ms": shares[dom]["avg_ms"] if dom else None,
                      "ops_per_launch": ops_launch,
+                     "ops_basis": ("per unordered pair" if dom == "pair_ff" else
+                                   "per neighbour entry (full list: each unordered pair evaluated from both ends)"),
+                     "frac_half_list": ((achieved / (peak_ops / 1e12)) * (1.0 if dom == "pair_ff" else 0.5))
+                                       if achieved else None,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"},
         "clocks": clocks,
         "gpu_launches": None,

@@ -140,7 +140,8 @@ __device__ __forceinline__ void r_from_r2(ff r2, ff& r, ff& rinv) {
 
 // quintic switch S(r) and dS/dr
 __device__ __forceinline__ void sw(const DevPot& P, float r, float& S, float& dS) {
-  float t = fminf(fmaxf((r - P.rs_f) * P.inv_w_f, 0.f), 1.f);
+  // clamp to [0, 1] as a saturating multiply (no separate min/max)
+  float t = __saturatef((r - P.rs_f) * P.inv_w_f);
   float t2 = t * t;
   float u = 1.f - t;
   S = fmaf(t2 * t, fmaf(t, fmaf(-6.f, t, 15.f), -10.f), 1.f);
@@ -366,6 +367,12 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
       separation(gs, si, sj, ent >> kCodeShift, d);
       const R s_j = sqrt6<R>() * sj.sig;
       const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      // every node lies at least |d| - max(s_i, s_j) from the origin site:
+      // only a pair closer than 0.5 A + that shift needs its nodes checked
+      constexpr bool kNodeCheck = PREC == 0 || PREC == 3;
+      const R s_max = s_i < s_j ? s_j : s_i;
+      const R near = (R)kRMin + s_max;
+      const bool close = D2 < near * near;
       R fst[NF], fav[NF];
       // static point
       {
@@ -394,11 +401,21 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
             const R r2 = pm == 0 ? base + tw : base - tw;
             R r, rinv, Sw, dS;
             r_from_r2(r2, r, rinv);
-            bad |= r2 < (R)(kRMin * kRMin);
+            if (kNodeCheck) bad |= r2 < (R)(kRMin * kRMin);
             sw(P, r, Sw, dS);
 #pragma unroll
             for (int v = 0; v < NF; ++v)
               if (v < P.n_f) fav[v] += rad_raw(P.f[v], r) * Sw;
+          }
+        }
+      }
+      if (!kNodeCheck && close) {  // rare: the exact node distances
+        for (int site = 0; site < 2; ++site) {
+          const R s = site == 0 ? s_i : s_j;
+          for (int a = 0; a < 3; ++a) {
+            const R base = D2 + s * s, tw = (R)2 * s * d[a];
+            bad |= (base + tw) < (R)(kRMin * kRMin);
+            bad |= (base - tw) < (R)(kRMin * kRMin);
           }
         }
       }
@@ -858,6 +875,21 @@ __global__ void __launch_bounds__(128) k_pair_ff(DevPot P, DevGrid g0, PassArgs 
   if (bad) atomicOr(A.flags, kFlagGeometry);
 }
 
+// per-site sums of the gathers in float-float on the FP32 pipe (a conversion
+// to FP64 per term would load GB300's slow FP64 pipe)
+struct AccF2 {
+  ff v;
+  __device__ __forceinline__ void zero() { v = ff(0.f, 0.f); }
+  __device__ __forceinline__ void add(ff x) { v = v + x; }
+  __device__ __forceinline__ double get() const { return ff_to_double(v); }
+  __device__ __forceinline__ void team_reduce(int nl) {
+    for (int o = nl >> 1; o > 0; o >>= 1) {
+      const ff w(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+      v = v + w;
+    }
+  }
+};
+
 __device__ __forceinline__ ff ld_ff(const float2* __restrict__ rec, int c) {
   const float2 v = __ldg(&rec[c]);
   return ff(v.x, v.y);
@@ -872,7 +904,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
   const int64_t i = tid / NL;
   const int lane = (int)(tid % NL);
   const bool active = i < A.n;
-  AccD rb[S], ra[S];
+  AccF2 rb[S], ra[S];
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     rb[k].zero();
@@ -962,7 +994,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
   const int64_t i = tid / NL;
   const int lane = (int)(tid % NL);
   const bool active = i < A.n;
-  AccD mu[S], epair;
+  AccF2 mu[S], epair;
   epair.zero();
 #pragma unroll
   for (int k = 0; k < S; ++k) mu[k].zero();

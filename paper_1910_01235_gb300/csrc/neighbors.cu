@@ -616,11 +616,14 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
                             const int* __restrict__ first_gt, const int* __restrict__ pair_off, int64_t npair,
                             int* __restrict__ pair_i, int* __restrict__ pair_t, int* __restrict__ pid,
                             int* __restrict__ flags) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i == 0 && pair_off[n] != npair) atomicOr(flags, kFlagOverflow);  // lists must be symmetric
-  if (i >= n) return;
+  // one warp per row, lanes over its entries
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w == 0 && lane == 0 && pair_off[n] != npair) atomicOr(flags, kFlagOverflow);  // lists must be symmetric
+  if (w >= n) return;
+  const int64_t i = w;
   const int beg = nb_off[i], end = nb_off[i + 1], fg = first_gt[i];
-  for (int t = beg; t < end; ++t) {
+  for (int t = beg + lane; t < end; t += 32) {
     const int64_t j = nb_ent[t] & kIdxMask;
     if (t >= fg) {
       const int p = pair_off[i] + (t - fg);
@@ -779,8 +782,8 @@ cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t 
                              const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pid, int* flags,
                              cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_pair_fill<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(nb_off, nb_ent, n, first_gt, pair_off, npair, pair_i,
-                                                          pair_t, pid, flags);
+  k_pair_fill<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, first_gt, pair_off, npair,
+                                                               pair_i, pair_t, pid, flags);
   return cudaGetLastError();
 }
 
