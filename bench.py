@@ -157,13 +157,18 @@ def ops_per_pair(kernel, n_phi, n_f, S):
         return 12 * (node + term * (n_phi + n_f)) + (node + term * n_f) + 500
     if kernel == "pair_ff":                 # once per unordered pair: 12 nodes x all terms + static f
         return 12 * (node + term * (n_phi + n_f)) + (node + term * n_f) + 60
+    if kernel == "pair32_density":          # the FP32 density terms of one unordered pair (13 points)
+        return 13 * (2 + 7 + 2 * n_f) + 20
+    if kernel == "pair32_force":            # the FP32 forces of one unordered pair, both width derivatives
+        node = 2 + 11 + 3 * (n_phi + n_f) + 3 + 4.25 + 2
+        return 12 * node + (2 + 11 + 4 * n_f + 1) + (20 + S * S + 4 * S * S + (n_phi + n_f) + 9 + 24)
     return None
 
 
 def units_per_launch(kernel, entries):
     """Units the ops count applies to: the half-list kernels evaluate each
     unordered pair once, the full-list kernels each neighbour entry."""
-    return entries // 2 if kernel == "pair_ff" else entries
+    return entries // 2 if kernel.startswith("pair") else entries
 
 
 def peak_fp32_ops(clock_mhz=2070.0):
@@ -389,9 +394,9 @@ def run_ours(args):
                      "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)",
                      "kernel_avg_ms": shares[dom]["avg_ms"] if dom else None,
                      "ops_per_launch": ops_launch,
-                     "ops_basis": ("per unordered pair" if dom == "pair_ff" else
+                     "ops_basis": ("per unordered pair" if dom.startswith("pair") else
                                    "per neighbour entry (full list: each unordered pair evaluated from both ends)"),
-                     "frac_half_list": ((achieved / (peak_ops / 1e12)) * (1.0 if dom == "pair_ff" else 0.5))
+                     "frac_half_list": ((achieved / (peak_ops / 1e12)) * (1.0 if dom.startswith("pair") else 0.5))
                                        if achieved else None,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"},
         "clocks": clocks,

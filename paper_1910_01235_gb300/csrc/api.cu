@@ -79,6 +79,8 @@ struct mxe_ctx {
   int *first_gt = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
   int *pair_i = nullptr, *pair_t = nullptr, *pid = nullptr;           // [pairs], [pairs], [entries]
   float2* pair_buf = nullptr;                                         // [pairs][pair_record_len]
+  float4 *pair_dens = nullptr, *pair_frc = nullptr;                   // [pairs] FP32 relaxation records
+  float* pair_gsj = nullptr;                                          // [pairs]
   int64_t pair_cap = 0, n_upairs = 0;
 
   // per-site work arrays
@@ -505,6 +507,12 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     CK(dalloc(&c->pair_i, cap / 2 + 64));
     CK(dalloc(&c->pair_t, cap / 2 + 64));
     CK(dalloc(&c->pair_buf, (cap / 2 + 64) * (int64_t)pair_record_len(c->dp)));
+    dfree(c->pair_dens);
+    dfree(c->pair_frc);
+    dfree(c->pair_gsj);
+    CK(dalloc(&c->pair_dens, cap / 2 + 64));
+    CK(dalloc(&c->pair_frc, cap / 2 + 64));
+    CK(dalloc(&c->pair_gsj, cap / 2 + 64));
     c->pair_cap = cap;
   }
   if (nbonds > c->bd_cap) {
@@ -623,8 +631,20 @@ void relax_pass_args(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
 mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
   cudaStream_t st = c->stream;
   const int64_t n = c->n;
-  CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
-  CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
+  if (c->precision == MXE_FP32_FF && c->pid && relax32_pairs_supported(c->dp)) {
+    // each unordered pair once: pair kernel, then the per-site gather
+    CK(TIMED("pair32_density", launch_relax32_pair(false, c->dp, c->grid, A, c->pair_i, c->pair_t, c->n_upairs,
+                                                    c->pair_dens, c->pair_frc, c->pair_gsj, st)));
+    CK(TIMED("gather32_density", launch_relax32_gather(false, c->nl, c->dp, A, c->pid, c->n_upairs, c->pair_dens,
+                                                        c->pair_frc, c->pair_gsj, st)));
+    CK(TIMED("pair32_force", launch_relax32_pair(true, c->dp, c->grid, A, c->pair_i, c->pair_t, c->n_upairs,
+                                                  c->pair_dens, c->pair_frc, c->pair_gsj, st)));
+    CK(TIMED("gather32_force", launch_relax32_gather(true, c->nl, c->dp, A, c->pid, c->n_upairs, c->pair_dens,
+                                                      c->pair_frc, c->pair_gsj, st)));
+  } else {
+    CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
+    CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
+  }
   float4* p32 = c->precision != MXE_FP64 ? c->pos32 : nullptr;
   if (c->nsys) {
     CK(TIMED("fire_reduce", launch_fire_seg_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->B, c->sf, c->ctrl, c->flags, st)));
@@ -1120,6 +1140,9 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->pair_t);
   dfree(c->pid);
   dfree(c->pair_buf);
+  dfree(c->pair_dens);
+  dfree(c->pair_frc);
+  dfree(c->pair_gsj);
   dfree(c->v_new);
   dfree(c->th_buf);
   dfree(c->th_sum);

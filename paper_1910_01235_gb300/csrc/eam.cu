@@ -1088,6 +1088,334 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
   if (!finite) atomicOr(A.flags, kFlagNonfinite);
 }
 
+// ---------------------------------------------------------------- half-list FP32 relaxation passes
+// The relaxation's density and force passes in the FP32-with-float-float-sums
+// mode, each unordered pair evaluated once:
+//  k_pair32_density: f_v(r_ij) and the sum of f_v over the 12 nodes (both
+//    symmetric in i, j) -> dens[p] (float4, n_f <= 2);
+//  k_gather32_density: per site the sums over its row, then the embedding
+//    coefficients (a, b) as the lean density pass writes them;
+//  k_pair32_force: with the pair's weights (x, a, b of both sites) the force
+//    on the row-owner site i, F_i = -(d T + U / 12), d = q_j - q_i (the other
+//    site receives -F_i: the pair functions are symmetric), and the width
+//    derivatives of both sites (over the nodes that move i and those that
+//    move j) -> frc[p] = (F_i, dF/dsigma_i part), gsj[p] = dF/dsigma_j part;
+//  k_gather32_force: per site the signed sums, then the thermal term.
+template <int S>
+__global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, PassArgs A,
+                                                        const int* __restrict__ pair_i,
+                                                        const int* __restrict__ pair_t, int64_t npair,
+                                                        float4* __restrict__ dens) {
+  using R = float;
+  constexpr int NF = S * S;
+  if (chunk_halted(A)) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int64_t i = pair_i[p];
+  const int tp = pair_t[p];
+  if (i < 0 || i >= A.n || tp < A.nb_off[i] || tp >= A.nb_off[i + 1]) {
+    atomicOr(A.flags, kFlagOverflow);
+    return;
+  }
+  const uint32_t ent = A.nb_ent[tp];
+  const int64_t j = ent & kIdxMask;
+  const DevGrid gs = site_grid(g0, A.batch, i);
+  SiteData<2, S> si, sj;
+  load_site(A, i, si);
+  load_site(A, j, sj);
+  R d[3];
+  separation(gs, si, sj, ent >> kCodeShift, d);
+  const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
+  const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const R near = (R)kRMin + fmaxf(s_i, s_j);
+  R fst[NF], fav[NF];
+  {
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+#pragma unroll
+    for (int v = 0; v < NF; ++v) {
+      fst[v] = v < P.n_f ? rad_raw(P.f[v], r) * Sw : 0.f;
+      fav[v] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int site = 0; site < 2; ++site) {
+    const R s = site == 0 ? s_i : s_j;
+    const R base = D2 + s * s;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R tw = 2.f * s * d[a];
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        const R r2 = pm == 0 ? base + tw : base - tw;
+        R r, rinv, Sw, dS;
+        r_from_r2(r2, r, rinv);
+        sw(P, r, Sw, dS);
+#pragma unroll
+        for (int v = 0; v < NF; ++v)
+          if (v < P.n_f) fav[v] += rad_raw(P.f[v], r) * Sw;
+      }
+    }
+  }
+  int bad = 0;
+  if (D2 < near * near) {  // rare: the exact node distances
+    for (int site = 0; site < 2; ++site) {
+      const R s = site == 0 ? s_i : s_j;
+      for (int a = 0; a < 3; ++a) {
+        const R base = D2 + s * s, tw = 2.f * s * d[a];
+        bad |= (base + tw) < (R)(kRMin * kRMin);
+        bad |= (base - tw) < (R)(kRMin * kRMin);
+      }
+    }
+  }
+  dens[p] = make_float4(fst[0], NF > 1 && P.n_f > 1 ? fst[NF > 1 ? 1 : 0] : 0.f, fav[0],
+                        NF > 1 && P.n_f > 1 ? fav[NF > 1 ? 1 : 0] : 0.f);
+  if (bad) atomicOr(A.flags, kFlagGeometry);
+}
+
+template <int S, int NL>
+__global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, const int* __restrict__ pid,
+                                                          const float4* __restrict__ dens, int64_t npair) {
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  AccFF rb[S], ra[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    rb[k].zero();
+    ra[k].zero();
+  }
+  if (active) {
+    const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+    for (int t = beg + lane; t < end; t += NL) {
+      const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
+      const int pp = __ldg(&pid[t]);
+      if (pp < 0 || pp >= npair) {
+        atomicOr(A.flags, kFlagOverflow);
+        continue;
+      }
+      const float4 rec = __ldg(&dens[pp]);
+      const float fst[2] = {rec.x, rec.y}, fav[2] = {rec.z, rec.w};
+      const float4 X = __ldg(&A.x32[j]);
+      const float xs[4] = {X.x, X.y, X.z, X.w};
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        float sb = 0.f, sa = 0.f;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const int v = P.f_of[k][l];
+          if (v < 0) continue;
+          sb += xs[l] * fst[v & 1];
+          sa += xs[l] * fav[v & 1];
+        }
+        rb[k].add(sb);
+        ra[k].add(sa);
+      }
+    }
+  }
+  if (NL > 1) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      rb[k].team_reduce(NL);
+      ra[k].team_reduce(NL);
+    }
+  }
+  if (!active || lane != 0) return;
+  int flag = 0;
+  float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const float4 X = A.x32[i];
+  const float xs[4] = {X.x, X.y, X.z, X.w};
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const float2 b2 = rb[k].get_pair(), a2 = ra[k].get_pair();
+    const float rf = b2.x + b2.y;
+    const float df = fmaf(a2.x, 1.0f / 12.0f, -b2.x) + fmaf(a2.y, 1.0f / 12.0f, -b2.y);
+    if (rf > (float)kRhoMin) {
+      const float Ef = (float)P.E[k];
+      const float isq = rsqrt_approx(rf);
+      const float dF = -0.5f * Ef * isq;
+      const float d2F = 0.25f * Ef * isq * isq * isq;
+      ab[2 * k] = xs[k] * d2F * df;
+      ab[2 * k + 1] = xs[k] * dF;
+    } else {
+      flag |= kFlagGeometry;
+    }
+  }
+  A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
+  if (flag) atomicOr(A.flags, flag);
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, PassArgs A,
+                                                      const int* __restrict__ pair_i, const int* __restrict__ pair_t,
+                                                      int64_t npair, float4* __restrict__ frc,
+                                                      float* __restrict__ gsj_out) {
+  using R = float;
+  constexpr int NF = S * S;
+  constexpr int NP = S * (S + 1) / 2;
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int64_t i = pair_i[p];
+  const int tp = pair_t[p];
+  if (i < 0 || i >= A.n || tp < A.nb_off[i] || tp >= A.nb_off[i + 1]) {
+    atomicOr(A.flags, kFlagOverflow);
+    return;
+  }
+  const uint32_t ent = A.nb_ent[tp];
+  const int64_t j = ent & kIdxMask;
+  const DevGrid gs = site_grid(g0, A.batch, i);
+  SiteData<2, S> si, sj;
+  load_site(A, i, si);
+  load_site(A, j, sj);
+  R ai[S], bi[S], aj[S], bj[S];
+  load_ab(A, i, ai, bi, (SiteData<2, S>*)nullptr);
+  load_ab(A, j, aj, bj, (SiteData<2, S>*)nullptr);
+  R d[3];
+  separation(gs, si, sj, ent >> kCodeShift, d);
+  const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
+  const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  R cphi[NP], cfa[NF], cfs[NF];
+#pragma unroll
+  for (int u = 0; u < NP; ++u) cphi[u] = 0.f;
+#pragma unroll
+  for (int v = 0; v < NF; ++v) cfa[v] = cfs[v] = 0.f;
+#pragma unroll
+  for (int k = 0; k < S; ++k)
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+#pragma unroll
+      for (int u = 0; u < NP; ++u)
+        if (P.phi_of[k][l] == u) cphi[u] += si.x[k] * sj.x[l];
+#pragma unroll
+      for (int v = 0; v < NF; ++v)
+        if (P.f_of[k][l] == v) {
+          cfa[v] += bi[k] * sj.x[l] + bj[k] * si.x[l];
+          cfs[v] += ai[k] * sj.x[l] + aj[k] * si.x[l];
+        }
+    }
+  R clphi[NP], clf[NF];
+#pragma unroll
+  for (int u = 0; u < NP; ++u) clphi[u] = cphi[u] * P.phi[u].lam_f;
+#pragma unroll
+  for (int v = 0; v < NF; ++v) clf[v] = cfa[v] * P.f[v].lam_f;
+  R Gs;
+  {
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+    Gs = 0.f;
+#pragma unroll
+    for (int v = 0; v < NF; ++v)
+      if (v < P.n_f) {
+        const R e = rad_raw(P.f[v], r);
+        Gs += cfs[v] * (e * (dS - P.f[v].lam_f * Sw));
+      }
+    Gs *= rinv;
+  }
+  R T = 0.f, U[3] = {0.f, 0.f, 0.f}, Vs[2] = {0.f, 0.f};
+#pragma unroll
+  for (int site = 0; site < 2; ++site) {
+    const R s = site == 0 ? s_i : s_j;
+    const R base = D2 + s * s;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R tw = 2.f * s * d[a];
+      R w2[2];
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        const R r2 = pm == 0 ? base + tw : base - tw;
+        R r, rinv, Sw, dS;
+        r_from_r2(r2, r, rinv);
+        sw(P, r, Sw, dS);
+        R A1 = 0.f, A2 = 0.f;
+#pragma unroll
+        for (int u = 0; u < NP; ++u)
+          if (u < P.n_phi) {
+            const R e = rad_raw(P.phi[u], r);
+            A1 += cphi[u] * e;
+            A2 += clphi[u] * e;
+          }
+#pragma unroll
+        for (int v = 0; v < NF; ++v)
+          if (v < P.n_f) {
+            const R e = rad_raw(P.f[v], r);
+            A1 += cfa[v] * e;
+            A2 += clf[v] * e;
+          }
+        w2[pm] = (A1 * dS - A2 * Sw) * rinv;
+      }
+      T += w2[0] + w2[1];
+      U[a] += s * (w2[0] - w2[1]);
+      Vs[site] += sqrt6<R>() * ((d[a] + s) * w2[0] - (d[a] - s) * w2[1]);
+    }
+  }
+  const R inv12 = 1.0f / 12.0f;
+  const R Tt = T * inv12 + Gs;
+  frc[p] = make_float4(-(d[0] * Tt + U[0] * inv12), -(d[1] * Tt + U[1] * inv12), -(d[2] * Tt + U[2] * inv12),
+                       Vs[0] * inv12);
+  gsj_out[p] = Vs[1] * inv12;
+}
+
+template <int S, int NL>
+__global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const int* __restrict__ pid,
+                                                        const float4* __restrict__ frc,
+                                                        const float* __restrict__ gsj, int64_t npair) {
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  AccFF g[3], gsig;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) g[c].zero();
+  gsig.zero();
+  if (active) {
+    const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+    for (int t = beg + lane; t < end; t += NL) {
+      const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
+      const int pp = __ldg(&pid[t]);
+      if (pp < 0 || pp >= npair) {
+        atomicOr(A.flags, kFlagOverflow);
+        continue;
+      }
+      const float4 f = __ldg(&frc[pp]);
+      if (j > i) {  // this site owns the pair
+        g[0].add(f.x);
+        g[1].add(f.y);
+        g[2].add(f.z);
+        gsig.add(f.w);
+      } else {
+        g[0].add(-f.x);
+        g[1].add(-f.y);
+        g[2].add(-f.z);
+        gsig.add(__ldg(&gsj[pp]));
+      }
+    }
+  }
+  if (NL > 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c].team_reduce(NL);
+    gsig.team_reduce(NL);
+  }
+  if (!active || lane != 0) return;
+  const int64_t n = A.n;
+  const double g0 = g[0].get(), g1 = g[1].get(), g2 = g[2].get();
+  const float2 gp = gsig.get_pair();
+  const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)A.sigma[i];
+  const double gs = (double)((gp.x - th) + gp.y);
+  if (A.gq) {
+    A.gq[i] = g0;
+    A.gq[n + i] = g1;
+    A.gq[2 * n + i] = g2;
+  }
+  if (A.gs) A.gs[i] = gs;
+  if (!(isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs))) atomicOr(A.flags, kFlagNonfinite);
+}
+
 // ---------------------------------------------------------------- K7: pack
 __global__ void k_pack(const double* __restrict__ q, const double* __restrict__ sigma, const double* __restrict__ x,
                        const int* __restrict__ abs_cell, int64_t n, int S, DevGrid g0, Batch B,
@@ -1366,6 +1694,55 @@ cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs&
     case 2: return pair_gather_s<2>(mu, nl, P, A, pid, buf, C, npair, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+namespace {
+template <int S, int NL>
+cudaError_t relax32_gather_t(bool force, const DevPot& P, const PassArgs& A, const int* pid, const float4* dens,
+                             const float4* frc, const float* gsj, int64_t npair, cudaStream_t s) {
+  const int threads = A.tpb > 0 ? A.tpb : 256;
+  const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
+  if (force) k_gather32_force<S, NL><<<blocks, threads, 0, s>>>(A, pid, frc, gsj, npair);
+  else k_gather32_density<S, NL><<<blocks, threads, 0, s>>>(P, A, pid, dens, npair);
+  return cudaGetLastError();
+}
+template <int S>
+cudaError_t relax32_gather_s(bool force, int nl, const DevPot& P, const PassArgs& A, const int* pid,
+                             const float4* dens, const float4* frc, const float* gsj, int64_t npair, cudaStream_t s) {
+  switch (nl) {
+    case 4: return relax32_gather_t<S, 4>(force, P, A, pid, dens, frc, gsj, npair, s);
+    case 8: return relax32_gather_t<S, 8>(force, P, A, pid, dens, frc, gsj, npair, s);
+    case 16: return relax32_gather_t<S, 16>(force, P, A, pid, dens, frc, gsj, npair, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+bool relax32_pairs_supported(const DevPot& P) { return P.S <= 2 && P.n_f <= 2; }
+
+cudaError_t launch_relax32_pair(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i,
+                                const int* pair_t, int64_t npair, float4* dens, float4* frc, float* gsj,
+                                cudaStream_t s) {
+  if (A.n == 0 || npair == 0) return cudaSuccess;
+  if (!relax32_pairs_supported(P)) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((npair + 127) / 128);
+  if (force) {
+    if (P.S == 1) k_pair32_force<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, frc, gsj);
+    else k_pair32_force<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, frc, gsj);
+  } else {
+    if (P.S == 1) k_pair32_density<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, dens);
+    else k_pair32_density<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, dens);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const int* pid,
+                                  int64_t npair, const float4* dens, const float4* frc, const float* gsj,
+                                  cudaStream_t s) {
+  if (A.n == 0) return cudaSuccess;
+  if (!relax32_pairs_supported(P)) return cudaErrorInvalidValue;
+  if (P.S == 1) return relax32_gather_s<1>(force, nl, P, A, pid, dens, frc, gsj, npair, s);
+  return relax32_gather_s<2>(force, nl, P, A, pid, dens, frc, gsj, npair, s);
 }
 
 }  // namespace mxe

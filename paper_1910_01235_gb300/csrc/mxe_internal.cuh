@@ -218,6 +218,16 @@ cudaError_t launch_pair_ff(const DevPot& P, const DevGrid& g, const PassArgs& A,
                            int64_t npair, float2* buf, cudaStream_t s);
 cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
                                int64_t npair, cudaStream_t s);
+// half-list FP32 relaxation passes (FP32 node math, float-float sums): the
+// pair kernel then the per-site gather, density (force = false: a, b packed
+// into ab32) or forces (dF/dq, dF/dsigma); records dens / frc + gsj per pair
+bool relax32_pairs_supported(const DevPot& P);
+cudaError_t launch_relax32_pair(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i,
+                                const int* pair_t, int64_t npair, float4* dens, float4* frc, float* gsj,
+                                cudaStream_t s);
+cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const int* pid,
+                                  int64_t npair, const float4* dens, const float4* frc, const float* gsj,
+                                  cudaStream_t s);
 cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s);
 // batches: F4 [nsys][4], one block per system in a fixed order
