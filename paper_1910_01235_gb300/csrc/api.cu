@@ -79,8 +79,8 @@ struct mxe_ctx {
   int *first_gt = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
   int *pair_i = nullptr, *pair_t = nullptr, *pid = nullptr;           // [pairs], [pairs], [entries]
   float2* pair_buf = nullptr;                                         // [pairs][pair_record_len]
-  float4 *pair_dens = nullptr, *pair_frc = nullptr;                   // [pairs] FP32 relaxation records
-  float* pair_gsj = nullptr;                                          // [pairs]
+  int* pair_rev = nullptr;                                            // [pairs] entry of the other end
+  float4 *ent_dens = nullptr, *ent_frc = nullptr;                     // [entries] FP32 relaxation records
   int64_t pair_cap = 0, n_upairs = 0;
 
   // per-site work arrays
@@ -507,12 +507,12 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     CK(dalloc(&c->pair_i, cap / 2 + 64));
     CK(dalloc(&c->pair_t, cap / 2 + 64));
     CK(dalloc(&c->pair_buf, (cap / 2 + 64) * (int64_t)pair_record_len(c->dp)));
-    dfree(c->pair_dens);
-    dfree(c->pair_frc);
-    dfree(c->pair_gsj);
-    CK(dalloc(&c->pair_dens, cap / 2 + 64));
-    CK(dalloc(&c->pair_frc, cap / 2 + 64));
-    CK(dalloc(&c->pair_gsj, cap / 2 + 64));
+    dfree(c->pair_rev);
+    dfree(c->ent_dens);
+    dfree(c->ent_frc);
+    CK(dalloc(&c->pair_rev, cap / 2 + 64));
+    CK(dalloc(&c->ent_dens, cap));
+    CK(dalloc(&c->ent_frc, cap));
     c->pair_cap = cap;
   }
   if (nbonds > c->bd_cap) {
@@ -537,7 +537,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     CK(TIMED("build_misc", launch_pair_count(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_cnt, st)));
     CK(TIMED("build_misc", launch_scan(c->pair_cnt, c->pair_off, n, c->totals + 3, (int*)c->scan_tmp, c->scan_len, st)));
     CK(TIMED("build_misc", launch_pair_fill(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_off, npairs / 2, c->pair_i,
-                                            c->pair_t, c->pid, c->flags, st)));
+                                            c->pair_t, c->pair_rev, c->pid, c->flags, st)));
     c->n_upairs = npairs / 2;
   }
   CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
@@ -633,14 +633,12 @@ mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
   const int64_t n = c->n;
   if (c->precision == MXE_FP32_FF && c->pid && relax32_pairs_supported(c->dp)) {
     // each unordered pair once: pair kernel, then the per-site gather
-    CK(TIMED("pair32_density", launch_relax32_pair(false, c->dp, c->grid, A, c->pair_i, c->pair_t, c->n_upairs,
-                                                    c->pair_dens, c->pair_frc, c->pair_gsj, st)));
-    CK(TIMED("gather32_density", launch_relax32_gather(false, c->nl, c->dp, A, c->pid, c->n_upairs, c->pair_dens,
-                                                        c->pair_frc, c->pair_gsj, st)));
-    CK(TIMED("pair32_force", launch_relax32_pair(true, c->dp, c->grid, A, c->pair_i, c->pair_t, c->n_upairs,
-                                                  c->pair_dens, c->pair_frc, c->pair_gsj, st)));
-    CK(TIMED("gather32_force", launch_relax32_gather(true, c->nl, c->dp, A, c->pid, c->n_upairs, c->pair_dens,
-                                                      c->pair_frc, c->pair_gsj, st)));
+    CK(TIMED("pair32_density", launch_relax32_pair(false, c->dp, c->grid, A, c->pair_i, c->pair_t, c->pair_rev,
+                                                    c->n_upairs, c->ent_dens, c->ent_frc, st)));
+    CK(TIMED("gather32_density", launch_relax32_gather(false, c->nl, c->dp, A, c->ent_dens, c->ent_frc, st)));
+    CK(TIMED("pair32_force", launch_relax32_pair(true, c->dp, c->grid, A, c->pair_i, c->pair_t, c->pair_rev,
+                                                  c->n_upairs, c->ent_dens, c->ent_frc, st)));
+    CK(TIMED("gather32_force", launch_relax32_gather(true, c->nl, c->dp, A, c->ent_dens, c->ent_frc, st)));
   } else {
     CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
     CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
@@ -1140,9 +1138,9 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->pair_t);
   dfree(c->pid);
   dfree(c->pair_buf);
-  dfree(c->pair_dens);
-  dfree(c->pair_frc);
-  dfree(c->pair_gsj);
+  dfree(c->pair_rev);
+  dfree(c->ent_dens);
+  dfree(c->ent_frc);
   dfree(c->v_new);
   dfree(c->th_buf);
   dfree(c->th_sum);

@@ -311,18 +311,24 @@ __device__ __forceinline__ bool skin_violated(const Ctrl* c) {
   return 2.0 * disp + kSqrt6 * (smax - c->sigma_max_build) > c->skin;
 }
 
-// Uniform early exit of the relaxation chunk.  Returns true if the kernel must stop.
+// Uniform early exit of the relaxation chunk.  Returns true if the kernel must
+// stop.  One thread per block evaluates the test (its FP64 square root would
+// otherwise run once per thread on the slow FP64 pipe) and shares it; every
+// thread of the block must call this before any early return.
 __device__ __forceinline__ bool chunk_halted(const PassArgs& A) {
   if (A.ctrl == nullptr) return false;
-  if (A.ctrl->halted) return true;
-  if (A.check_skin && skin_violated(A.ctrl)) {
-    if (threadIdx.x == 0) {
+  __shared__ int halt;
+  if (threadIdx.x == 0) {
+    int h = A.ctrl->halted ? 1 : 0;
+    if (!h && A.check_skin && skin_violated(A.ctrl)) {
       A.ctrl->reason = kReasonRebuild;
       A.ctrl->halted = 1;
+      h = 1;
     }
-    return true;
+    halt = h;
   }
-  return false;
+  __syncthreads();
+  return halt != 0;
 }
 
 // ---------------------------------------------------------------- K2: density pass
@@ -912,6 +918,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
   }
   if (active) {
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+#pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
       const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
       const int pp = __ldg(&pid[t]);
@@ -927,7 +934,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
       for (int k = 0; k < S; ++k) sj.x[k] = ff(xs[k], xl[k]);
 #pragma unroll
       for (int k = 0; k < S; ++k) {
-        R sb = (R)0, sa = (R)0;
+        R sb(0.f, 0.f), sa(0.f, 0.f);
 #pragma unroll
         for (int l = 0; l < S; ++l) {
           const int v = P.f_of[k][l];
@@ -1025,10 +1032,10 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
       }
       R aj[S], bj[S];
       load_ab(A, j, aj, bj, (SiteData<3, S>*)nullptr);
-      R ep = (R)0;
+      R ep(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < S; ++k) {
-        R m = (R)0;
+        R m(0.f, 0.f);
 #pragma unroll
         for (int l = 0; l < S; ++l) {
           const int u = P.phi_of[k][l];
@@ -1043,7 +1050,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
         }
         mu[k].add(m);
       }
-      epair.add((R)0.5 * inv12 * ep);
+      epair.add(ff(0.5f, 0.f) * inv12 * ep);
     }
   }
   if (NL > 1) {
@@ -1104,7 +1111,8 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
 template <int S>
 __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, PassArgs A,
                                                         const int* __restrict__ pair_i,
-                                                        const int* __restrict__ pair_t, int64_t npair,
+                                                        const int* __restrict__ pair_t,
+                                                        const int* __restrict__ pair_rev, int64_t npair,
                                                         float4* __restrict__ dens) {
   using R = float;
   constexpr int NF = S * S;
@@ -1169,14 +1177,33 @@ __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, Pa
       }
     }
   }
-  dens[p] = make_float4(fst[0], NF > 1 && P.n_f > 1 ? fst[NF > 1 ? 1 : 0] : 0.f, fav[0],
-                        NF > 1 && P.n_f > 1 ? fav[NF > 1 ? 1 : 0] : 0.f);
-  if (bad) atomicOr(A.flags, kFlagGeometry);
+  // each entry receives its own site's density contributions from the other
+  // site: (rho_bar^0, rho_bar^1, <rho>^0, <rho>^1) x 12 for the average
+  float ci[4] = {0.f, 0.f, 0.f, 0.f}, cj[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < S; ++k)
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      const int v = P.f_of[k][l];
+#pragma unroll
+      for (int w = 0; w < NF; ++w)
+        if (v == w) {
+          ci[k] += sj.x[l] * fst[w];
+          ci[2 + k] += sj.x[l] * fav[w];
+          cj[k] += si.x[l] * fst[w];
+          cj[2 + k] += si.x[l] * fav[w];
+        }
+    }
+  const int tr = pair_rev[p];
+  dens[tp] = make_float4(ci[0], ci[1], ci[2], ci[3]);
+  if (tr >= A.nb_off[j] && tr < A.nb_off[j + 1]) dens[tr] = make_float4(cj[0], cj[1], cj[2], cj[3]);
+  else bad |= 2;
+  if (bad & 1) atomicOr(A.flags, kFlagGeometry);
+  if (bad & 2) atomicOr(A.flags, kFlagOverflow);
 }
 
 template <int S, int NL>
-__global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, const int* __restrict__ pid,
-                                                          const float4* __restrict__ dens, int64_t npair) {
+__global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, const float4* __restrict__ dens) {
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
@@ -1190,29 +1217,14 @@ __global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, 
   }
   if (active) {
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+#pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
-      const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
-      const int pp = __ldg(&pid[t]);
-      if (pp < 0 || pp >= npair) {
-        atomicOr(A.flags, kFlagOverflow);
-        continue;
-      }
-      const float4 rec = __ldg(&dens[pp]);
-      const float fst[2] = {rec.x, rec.y}, fav[2] = {rec.z, rec.w};
-      const float4 X = __ldg(&A.x32[j]);
-      const float xs[4] = {X.x, X.y, X.z, X.w};
-#pragma unroll
-      for (int k = 0; k < S; ++k) {
-        float sb = 0.f, sa = 0.f;
-#pragma unroll
-        for (int l = 0; l < S; ++l) {
-          const int v = P.f_of[k][l];
-          if (v < 0) continue;
-          sb += xs[l] * fst[v & 1];
-          sa += xs[l] * fav[v & 1];
-        }
-        rb[k].add(sb);
-        ra[k].add(sa);
+      const float4 rec = __ldg(&dens[t]);
+      rb[0].add(rec.x);
+      ra[0].add(rec.z);
+      if (S > 1) {
+        rb[S > 1 ? 1 : 0].add(rec.y);
+        ra[S > 1 ? 1 : 0].add(rec.w);
       }
     }
   }
@@ -1251,8 +1263,8 @@ __global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, 
 template <int S>
 __global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, PassArgs A,
                                                       const int* __restrict__ pair_i, const int* __restrict__ pair_t,
-                                                      int64_t npair, float4* __restrict__ frc,
-                                                      float* __restrict__ gsj_out) {
+                                                      const int* __restrict__ pair_rev, int64_t npair,
+                                                      float4* __restrict__ frc) {
   using R = float;
   constexpr int NF = S * S;
   constexpr int NP = S * (S + 1) / 2;
@@ -1355,15 +1367,17 @@ __global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, Pass
   }
   const R inv12 = 1.0f / 12.0f;
   const R Tt = T * inv12 + Gs;
-  frc[p] = make_float4(-(d[0] * Tt + U[0] * inv12), -(d[1] * Tt + U[1] * inv12), -(d[2] * Tt + U[2] * inv12),
-                       Vs[0] * inv12);
-  gsj_out[p] = Vs[1] * inv12;
+  // this entry: the force on i and its width derivative; the reverse entry:
+  // the force on j (Newton's third law) and j's width derivative
+  const float Fx = -(d[0] * Tt + U[0] * inv12), Fy = -(d[1] * Tt + U[1] * inv12), Fz = -(d[2] * Tt + U[2] * inv12);
+  frc[tp] = make_float4(Fx, Fy, Fz, Vs[0] * inv12);
+  const int tr = pair_rev[p];
+  if (tr >= A.nb_off[j] && tr < A.nb_off[j + 1]) frc[tr] = make_float4(-Fx, -Fy, -Fz, Vs[1] * inv12);
+  else atomicOr(A.flags, kFlagOverflow);
 }
 
 template <int S, int NL>
-__global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const int* __restrict__ pid,
-                                                        const float4* __restrict__ frc,
-                                                        const float* __restrict__ gsj, int64_t npair) {
+__global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const float4* __restrict__ frc) {
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
@@ -1375,25 +1389,13 @@ __global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const int* _
   gsig.zero();
   if (active) {
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
+#pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
-      const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
-      const int pp = __ldg(&pid[t]);
-      if (pp < 0 || pp >= npair) {
-        atomicOr(A.flags, kFlagOverflow);
-        continue;
-      }
-      const float4 f = __ldg(&frc[pp]);
-      if (j > i) {  // this site owns the pair
-        g[0].add(f.x);
-        g[1].add(f.y);
-        g[2].add(f.z);
-        gsig.add(f.w);
-      } else {
-        g[0].add(-f.x);
-        g[1].add(-f.y);
-        g[2].add(-f.z);
-        gsig.add(__ldg(&gsj[pp]));
-      }
+      const float4 f = __ldg(&frc[t]);
+      g[0].add(f.x);
+      g[1].add(f.y);
+      g[2].add(f.z);
+      gsig.add(f.w);
     }
   }
   if (NL > 1) {
@@ -1698,21 +1700,21 @@ cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs&
 
 namespace {
 template <int S, int NL>
-cudaError_t relax32_gather_t(bool force, const DevPot& P, const PassArgs& A, const int* pid, const float4* dens,
-                             const float4* frc, const float* gsj, int64_t npair, cudaStream_t s) {
+cudaError_t relax32_gather_t(bool force, const DevPot& P, const PassArgs& A, const float4* dens, const float4* frc,
+                             cudaStream_t s) {
   const int threads = A.tpb > 0 ? A.tpb : 256;
   const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
-  if (force) k_gather32_force<S, NL><<<blocks, threads, 0, s>>>(A, pid, frc, gsj, npair);
-  else k_gather32_density<S, NL><<<blocks, threads, 0, s>>>(P, A, pid, dens, npair);
+  if (force) k_gather32_force<S, NL><<<blocks, threads, 0, s>>>(A, frc);
+  else k_gather32_density<S, NL><<<blocks, threads, 0, s>>>(P, A, dens);
   return cudaGetLastError();
 }
 template <int S>
-cudaError_t relax32_gather_s(bool force, int nl, const DevPot& P, const PassArgs& A, const int* pid,
-                             const float4* dens, const float4* frc, const float* gsj, int64_t npair, cudaStream_t s) {
+cudaError_t relax32_gather_s(bool force, int nl, const DevPot& P, const PassArgs& A, const float4* dens,
+                             const float4* frc, cudaStream_t s) {
   switch (nl) {
-    case 4: return relax32_gather_t<S, 4>(force, P, A, pid, dens, frc, gsj, npair, s);
-    case 8: return relax32_gather_t<S, 8>(force, P, A, pid, dens, frc, gsj, npair, s);
-    case 16: return relax32_gather_t<S, 16>(force, P, A, pid, dens, frc, gsj, npair, s);
+    case 4: return relax32_gather_t<S, 4>(force, P, A, dens, frc, s);
+    case 8: return relax32_gather_t<S, 8>(force, P, A, dens, frc, s);
+    case 16: return relax32_gather_t<S, 16>(force, P, A, dens, frc, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1721,28 +1723,27 @@ cudaError_t relax32_gather_s(bool force, int nl, const DevPot& P, const PassArgs
 bool relax32_pairs_supported(const DevPot& P) { return P.S <= 2 && P.n_f <= 2; }
 
 cudaError_t launch_relax32_pair(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i,
-                                const int* pair_t, int64_t npair, float4* dens, float4* frc, float* gsj,
+                                const int* pair_t, const int* pair_rev, int64_t npair, float4* dens, float4* frc,
                                 cudaStream_t s) {
   if (A.n == 0 || npair == 0) return cudaSuccess;
   if (!relax32_pairs_supported(P)) return cudaErrorInvalidValue;
   const unsigned blocks = (unsigned)((npair + 127) / 128);
   if (force) {
-    if (P.S == 1) k_pair32_force<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, frc, gsj);
-    else k_pair32_force<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, frc, gsj);
+    if (P.S == 1) k_pair32_force<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, frc);
+    else k_pair32_force<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, frc);
   } else {
-    if (P.S == 1) k_pair32_density<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, dens);
-    else k_pair32_density<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, dens);
+    if (P.S == 1) k_pair32_density<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, dens);
+    else k_pair32_density<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, dens);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const int* pid,
-                                  int64_t npair, const float4* dens, const float4* frc, const float* gsj,
-                                  cudaStream_t s) {
+cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const float4* dens,
+                                  const float4* frc, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   if (!relax32_pairs_supported(P)) return cudaErrorInvalidValue;
-  if (P.S == 1) return relax32_gather_s<1>(force, nl, P, A, pid, dens, frc, gsj, npair, s);
-  return relax32_gather_s<2>(force, nl, P, A, pid, dens, frc, gsj, npair, s);
+  if (P.S == 1) return relax32_gather_s<1>(force, nl, P, A, dens, frc, s);
+  return relax32_gather_s<2>(force, nl, P, A, dens, frc, s);
 }
 
 }  // namespace mxe

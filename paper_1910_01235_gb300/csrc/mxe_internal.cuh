@@ -157,8 +157,8 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
 cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* first_gt, int* cnt,
                               cudaStream_t s);
 cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
-                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pid, int* flags,
-                             cudaStream_t s);
+                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pair_rev, int* pid,
+                             int* flags, cudaStream_t s);
 // exclusive scan of n int32 counts into out[0..n] (out[n] = total, int64 total in *total64)
 cudaError_t launch_scan(const int* in, int* out, int64_t n, long long* total64, int* tmp, int64_t tmp_len,
                         cudaStream_t s);
@@ -219,15 +219,15 @@ cudaError_t launch_pair_ff(const DevPot& P, const DevGrid& g, const PassArgs& A,
 cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
                                int64_t npair, cudaStream_t s);
 // half-list FP32 relaxation passes (FP32 node math, float-float sums): the
-// pair kernel then the per-site gather, density (force = false: a, b packed
-// into ab32) or forces (dF/dq, dF/dsigma); records dens / frc + gsj per pair
+// pair kernel writes each pair's record to both of its entries (pair_t[p],
+// pair_rev[p]); the gather then reads its own row: density (force = false:
+// a, b packed into ab32) or forces (dF/dq, dF/dsigma); dens, frc: [entries]
 bool relax32_pairs_supported(const DevPot& P);
 cudaError_t launch_relax32_pair(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i,
-                                const int* pair_t, int64_t npair, float4* dens, float4* frc, float* gsj,
+                                const int* pair_t, const int* pair_rev, int64_t npair, float4* dens, float4* frc,
                                 cudaStream_t s);
-cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const int* pid,
-                                  int64_t npair, const float4* dens, const float4* frc, const float* gsj,
-                                  cudaStream_t s);
+cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const float4* dens,
+                                  const float4* frc, cudaStream_t s);
 cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s);
 // batches: F4 [nsys][4], one block per system in a fixed order

@@ -614,8 +614,8 @@ __global__ void k_pair_count(const int* __restrict__ nb_off, const uint32_t* __r
 
 __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __restrict__ nb_ent, int64_t n,
                             const int* __restrict__ first_gt, const int* __restrict__ pair_off, int64_t npair,
-                            int* __restrict__ pair_i, int* __restrict__ pair_t, int* __restrict__ pid,
-                            int* __restrict__ flags) {
+                            int* __restrict__ pair_i, int* __restrict__ pair_t, int* __restrict__ pair_rev,
+                            int* __restrict__ pid, int* __restrict__ flags) {
   // one warp per row, lanes over its entries
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -641,6 +641,7 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
       const int t2 = first_above(nb_ent, jb, je, (uint32_t)i) - 1;
       if (t2 >= jb && (nb_ent[t2] & kIdxMask) == (uint32_t)i && pair_off[j] + (t2 - jb) < npair) {
         pid[t] = pair_off[j] + (t2 - jb);
+        pair_rev[pair_off[j] + (t2 - jb)] = t;
       } else {
         pid[t] = 0;
         atomicOr(flags, kFlagOverflow);
@@ -779,11 +780,11 @@ cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t
 }
 
 cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
-                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pid, int* flags,
-                             cudaStream_t s) {
+                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pair_rev, int* pid,
+                             int* flags, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_pair_fill<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, first_gt, pair_off, npair,
-                                                               pair_i, pair_t, pid, flags);
+                                                               pair_i, pair_t, pair_rev, pid, flags);
   return cudaGetLastError();
 }
 
