@@ -81,6 +81,7 @@ struct mxe_ctx {
   float2* pair_buf = nullptr;                                         // [pairs][pair_record_len]
   int* pair_rev = nullptr;                                            // [pairs] entry of the other end
   float4 *ent_dens = nullptr, *ent_frc = nullptr;                     // [entries] FP32 relaxation records
+  bool relax_records = false;  // allocate them (first relaxation of the context, then with every list growth)
   int64_t pair_cap = 0, n_upairs = 0;
 
   // per-site work arrays
@@ -511,8 +512,10 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     dfree(c->ent_dens);
     dfree(c->ent_frc);
     CK(dalloc(&c->pair_rev, cap / 2 + 64));
-    CK(dalloc(&c->ent_dens, cap));
-    CK(dalloc(&c->ent_frc, cap));
+    if (c->relax_records) {
+      CK(dalloc(&c->ent_dens, cap));
+      CK(dalloc(&c->ent_frc, cap));
+    }
     c->pair_cap = cap;
   }
   if (nbonds > c->bd_cap) {
@@ -626,12 +629,26 @@ void relax_pass_args(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
   A.lean = 1;
 }
 
-// One FIRE iteration: the force passes, then the reduction, logic and update
-// (per system for a batch).
-mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
+// The per-entry records of the half-list relaxation passes are allocated by
+// the first relaxation of a float-float context (outside any stream capture)
+// and kept, resized with the lists, from then on.
+mxe_status ensure_relax_records(mxe_ctx* c) {
+  if (c->precision != MXE_FP32_FF || !c->pid || !relax32_pairs_supported(c->dp)) return MXE_OK;
+  c->relax_records = true;
+  if (c->ent_dens && c->ent_frc) return MXE_OK;
+  dfree(c->ent_dens);
+  dfree(c->ent_frc);
+  CK(dalloc(&c->ent_dens, c->pair_cap));
+  CK(dalloc(&c->ent_frc, c->pair_cap));
+  return MXE_OK;
+}
+
+// The force passes of one relaxation iteration (densities, then dF/dq and
+// dF/dsigma into A.gq / A.gs): half list in float-float contexts, else the
+// full-list passes.
+mxe_status enqueue_force_passes(mxe_ctx* c, const PassArgs& A) {
   cudaStream_t st = c->stream;
-  const int64_t n = c->n;
-  if (c->precision == MXE_FP32_FF && c->pid && relax32_pairs_supported(c->dp)) {
+  if (c->precision == MXE_FP32_FF && c->pid && c->ent_dens && c->ent_frc && relax32_pairs_supported(c->dp)) {
     // each unordered pair once: pair kernel, then the per-site gather
     CK(TIMED("pair32_density", launch_relax32_pair(false, c->dp, c->grid, A, c->pair_i, c->pair_t, c->pair_rev,
                                                     c->n_upairs, c->ent_dens, c->ent_frc, st)));
@@ -643,6 +660,16 @@ mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
     CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
     CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
   }
+  return MXE_OK;
+}
+
+// One FIRE iteration: the force passes, then the reduction, logic and update
+// (per system for a batch).
+mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->n;
+  mxe_status fm = enqueue_force_passes(c, A);
+  if (fm != MXE_OK) return fm;
   float4* p32 = c->precision != MXE_FP64 ? c->pos32 : nullptr;
   if (c->nsys) {
     CK(TIMED("fire_reduce", launch_fire_seg_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->B, c->sf, c->ctrl, c->flags, st)));
@@ -839,9 +866,10 @@ mxe_status enqueue_tune_work(mxe_ctx* c, const mxe_state* s) {
   fill_pass(c, s, A);
   A.site_E = nullptr;
   A.lean = 1;
+  if (c->precision != MXE_FP64) CK(launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32, nullptr, nullptr, c->stream));
   for (int r = 0; r < 2; ++r) {
-    CK(launch_density(c->precision, c->nl, c->dp, c->grid, A, c->stream));
-    CK(launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, c->stream));
+    ms = enqueue_force_passes(c, A);
+    if (ms != MXE_OK) return ms;
   }
   return MXE_OK;
 }
@@ -1613,6 +1641,8 @@ mxe_status mxe_relax(mxe_ctx* c, mxe_state* s, double ftol, int32_t max_iter, co
     CK(cudaMemsetAsync(c->vs, 0, sizeof(double) * n, st));
   }
   Ctrl& H = *c->ctrl_h;
+  mxe_status rr = ensure_relax_records(c);
+  if (rr != MXE_OK) return rr;
   init_ctrl(c, H, fp, ftol, max_iter);
   CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   if (c->nsys) CK(launch_fire_seg_init(c->sf, c->nsys, fp.dt0, fp.alpha0, nullptr, st));
@@ -1652,6 +1682,8 @@ mxe_status mxe_run_staggered(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
   mxe_status pre = mxe_sync_status(c);
   if (pre != MXE_OK) return pre;
   Ctrl& H = *c->ctrl_h;
+  mxe_status rr = ensure_relax_records(c);
+  if (rr != MXE_OK) return rr;
   init_ctrl(c, H, fp, ftol, max_iter);
   CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   const StepKey key{s->q, s->sigma, s->x, s->T, s->sublattice, s->mobile_mask, dt, nu0, Qm, max_iter,
@@ -1720,6 +1752,8 @@ mxe_status mxe_autotune(mxe_ctx* c, const mxe_state* s, int32_t* lanes_out, int3
   mxe_status pre = mxe_sync_status(c);
   if (pre != MXE_OK) return pre;
   cudaStream_t st = c->stream;
+  mxe_status rr = ensure_relax_records(c);
+  if (rr != MXE_OK) return rr;
   const bool timing = c->timing;
   c->timing = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
