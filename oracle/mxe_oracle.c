@@ -54,6 +54,12 @@ typedef struct {
     double f_xi[ORC_MAXS][ORC_MAXS], f_q[ORC_MAXS][ORC_MAXS], f_r0[ORC_MAXS][ORC_MAXS];
     double E[ORC_MAXS];
     double r_switch, r_cut;
+    /* Thermalized Lennard-Jones pair terms (App. C.1) in place of phi when
+       lj != 0: phi_kl = 4 eps_kl [(s_kl / r)^12 - (s_kl / r)^6] S(r).  An
+       element with E_k = 0 has no embedding energy. */
+    int32_t lj;
+    int32_t pad;
+    double lj_eps[ORC_MAXS][ORC_MAXS], lj_sigma[ORC_MAXS][ORC_MAXS];
 } orc_potential;
 
 typedef struct {
@@ -364,6 +370,15 @@ static void phi_fn(const orc_potential *P, int k, int l, double r, double *v, do
 {
     double S, dS;
     switch_fn(P, r, &S, &dS);
+    if (P->lj) {
+        const double eps = P->lj_eps[k][l], s = P->lj_sigma[k][l];
+        const double x6 = pow(s / r, 6.0), x12 = x6 * x6;
+        const double e = 4.0 * eps * (x12 - x6);
+        const double de = 4.0 * eps * (-12.0 * x12 + 6.0 * x6) / r;
+        *v = e * S;
+        *dv = de * S + e * dS;
+        return;
+    }
     if (P->cross_geomean && k != l) {
         /* cross pair = pointwise geometric mean of the two pure pair terms */
         double eu, deu, ew, dew;
@@ -511,6 +526,10 @@ int orc_free_energy(const orc_system *sys, const orc_potential *P,
             }
             rb[k * n + i] = sb;
             ra[k * n + i] = sa;
+            if (P->E[k] == 0.0) {  /* no embedding energy for this element */
+                e[k * n + i] = A[k * n + i] = B[k * n + i] = 0.0;
+                continue;
+            }
             if (!(sb > ORC_RHO_MIN)) { geometry = 1; continue; }
             double F, dF, d2F;
             embed_fn(P, k, sb, &F, &dF, &d2F);

@@ -54,6 +54,11 @@ class Potential:
     r_switch: float = 4.5
     r_cut: float = 5.0
     cross_geomean: bool = False
+    # thermalized Lennard-Jones pair terms in place of phi (App. C.1):
+    # 4 eps_kl [(s_kl / r)^12 - (s_kl / r)^6] S(r); E_k = 0 removes the embedding
+    lj: bool = False
+    lj_eps: Optional[np.ndarray] = None
+    lj_sigma: Optional[np.ndarray] = None
 
 
 def _tables(S):
@@ -101,6 +106,16 @@ def potential_binary_variant_s() -> Potential:
     P.phi_p[:] = np.where(P.phi_p != 0, 5.0, 0.0)
     P.f_q[:] = np.where(P.f_q != 0, 3.0, 0.0)
     return P
+
+
+def potential_lj(eps=0.1, sigma_lj=2.3) -> Potential:
+    """One species with a 12-6 Lennard-Jones pair term (minimum at
+    2^(1/6) sigma_lj = 2.58 A, near the nearest-neighbour distance 2.55 A of
+    the a = 3.6 A lattice), no density and no embedding; same switch."""
+    S = 1
+    pA, pp, pr0, fx, fq, fr0 = _tables(S)
+    return Potential(S, pA, pp, pr0, fx, fq, fr0, np.array([0.0]), 4.5, 5.0, False, True,
+                     np.full((1, 1), eps), np.full((1, 1), sigma_lj))
 
 
 # The eight parameters differentiated in the surface-alloy workload: for each
