@@ -84,7 +84,13 @@ typedef struct {
  * cross_geomean != 0: phi_kl for k != l is sqrt(phi_kk phi_ll) pointwise and
  * the off-diagonal phi entries are ignored.  Otherwise phi must be symmetric
  * (phi_kl = phi_lk), else mxe_create returns MXE_ERR_ARG.  A = 0 or xi = 0
- * switches a term off.                                                       */
+ * switches a term off.
+ * lj != 0: the pair terms are thermalized Lennard-Jones terms (App. C.1)
+ *   phi_kl(r) = 4 lj_eps[k][l] ((lj_sigma[k][l] / r)^12 - (lj_sigma[k][l] / r)^6) S(r)
+ * (phi_* and cross_geomean ignored; the tables must be symmetric, eps >= 0,
+ * sigma > 0).  An element with E[k] = 0 has no embedding energy (no density
+ * check either), so lj with E = 0 and f_xi = 0 is a pure pair potential.
+ * Lennard-Jones terms are evaluated in MXE_FP64 contexts only.               */
 typedef struct {
     int32_t n_species;
     int32_t cross_geomean;
@@ -92,6 +98,9 @@ typedef struct {
     double f_xi[MXE_MAXS][MXE_MAXS], f_q[MXE_MAXS][MXE_MAXS], f_r0[MXE_MAXS][MXE_MAXS];
     double E[MXE_MAXS];
     double r_switch, r_cut;
+    int32_t lj;
+    int32_t pad;
+    double lj_eps[MXE_MAXS][MXE_MAXS], lj_sigma[MXE_MAXS][MXE_MAXS];
 } mxe_potential;
 
 /* Per-site state (device pointers, caller-owned).  q and sigma are in-out for

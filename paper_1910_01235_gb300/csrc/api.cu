@@ -245,10 +245,10 @@ mxe_status map_flags(int f) {
 }
 
 // Distinct radial terms of the potential (dedupe identical (A, kappa, lambda)).
-int add_fn(RadialFn* tab, int& count, int cap, double A, double kappa, double lambda) {
+int add_fn(RadialFn* tab, int& count, int cap, double A, double kappa, double lambda, int kind = 0) {
   if (A == 0.0) return -1;
   for (int u = 0; u < count; ++u)
-    if (tab[u].A == A && tab[u].kappa == kappa && tab[u].lambda == lambda) return u;
+    if (tab[u].A == A && tab[u].kappa == kappa && tab[u].lambda == lambda && tab[u].kind == kind) return u;
   if (count >= cap) return -2;
   RadialFn& F = tab[count];
   F.A = A;
@@ -259,6 +259,7 @@ int add_fn(RadialFn* tab, int& count, int cap, double A, double kappa, double la
   F.c1 = (float)(lambda * log2e);
   F.lam_f = (float)lambda;
   F.on = 1;
+  F.kind = kind;
   F.lnA_kappa_ff = ff(std::log(A) + kappa);
   F.lambda_ff = ff(lambda);
   return count++;
@@ -280,8 +281,18 @@ mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
       if (p.phi_A[k][l] < 0.0 || p.f_xi[k][l] < 0.0) return MXE_ERR_ARG;
     }
   }
+  d.lj = p.lj ? 1 : 0;
   for (int k = 0; k < S; ++k)
-    for (int l = k; l < S; ++l) {
+    for (int l = k; l < S && p.lj; ++l) {
+      // thermalized Lennard-Jones pair terms: A = 4 eps, kappa = sigma
+      const double eps = p.lj_eps[k][l], sg = p.lj_sigma[k][l];
+      if (eps != p.lj_eps[l][k] || sg != p.lj_sigma[l][k] || !(eps >= 0.0) || !(sg > 0.0)) return MXE_ERR_ARG;
+      int u = add_fn(d.phi, d.n_phi, kMaxPhiFn, 4.0 * eps, sg, 0.0, 1);
+      if (u == -2) return MXE_ERR_ARG;
+      d.phi_of[k][l] = d.phi_of[l][k] = (int8_t)u;
+    }
+  for (int k = 0; k < S; ++k)
+    for (int l = k; l < S && !p.lj; ++l) {
       double A, kap, lam;
       if (p.cross_geomean && k != l) {
         // sqrt(phi_kk phi_ll) = sqrt(A_k A_l) exp((p_k + p_l)/2 - (p_k/r0_k + p_l/r0_l)/2 r) S(r)
@@ -1031,6 +1042,7 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
   mxe_ctx* c = new (std::nothrow) mxe_ctx();
   if (!c) return MXE_ERR_OOM;
   mxe_status ms = make_devpot(*pot, c->dp);
+  if (ms == MXE_OK && c->dp.lj && precision != MXE_FP64) ms = MXE_ERR_ARG;  // FP64 passes only
   if (ms != MXE_OK) {
     delete c;
     return ms;
@@ -1341,7 +1353,7 @@ mxe_status mxe_potential_terms(mxe_ctx* c, int32_t* n_phi, int32_t* n_f, double*
 mxe_status mxe_tangent(mxe_ctx* c, const mxe_state* s, const double* dq_dev, const double* dsigma_dev,
                        const double* dx_dev, double* dFdq_dev, double* dFdsigma_dev, double* mu_ex_dev,
                        double* dFdq_t_dev, double* dFdsigma_t_dev, double* mu_ex_t_dev, double* dterm_dev) {
-  if (!c || !state_ok(c, s)) return MXE_ERR_ARG;
+  if (!c || !state_ok(c, s) || c->dp.lj) return MXE_ERR_ARG;
   if (!c->have_list) return MXE_ERR_STATE;
   Guard gd(c->device);
   mxe_status ms = ensure_tangent(c);
@@ -1373,7 +1385,7 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
   if (!c || !state_ok(c, s) || n_steps < 0 || every < 1 || !w_dev || !dterm_host || !(cg_tol > 0.0) ||
       cg_max < 1 || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm) || !(ftol >= 0.0) || max_iter < 0)
     return MXE_ERR_ARG;
-  if (c->precision != MXE_FP64 || c->fix_x_mask || c->fix_mu_mask) return MXE_ERR_ARG;
+  if (c->precision != MXE_FP64 || c->fix_x_mask || c->fix_mu_mask || c->dp.lj) return MXE_ERR_ARG;
   if (!c->have_list) return MXE_ERR_STATE;
   Guard gd(c->device);
   mxe_status ms = ensure_tangent(c);

@@ -183,6 +183,19 @@ __device__ __forceinline__ ff rad_lam(const RadialFn& F, ff) { return F.lambda_f
 __device__ __forceinline__ float rad_lam(const RadialFn& F, float) { return F.lam_f; }
 __device__ __forceinline__ double rad_lam(const RadialFn& F, double) { return F.lambda; }
 
+// A pair term and minus its derivative (FP64 passes): exponential terms, or
+// thermalized Lennard-Jones terms A ((s / r)^12 - (s / r)^6) (kind 1).
+__device__ __forceinline__ void rad_pair(const RadialFn& F, double r, double& e, double& mde) {
+  if (F.kind == 1) {
+    const double x = F.kappa / r, x2 = x * x, x6 = x2 * x2 * x2;
+    e = F.A * (x6 * x6 - x6);
+    mde = F.A * (12.0 * x6 * x6 - 6.0 * x6) / r;
+  } else {
+    e = F.A * exp(F.kappa - F.lambda * r);
+    mde = F.lambda * e;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T sqrt6();
 template <>
@@ -490,7 +503,9 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
     const double ravg = ra[k].get() * (1.0 / 12.0);
     const double xk = A.x[k * n + i];
     double e = 0.0, ak = 0.0, bk = 0.0;
-    if (rbar > kRhoMin) {
+    if (P.E[k] == 0.0) {
+      // no embedding energy for this element
+    } else if (rbar > kRhoMin) {
       if (PREC == 0 || PREC == 3) {
         const double sq = sqrt(rbar);
         const double F = -P.E[k] * sq;
@@ -662,9 +677,16 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
 #pragma unroll
               for (int u = 0; u < NP; ++u)
                 if (u < P.n_phi) {
-                  const R e = rad_raw(P.phi[u], r);
-                  A1p += cphi[u] * e;
-                  A2 += clphi[u] * e;
+                  if constexpr (PREC == 0) {
+                    double e, mde;
+                    rad_pair(P.phi[u], r, e, mde);
+                    A1p += cphi[u] * e;
+                    A2 += cphi[u] * mde;
+                  } else {
+                    const R e = rad_raw(P.phi[u], r);
+                    A1p += cphi[u] * e;
+                    A2 += clphi[u] * e;
+                  }
                 }
 #pragma unroll
               for (int v = 0; v < NF; ++v)
@@ -679,9 +701,16 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
 #pragma unroll
               for (int u = 0; u < NP; ++u)
                 if (u < P.n_phi) {
-                  const R e = rad_raw(P.phi[u], r);
-                  aphi[u] += e * Sw;
-                  if (DER) G += cphi[u] * (e * (dS - rad_lam(P.phi[u], r) * Sw));
+                  if constexpr (PREC == 0) {
+                    double e, mde;
+                    rad_pair(P.phi[u], r, e, mde);
+                    aphi[u] += e * Sw;
+                    if (DER) G += cphi[u] * (e * dS - mde * Sw);
+                  } else {
+                    const R e = rad_raw(P.phi[u], r);
+                    aphi[u] += e * Sw;
+                    if (DER) G += cphi[u] * (e * (dS - rad_lam(P.phi[u], r) * Sw));
+                  }
                 }
 #pragma unroll
               for (int v = 0; v < NF; ++v)

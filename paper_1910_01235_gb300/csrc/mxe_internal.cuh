@@ -38,15 +38,17 @@ enum : int {
 //  c0 = log2(A) + kappa log2(e), c1 = lambda log2(e).
 //  Float-float: g_raw = exp(lnA_kappa - lambda r) with both constants as float pairs.
 struct RadialFn {
-  double A, kappa, lambda;
+  double A, kappa, lambda;  // kind 0: A exp(kappa - lambda r); kind 1: A ((kappa / r)^12 - (kappa / r)^6)
   float c0, c1, lam_f;
   int on;
+  int kind;
   ff lnA_kappa_ff, lambda_ff;
 };
 
 // Potential in the form the kernels read (passed by value).
 struct DevPot {
   int S;
+  int lj;  // pair terms of kind 1 (FP64 passes only)
   int n_phi, n_f;
   RadialFn phi[kMaxPhiFn];
   RadialFn f[kMaxFFn];

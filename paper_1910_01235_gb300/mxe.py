@@ -37,7 +37,9 @@ class mxe_box(C.Structure):
 class mxe_potential(C.Structure):
     _fields_ = [("n_species", C.c_int32), ("cross_geomean", C.c_int32)] + [
         (nm, (C.c_double * MAXS) * MAXS) for nm in ("phi_A", "phi_p", "phi_r0", "f_xi", "f_q", "f_r0")
-    ] + [("E", C.c_double * MAXS), ("r_switch", C.c_double), ("r_cut", C.c_double)]
+    ] + [("E", C.c_double * MAXS), ("r_switch", C.c_double), ("r_cut", C.c_double),
+         ("lj", C.c_int32), ("pad", C.c_int32), ("lj_eps", (C.c_double * MAXS) * MAXS),
+         ("lj_sigma", (C.c_double * MAXS) * MAXS)]
 
 
 class mxe_state(C.Structure):
@@ -311,6 +313,12 @@ def make_potential(pot) -> mxe_potential:
     for k in range(S):
         P.E[k] = float(pot.E[k])
     P.r_switch, P.r_cut = float(pot.r_switch), float(pot.r_cut)
+    if getattr(pot, "lj", False):
+        P.lj = 1
+        for k in range(S):
+            for l in range(S):
+                P.lj_eps[k][l] = float(pot.lj_eps[k, l])
+                P.lj_sigma[k][l] = float(pot.lj_sigma[k, l])
     return P
 
 
