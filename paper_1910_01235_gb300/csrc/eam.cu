@@ -839,8 +839,6 @@ __global__ void __launch_bounds__(128) k_pair_ff(DevPot P, DevGrid g0, PassArgs 
                                                  const int* __restrict__ pair_t, int64_t npair,
                                                  float2* __restrict__ buf, int C) {
   using R = ff;
-  constexpr int NF = S * S;
-  constexpr int NP = S * (S + 1) / 2;
   if (chunk_halted(A)) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npair) return;
@@ -861,52 +859,44 @@ __global__ void __launch_bounds__(128) k_pair_ff(DevPot P, DevGrid g0, PassArgs 
   const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
   const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   int bad = D2 < (R)(kRMin * kRMin);
-  R fst[NF], fav[NF], aph[NP];
+  // the 13 points once: r and S(r) of the 12 nodes (0..11) and the static point (12)
+  R pr[13], pw[13];
   {
-    R r, rinv, Sw, dS;
-    r_from_r2(D2, r, rinv);
-    sw(P, r, Sw, dS);
-#pragma unroll
-    for (int v = 0; v < NF; ++v) {
-      fst[v] = v < P.n_f ? rad_raw(P.f[v], r) * Sw : (R)0;
-      fav[v] = (R)0;
-    }
-#pragma unroll
-    for (int u = 0; u < NP; ++u) aph[u] = (R)0;
+    R rinv, dS;
+    r_from_r2(D2, pr[12], rinv);
+    sw(P, pr[12], pw[12], dS);
   }
 #pragma unroll 1
-  for (int site = 0; site < 2; ++site) {
+  for (int k = 0; k < 12; ++k) {
+    const int site = k / 6, a = (k / 2) % 3, pm = k & 1;
     const R s = site == 0 ? s_i : s_j;
+    const R tw = (R)2 * s * d[a];
     const R base = D2 + s * s;
-#pragma unroll 1
-    for (int a = 0; a < 3; ++a) {
-      const R tw = (R)2 * s * d[a];
-#pragma unroll
-      for (int pm = 0; pm < 2; ++pm) {
-        const R r2 = pm == 0 ? base + tw : base - tw;
-        R r, rinv, Sw, dS;
-        r_from_r2(r2, r, rinv);
-        bad |= r2 < (R)(kRMin * kRMin);
-        sw(P, r, Sw, dS);
-#pragma unroll
-        for (int u = 0; u < NP; ++u)
-          if (u < P.n_phi) aph[u] += rad_raw(P.phi[u], r) * Sw;
-#pragma unroll
-        for (int v = 0; v < NF; ++v)
-          if (v < P.n_f) fav[v] += rad_raw(P.f[v], r) * Sw;
-      }
-    }
+    const R r2 = pm == 0 ? base + tw : base - tw;
+    bad |= r2 < (R)(kRMin * kRMin);
+    R rinv, dS;
+    r_from_r2(r2, pr[k], rinv);
+    sw(P, pr[k], pw[k], dS);
   }
+  // one term at a time over the points (rolled: one copy of the float-float
+  // exponential in the loop body)
   float2* o = buf + p * (int64_t)C;
-#pragma unroll
-  for (int v = 0; v < NF; ++v)
-    if (v < P.n_f) {
-      o[v] = make_float2(fst[v].hi, fst[v].lo);
-      o[P.n_f + v] = make_float2(fav[v].hi, fav[v].lo);
-    }
-#pragma unroll
-  for (int u = 0; u < NP; ++u)
-    if (u < P.n_phi) o[2 * P.n_f + u] = make_float2(aph[u].hi, aph[u].lo);
+#pragma unroll 1
+  for (int v = 0; v < P.n_f; ++v) {
+    R acc(0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < 12; ++k) acc += rad_raw(P.f[v], pr[k]) * pw[k];
+    const R st = rad_raw(P.f[v], pr[12]) * pw[12];
+    o[v] = make_float2(st.hi, st.lo);
+    o[P.n_f + v] = make_float2(acc.hi, acc.lo);
+  }
+#pragma unroll 1
+  for (int u = 0; u < P.n_phi; ++u) {
+    R acc(0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < 12; ++k) acc += rad_raw(P.phi[u], pr[k]) * pw[k];
+    o[2 * P.n_f + u] = make_float2(acc.hi, acc.lo);
+  }
   if (bad) atomicOr(A.flags, kFlagGeometry);
 }
 

@@ -410,9 +410,11 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   const int base = B.nsys ? B.cell_base[sys] : 0;
   const CellStage cs = stage_cell(cell, base, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  uint32_t* buf = reinterpret_cast<uint32_t*>(cj + cand_cap) + (size_t)warp * max_row;
-  uint8_t* isb = reinterpret_cast<uint8_t*>(reinterpret_cast<uint32_t*>(cj + cand_cap) + (size_t)nwarps * max_row) +
-                 (size_t)warp * max_row;
+  // per warp: the row's entries and its sort keys (j << 1 | bond), 16-byte aligned
+  const int stride = (max_row + 3) & ~3;
+  uint32_t* rows = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(cj + cand_cap) + 15) & ~uintptr_t(15));
+  uint32_t* buf = rows + (size_t)warp * stride;
+  uint32_t* kw = rows + (size_t)(nwarps + warp) * stride;
   const float rl2f = (float)rl2, rb2f = (float)rb2;
   for (int h = hbeg + warp; h < hend; h += nwarps) {
     const int64_t i = cell_sites[h];
@@ -446,24 +448,28 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
         const int pos = m + __popc(msk & ((1u << lane) - 1u));
         if (pos < max_row) {
           buf[pos] = ent;
-          isb[pos] = r.bond ? 1 : 0;
+          kw[pos] = ((uint32_t)j << 1) | (r.bond ? 1u : 0u);
         }
       }
       m += __popc(msk);
     }
-    __syncwarp();
     if (m > max_row) m = max_row;  // cannot happen: max_row is the counted maximum
+    const int m4 = (m + 3) >> 2;
+    for (int e = m + lane; e < 4 * m4; e += 32) kw[e] = 0xFFFFFFFFu;  // pads rank after every key
+    __syncwarp();
     const int off = nb_off[i], boff = bd_off[i];
+    const uint4* k4 = reinterpret_cast<const uint4*>(kw);
     for (int e = lane; e < m; e += 32) {
-      const uint32_t je = buf[e] & kIdxMask;
+      const uint32_t ke = kw[e] & ~1u;  // j << 1: keys of smaller j are below it
       int rank = 0, brank = 0;
-      for (int f = 0; f < m; ++f) {
-        const int less = (buf[f] & kIdxMask) < je;
-        rank += less;
-        brank += less & isb[f];
+      for (int f = 0; f < m4; ++f) {
+        const uint4 v = k4[f];
+        const uint32_t l0 = v.x < ke, l1 = v.y < ke, l2 = v.z < ke, l3 = v.w < ke;
+        rank += (int)(l0 + l1 + l2 + l3);
+        brank += (int)((l0 & v.x) + (l1 & v.y) + (l2 & v.z) + (l3 & v.w));
       }
       nb_ent[off + rank] = buf[e];
-      if (isb[e]) bd_idx[boff + brank] = (int)je;
+      if (kw[e] & 1u) bd_idx[boff + brank] = (int)(ke >> 1);
     }
     __syncwarp();
   }
@@ -705,7 +711,7 @@ cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const Batch& B, con
 
 size_t cell_stage_bytes(int cand_cap, int max_row, bool fill) {
   size_t b = (size_t)cand_cap * (sizeof(float4) + sizeof(int));
-  if (fill) b += (size_t)(kCellThreads / 32) * (size_t)max_row * 5;
+  if (fill) b += 16 + (size_t)(kCellThreads / 32) * 2 * (size_t)((max_row + 3) & ~3) * sizeof(uint32_t);
   return b + 16;
 }
 
