@@ -83,6 +83,10 @@ struct mxe_ctx {
   float4 *ent_dens = nullptr, *ent_frc = nullptr;                     // [entries] FP32 relaxation records
   bool relax_records = false;  // allocate them (first relaxation of the context, then with every list growth)
   int64_t pair_cap = 0, n_upairs = 0;
+  // rows of a fill without a count pass, at a fixed stride
+  uint32_t* rows_tmp = nullptr;
+  int* brows_tmp = nullptr;
+  int64_t rows_cap = 0;
 
   // per-site work arrays
   double *rho_bar = nullptr, *rho_avg = nullptr, *a = nullptr, *b = nullptr, *e = nullptr;
@@ -485,9 +489,35 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   // MXE_NEIGHBOR_PER_SITE forces the warp-per-site kernels (they are the
   // fallback for stencils too dense for shared memory; tests compare both)
   const bool staged = cell_stage_bytes(cand_cap, 256, true) <= 64 * 1024 && !std::getenv("MXE_NEIGHBOR_PER_SITE");
-  // counts
+  // counts: from a fill at a fixed stride when the previous build's longest row
+  // bounds it (no count pass), else a count pass before the fill
   const double rl2 = r_list * r_list, rb2 = r_bond * r_bond;
-  if (staged) {
+  bool direct = false;
+  int stride = 0;
+  if (staged && c->max_row_h > 0 && c->max_row_h + 16 <= 256 && !std::getenv("MXE_NEIGHBOR_COUNT")) {
+    stride = (c->max_row_h + 16 + 3) & ~3;
+    if ((int64_t)n * stride > c->rows_cap) {
+      dfree(c->rows_tmp);
+      dfree(c->brows_tmp);
+      CK(dalloc(&c->rows_tmp, (int64_t)n * stride));
+      CK(dalloc(&c->brows_tmp, (int64_t)n * stride));
+      c->rows_cap = (int64_t)n * stride;
+    }
+    CK(TIMED("build_fill", launch_cell_fill_direct(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, B,
+                                                   c->cell_start, c->cell_sites, c->abs_cell, rl2, rb2, band, cand_cap,
+                                                   stride, c->rows_tmp, c->brows_tmp, c->nb_cnt, c->bd_cnt,
+                                                   c->max_row, c->flags, st)));
+    CK(TIMED("build_misc", launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st)));
+    CK(TIMED("build_misc", launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st)));
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->ints_h, c->max_row, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    direct = c->ints_h[0] <= stride;  // else a row did not fit: count + fill
+    if (!direct) CK(cudaMemsetAsync(c->max_row, 0, sizeof(int), st));
+  }
+  if (direct) {
+    // counts, offsets and totals are in place
+  } else if (staged) {
     CK(TIMED("build_count", launch_cell_count(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, B, c->cell_start,
                                               c->cell_sites, rl2, rb2, band, cand_cap, c->nb_cnt, c->bd_cnt,
                                               c->max_row, c->flags, st)));
@@ -496,11 +526,13 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
                                              c->cell_start, c->cell_sites, rl2, rb2, band, c->nb_cnt, c->bd_cnt,
                                              c->max_row, st)));
   }
-  CK(TIMED("build_misc", launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st)));
-  CK(TIMED("build_misc", launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st)));
-  CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(c->ints_h, c->max_row, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  if (!direct) {
+    CK(TIMED("build_misc", launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st)));
+    CK(TIMED("build_misc", launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st)));
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->ints_h, c->max_row, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
   const long long npairs = c->totals_h[1], nbonds = c->totals_h[2];
   if (npairs > 2147483647LL || nbonds > 2147483647LL) return MXE_ERR_NBR_OVERFLOW;
   if (npairs > c->nb_cap) {
@@ -537,7 +569,10 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   }
   const int max_row = c->ints_h[0];
   if ((int64_t)max_row * 5 > 200 * 1024) return MXE_ERR_NBR_OVERFLOW;
-  if (staged && max_row <= 256) {
+  if (direct) {
+    CK(TIMED("build_misc", launch_row_compact(c->rows_tmp, c->brows_tmp, stride, n, c->nb_off, c->bd_off, c->nb_ent,
+                                              c->bd_idx, st)));
+  } else if (staged && max_row <= 256) {
     CK(TIMED("build_fill", launch_cell_fill(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, B, c->cell_start,
                                             c->cell_sites, c->abs_cell, rl2, rb2, band, cand_cap, c->nb_off,
                                             c->nb_ent, c->bd_off, c->bd_idx, max_row, c->flags, st)));
@@ -1178,6 +1213,8 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->pair_t);
   dfree(c->pid);
   dfree(c->pair_buf);
+  dfree(c->rows_tmp);
+  dfree(c->brows_tmp);
   dfree(c->pair_rev);
   dfree(c->ent_dens);
   dfree(c->ent_frc);

@@ -161,6 +161,16 @@ cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t
 cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
                              const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pair_rev, int* pid,
                              int* flags, cudaStream_t s);
+// fill without a count pass: rows at a fixed stride (the previous build's
+// longest row plus a margin), counts and the longest row; then the scan of the
+// counts and the compaction into the CSR (a longer row: count + fill instead)
+cudaError_t launch_cell_fill_direct(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask,
+                                    int64_t n, int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start,
+                                    const int* cell_sites, const int* abs_cell, double rl2, double rb2, float band,
+                                    int cand_cap, int stride, uint32_t* rows, int* brows, int* nb_cnt, int* bd_cnt,
+                                    int* row_max, int* flags, cudaStream_t s);
+cudaError_t launch_row_compact(const uint32_t* rows, const int* brows, int stride, int64_t n, const int* nb_off,
+                               const int* bd_off, uint32_t* nb_ent, int* bd_idx, cudaStream_t s);
 // exclusive scan of n int32 counts into out[0..n] (out[n] = total, int64 total in *total64)
 cudaError_t launch_scan(const int* in, int* out, int64_t n, long long* total64, int* tmp, int64_t tmp_len,
                         cudaStream_t s);

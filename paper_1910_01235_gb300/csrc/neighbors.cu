@@ -392,12 +392,18 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
   }
 }
 
+// DIRECT: no count pass before: row i goes to nb_ent[i * max_row ...] (max_row
+// = the stride, from the previous build) with its counts in nb_cnt / bd_cnt
+// and the longest row in *row_max; a row longer than the stride is cut and
+// its true length reported, so the caller can fall back to count + fill.
+template <bool DIRECT>
 __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
     int64_t n, DevGrid g0, Batch B, const int* __restrict__ cell_start, const int* __restrict__ cell_sites,
     const int* __restrict__ abs_cell, double rl2, double rb2, float band, int cand_cap,
     const int* __restrict__ nb_off, uint32_t* __restrict__ nb_ent, const int* __restrict__ bd_off,
-    int* __restrict__ bd_idx, int max_row, int* __restrict__ flags) {
+    int* __restrict__ bd_idx, int max_row, int* __restrict__ nb_cnt, int* __restrict__ bd_cnt,
+    int* __restrict__ row_max, int* __restrict__ flags) {
   extern __shared__ unsigned char smem[];
   __shared__ int s_off[28], s_beg[27];
   float4* cq = reinterpret_cast<float4*>(smem);
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     const int Ai[3] = {abs_cell[i], abs_cell[n + i], abs_cell[2 * n + i]};
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
-    int m = 0;
+    int m = 0, nbond = 0;
     for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
       const int t = t0 + lane;
       CandResult r{false, false, {0.f, 0.f, 0.f}};
@@ -452,12 +458,19 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
         }
       }
       m += __popc(msk);
+      if (DIRECT) nbond += __popc(__ballot_sync(0xffffffffu, r.bond));
     }
-    if (m > max_row) m = max_row;  // cannot happen: max_row is the counted maximum
+    if (DIRECT && lane == 0) {
+      nb_cnt[i] = m;
+      bd_cnt[i] = nbond;
+      atomicMax(row_max, m);
+    }
+    if (m > max_row) m = max_row;  // count + fill: cannot happen (max_row is the counted maximum)
     const int m4 = (m + 3) >> 2;
     for (int e = m + lane; e < 4 * m4; e += 32) kw[e] = 0xFFFFFFFFu;  // pads rank after every key
     __syncwarp();
-    const int off = nb_off[i], boff = bd_off[i];
+    const int64_t off = DIRECT ? i * (int64_t)max_row : (int64_t)nb_off[i];
+    const int64_t boff = DIRECT ? i * (int64_t)max_row : (int64_t)bd_off[i];
     const uint4* k4 = reinterpret_cast<const uint4*>(kw);
     for (int e = lane; e < m; e += 32) {
       const uint32_t ke = kw[e] & ~1u;  // j << 1: keys of smaller j are below it
@@ -656,6 +669,20 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
   }
 }
 
+
+// rows written at a fixed stride -> CSR (one warp per row)
+__global__ void k_row_compact(const uint32_t* __restrict__ rows, const int* __restrict__ brows, int stride, int64_t n,
+                              const int* __restrict__ nb_off, const int* __restrict__ bd_off,
+                              uint32_t* __restrict__ nb_ent, int* __restrict__ bd_idx) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int m = nb_off[i + 1] - nb_off[i], b = bd_off[i + 1] - bd_off[i];
+  const uint32_t* src = rows + i * (int64_t)stride;
+  const int* bsrc = brows + i * (int64_t)stride;
+  for (int e = lane; e < m; e += 32) nb_ent[nb_off[i] + e] = src[e];
+  for (int e = lane; e < b; e += 32) bd_idx[bd_off[i] + e] = bsrc[e];
+}
 }  // namespace
 
 cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, const Batch& B, int* cell_of,
@@ -736,11 +763,36 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
   if (n == 0 || ncell == 0) return cudaSuccess;
   if (max_row < 1) max_row = 1;
   const size_t shm = cell_stage_bytes(cand_cap, max_row, true);
-  cudaError_t e = cudaFuncSetAttribute(k_cell_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  cudaError_t e = cudaFuncSetAttribute(k_cell_fill<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
-  k_cell_fill<<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start, cell_sites,
-                                                         abs_cell, rl2, rb2, band, cand_cap, nb_off, nb_ent, bd_off,
-                                                         bd_idx, max_row, flags);
+  k_cell_fill<false><<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start,
+                                                                cell_sites, abs_cell, rl2, rb2, band, cand_cap, nb_off,
+                                                                nb_ent, bd_off, bd_idx, max_row, nullptr, nullptr,
+                                                                nullptr, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_fill_direct(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask,
+                                    int64_t n, int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start,
+                                    const int* cell_sites, const int* abs_cell, double rl2, double rb2, float band,
+                                    int cand_cap, int stride, uint32_t* rows, int* brows, int* nb_cnt, int* bd_cnt,
+                                    int* row_max, int* flags, cudaStream_t s) {
+  if (n == 0 || ncell == 0) return cudaSuccess;
+  const size_t shm = cell_stage_bytes(cand_cap, stride, true);
+  cudaError_t e = cudaFuncSetAttribute(k_cell_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  k_cell_fill<true><<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start,
+                                                               cell_sites, abs_cell, rl2, rb2, band, cand_cap, nullptr,
+                                                               rows, nullptr, brows, stride, nb_cnt, bd_cnt, row_max,
+                                                               flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_compact(const uint32_t* rows, const int* brows, int stride, int64_t n, const int* nb_off,
+                               const int* bd_off, uint32_t* nb_ent, int* bd_idx, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_row_compact<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(rows, brows, stride, n, nb_off, bd_off, nb_ent,
+                                                                  bd_idx);
   return cudaGetLastError();
 }
 

@@ -502,3 +502,32 @@ def test_empty_system(prec):
     st, it, fm = g.relax(1e-6, 10)
     assert st == M.OK and it == 0
     g.close()
+
+
+@pytest.mark.parametrize("case", ["single", "binary", "slab"])
+def test_second_build_without_count_pass_is_bit_exact(case):
+    """A context that has built once fills its next lists at a fixed stride
+    (previous longest row plus a margin) without a count pass; rows that
+    grow past the stride fall back to count + fill.  Both must give the
+    oracle's sets bit for bit."""
+    s = CASES[case]()
+    g = M.MxeSystem(s, "fp64")
+    g.build_neighbors()
+    rng = np.random.default_rng(29)
+    for grow in (0.0, 0.6):   # the second state: same widths, then much wider (longer rows)
+        t = s.copy()
+        t.q = s.q + rng.uniform(-0.05, 0.05, s.q.shape)
+        t.sigma = s.sigma + grow
+        g.q.copy_(torch.as_tensor(t.q, device=g.device))
+        g.sigma.copy_(torch.as_tensor(t.sigma, device=g.device))
+        g.build_neighbors()
+        off, idx = (a.cpu().numpy() for a in g.export_neighbors())
+        st, oo, oi = O.neighbors(t.q, t.L, g.r_list)
+        assert st == O.OK
+        np.testing.assert_array_equal(off, oo)
+        np.testing.assert_array_equal(idx, oi)
+        boff, bidx = (a.cpu().numpy() for a in g.export_bonds())
+        bo, bi = O.bonds(t, g.r_bond, oo, oi)
+        np.testing.assert_array_equal(boff, bo)
+        np.testing.assert_array_equal(bidx, bi)
+    g.close()
