@@ -602,6 +602,12 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   return MXE_OK;
 }
 
+// The FP32 force passes run on the half list: float-float context, pair index
+// and relaxation records present (allocated by the first relaxation).
+bool half_list_forces(const mxe_ctx* c) {
+  return c->precision == MXE_FP32_FF && c->pid && c->ent_dens && c->ent_frc && relax32_pairs_supported(c->dp);
+}
+
 // Free energy and gradients.  want_mu: the chemical potentials are requested.
 // The FP32 modes evaluate mu (and then the energies) with more accurate
 // density and chemical-potential passes -- FP64 in MXE_FP32_MIXED, float-float
@@ -637,7 +643,14 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
   if (A.gq != nullptr || A.gs != nullptr) {
     PassArgs F = A;
     F.site_E = nullptr;  // energies already come from the accurate pass
-    CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, F, st)));
+    if (half_list_forces(c)) {
+      // the relaxation's force pass: each unordered pair once, then the gather
+      CK(TIMED("pair32_force", launch_relax32_pair(true, c->dp, c->grid, F, c->pair_i, c->pair_t, c->pair_rev,
+                                                    c->n_upairs, c->ent_dens, c->ent_frc, st)));
+      CK(TIMED("gather32_force", launch_relax32_gather(true, c->nl, c->dp, F, c->ent_dens, c->ent_frc, st)));
+    } else {
+      CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, F, st)));
+    }
   }
   return MXE_OK;
 }
@@ -694,7 +707,7 @@ mxe_status ensure_relax_records(mxe_ctx* c) {
 // full-list passes.
 mxe_status enqueue_force_passes(mxe_ctx* c, const PassArgs& A) {
   cudaStream_t st = c->stream;
-  if (c->precision == MXE_FP32_FF && c->pid && c->ent_dens && c->ent_frc && relax32_pairs_supported(c->dp)) {
+  if (half_list_forces(c)) {
     // each unordered pair once: pair kernel, then the per-site gather
     CK(TIMED("pair32_density", launch_relax32_pair(false, c->dp, c->grid, A, c->pair_i, c->pair_t, c->pair_rev,
                                                     c->n_upairs, c->ent_dens, c->ent_frc, st)));

@@ -973,42 +973,64 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
       ra[k].team_reduce(NL);
     }
   }
-  if (!active || lane != 0) return;
-  const int64_t n = A.n;
-  int flag = 0;
-  float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+  // Per-site tail: team lane k < S takes species k (the FP64 square root and
+  // divisions then issue once per warp, not S times); the sums are those of
+  // team lane 0, so the result does not depend on which lane finishes it.
+  // Every lane reaches every shuffle.
+  static_assert(S <= 2 && NL >= S, "one team lane per species");
+  const int src = (int)(threadIdx.x & 31) - lane;
+  ff rbk(0.f, 0.f), rak(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const double rbar = rb[k].get();
-    const double ravg = ra[k].get() * (1.0 / 12.0);
+    const ff wb(__shfl_sync(0xffffffffu, rb[k].v.hi, src), __shfl_sync(0xffffffffu, rb[k].v.lo, src));
+    const ff wa(__shfl_sync(0xffffffffu, ra[k].v.hi, src), __shfl_sync(0xffffffffu, ra[k].v.lo, src));
+    if (lane == k) {
+      rbk = wb;
+      rak = wa;
+    }
+  }
+  const int64_t n = A.n;
+  const bool mine = active && lane < S;
+  float abk = 0.f, bbk = 0.f, lak = 0.f, lbk = 0.f;
+  if (mine) {
+    const int k = lane;
+    const double Ek = (S > 1 && k == 1) ? P.E[S > 1 ? 1 : 0] : P.E[0];
+    const double rbar = ff_to_double(rbk);
+    const double ravg = ff_to_double(rak) * (1.0 / 12.0);
     const double xk = A.x[k * n + i];
     double e = 0.0, ak = 0.0, bk = 0.0;
     if (rbar > kRhoMin) {
       const double sq = sqrt(rbar);
-      const double F = -P.E[k] * sq;
-      const double dF = -P.E[k] / (2.0 * sq);
-      const double d2F = P.E[k] / (4.0 * rbar * sq);
+      const double F = -Ek * sq;
+      const double dF = -Ek / (2.0 * sq);
+      const double d2F = Ek / (4.0 * rbar * sq);
       e = F + dF * (ravg - rbar);
       ak = xk * d2F * (ravg - rbar);
       bk = xk * dF;
     } else {
-      flag |= kFlagGeometry;
+      atomicOr(A.flags, kFlagGeometry);
     }
     A.rho_bar[k * n + i] = rbar;
     A.rho_avg[k * n + i] = ravg;
     A.e[k * n + i] = e;
     A.a[k * n + i] = ak;
     A.b[k * n + i] = bk;
-    ab[2 * k] = (float)ak;
-    ab[2 * k + 1] = (float)bk;
-    if (k < 2) {
-      lo[2 * k] = (float)(ak - (double)ab[2 * k]);
-      lo[2 * k + 1] = (float)(bk - (double)ab[2 * k + 1]);
-    }
+    abk = (float)ak;
+    bbk = (float)bk;
+    lak = (float)(ak - (double)abk);
+    lbk = (float)(bk - (double)bbk);
   }
+  // the packed FP32 (a, b) records of both species, written by team lane 0
+  float ab[4] = {abk, bbk, 0.f, 0.f}, lo[4] = {lak, lbk, 0.f, 0.f};
+  if (S > 1) {
+    ab[2] = __shfl_sync(0xffffffffu, abk, src + 1);
+    ab[3] = __shfl_sync(0xffffffffu, bbk, src + 1);
+    lo[2] = __shfl_sync(0xffffffffu, lak, src + 1);
+    lo[3] = __shfl_sync(0xffffffffu, lbk, src + 1);
+  }
+  if (!active || lane != 0) return;
   A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
   A.ab32lo[2 * i] = make_float4(lo[0], lo[1], lo[2], lo[3]);
-  if (flag) atomicOr(A.flags, flag);
 }
 
 template <int S, int NL>
@@ -1077,39 +1099,71 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
 #pragma unroll
     for (int k = 0; k < S; ++k) mu[k].team_reduce(NL);
   }
-  if (!active || lane != 0) return;
-  const int64_t n = A.n;
-  const double kT = kKB * A.T[i];
-  const double sg = A.sigma[i];
-  bool finite = true;
-  double xv = 1.0;
-#pragma unroll
-  for (int k = 0; k < S; ++k) xv -= A.x[k * n + i];
-  const double lv = log(fmax(xv, kLogFloor));
+  // Per-site tail on the first S + 2 team lanes, one FP64 logarithm each:
+  // lane k < S ln x_k (with the floor of the chemical potential), lane S
+  // ln x_v, lane S + 1 ln sigma; x ln x of the mixing entropy reuses them
+  // (a separate logarithm only for 0 < x below the floor).  The sums are
+  // those of team lane 0; every lane reaches every shuffle.
+  static_assert(NL >= S + 2, "one team lane per logarithm");
+  const int src = (int)(threadIdx.x & 31) - lane;
+  ff mk(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const double m = mu[k].get() + A.e[k * n + i];
-    finite = finite && isfinite(m);
-    if (A.mu_ex) A.mu_ex[k * n + i] = m;
-    if (A.mu) A.mu[k * n + i] = m + kT * (log(fmax(A.x[k * n + i], kLogFloor)) - lv);
+    const ff w(__shfl_sync(0xffffffffu, mu[k].v.hi, src), __shfl_sync(0xffffffffu, mu[k].v.lo, src));
+    if (lane == k) mk = w;
   }
-  if (A.site_E) {
-    double xr = 1.0, mix = 0.0, emb = 0.0;
+  const int64_t n = A.n;
+  double xk = 0.0, xv = 1.0;
+  if (active) {
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-      const double xk = A.x[k * n + i];
-      xr -= xk;
-      if (xk > 0.0) mix += xk * log(xk);
-      emb += xk * A.e[k * n + i];
+      const double v = A.x[k * n + i];
+      xv -= v;
+      if (lane == k) xk = v;
     }
-    if (xr > 0.0) mix += xr * log(xr);
-    const double EV = epair.get() + emb;
-    const double Fv = -3.0 * kT * log(sg);
-    const double Fm = kT * mix;
-    A.site_E[i] = EV;
-    A.site_E[n + i] = Fv;
-    A.site_E[2 * n + i] = Fm;
-    finite = finite && isfinite(EV) && isfinite(Fv) && isfinite(Fm);
+  }
+  double arg = 1.0;
+  if (active) {
+    if (lane < S) arg = fmax(xk, kLogFloor);
+    else if (lane == S) arg = fmax(xv, kLogFloor);
+    else if (lane == S + 1 && A.site_E) arg = A.sigma[i];
+  }
+  const double L = log(arg);
+  const double lv = __shfl_sync(0xffffffffu, L, src + S);
+  bool finite = true;
+  if (active && lane < S) {
+    const double kT = kKB * A.T[i];
+    const double m = ff_to_double(mk) + A.e[lane * n + i];
+    finite = isfinite(m);
+    if (A.mu_ex) A.mu_ex[lane * n + i] = m;
+    if (A.mu) A.mu[lane * n + i] = m + kT * (L - lv);
+  }
+  if (A.site_E) {
+    const double xs = lane < S ? xk : xv;
+    double t = 0.0;
+    if (active && lane <= S && xs > 0.0) t = xs * (xs >= kLogFloor ? L : log(xs));
+    double tk[S + 1];
+#pragma unroll
+    for (int k = 0; k <= S; ++k) tk[k] = __shfl_sync(0xffffffffu, t, src + k);
+    const double Ls = __shfl_sync(0xffffffffu, L, src + S + 1);
+    if (active && lane == 0) {
+      const double kT = kKB * A.T[i];
+      double mix = 0.0, emb = 0.0;
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        const double x = A.x[k * n + i];
+        if (x > 0.0) mix += tk[k];
+        emb += x * A.e[k * n + i];
+      }
+      if (xv > 0.0) mix += tk[S];
+      const double EV = epair.get() + emb;
+      const double Fv = -3.0 * kT * Ls;
+      const double Fm = kT * mix;
+      A.site_E[i] = EV;
+      A.site_E[n + i] = Fv;
+      A.site_E[2 * n + i] = Fm;
+      finite = finite && isfinite(EV) && isfinite(Fv) && isfinite(Fm);
+    }
   }
   if (!finite) atomicOr(A.flags, kFlagNonfinite);
 }
@@ -1422,19 +1476,36 @@ __global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const float4
     for (int c = 0; c < 3; ++c) g[c].team_reduce(NL);
     gsig.team_reduce(NL);
   }
-  if (!active || lane != 0) return;
-  const int64_t n = A.n;
-  const double g0 = g[0].get(), g1 = g[1].get(), g2 = g[2].get();
-  const float2 gp = gsig.get_pair();
-  const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)A.sigma[i];
-  const double gs = (double)((gp.x - th) + gp.y);
-  if (A.gq) {
-    A.gq[i] = g0;
-    A.gq[n + i] = g1;
-    A.gq[2 * n + i] = g2;
+  // Per-site tail: team lanes 0-2 the force components, lane 3 the width
+  // derivative with its thermal term, each from team lane 0's sums, so the
+  // float -> double conversions issue once per warp.
+  static_assert(NL >= 4, "one team lane per output");
+  const int src = (int)(threadIdx.x & 31) - lane;
+  float hi = 0.f, lo = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float h = __shfl_sync(0xffffffffu, g[c].hi, src), l = __shfl_sync(0xffffffffu, g[c].lo, src);
+    if (lane == c) {
+      hi = h;
+      lo = l;
+    }
   }
-  if (A.gs) A.gs[i] = gs;
-  if (!(isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs))) atomicOr(A.flags, kFlagNonfinite);
+  const float2 gp =
+      make_float2(__shfl_sync(0xffffffffu, gsig.hi, src), __shfl_sync(0xffffffffu, gsig.lo, src));
+  if (!active || lane > 3) return;
+  const int64_t n = A.n;
+  if (lane == 3) {
+    const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)A.sigma[i];
+    hi = (gp.x - th) + gp.y;
+    lo = 0.f;
+  }
+  const double v = (double)hi + (double)lo;
+  if (lane < 3) {
+    if (A.gq) A.gq[lane * n + i] = v;
+  } else if (A.gs) {
+    A.gs[i] = v;
+  }
+  if (!isfinite(v)) atomicOr(A.flags, kFlagNonfinite);
 }
 
 // ---------------------------------------------------------------- K7: pack
