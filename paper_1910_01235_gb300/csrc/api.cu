@@ -54,7 +54,7 @@ struct mxe_ctx {
   int* cell_count = nullptr;
   int* cell_start = nullptr;
   int* cell_sites = nullptr;
-  float4* qf = nullptr;  // FP32 copies of the positions for the neighbour prefilter
+  float4* qf = nullptr;  // [2][n] FP32 positions for the neighbour prefilter: absolute, then within the cell
   int64_t ncell_cap = 0;
 
   // neighbour / bond CSR
@@ -463,8 +463,12 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   // doubled for a differing image choice near half a box; then
   // | |d|^2_f32 - |d|^2 | <= 2 sqrt3 r delta + 3 delta^2 + 3 u r^2, plus u r^2
   // for the rounded cutoff; the band is twice that.
+  // The cell-staged kernels on grids of >= 3 cells per axis take d from
+  // positions within the cell (|.| <= h) and the stencil offset times h_f:
+  // per component at most 8 u h (the two rounded positions, h_f, the shifted
+  // candidate, the difference) <= 8 u Lmax / 3, the second bound below.
   const double u = std::ldexp(1.0, -24);
-  const double delta = 2.0 * (6.0 * u * qmax + u * Lmax + u * r_list);
+  const double delta = std::max(2.0 * (6.0 * u * qmax + u * Lmax + u * r_list), 8.0 * u * Lmax / 3.0);
   const double band_d = 2.0 * (2.0 * std::sqrt(3.0) * r_list * delta + 3.0 * delta * delta + 4.0 * u * r_list * r_list);
   const float band = (float)(band_d * (1.0 + 1e-6));
   mxe_status ms = ensure_cells(c, ncell);
@@ -1125,7 +1129,7 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
   A(dalloc(&c->totals, 4));
   A(dalloc(&c->max_row, 2));
   A(dalloc(&c->smax_bits, 2));
-  A(dalloc(&c->qf, n));
+  A(dalloc(&c->qf, 2 * n));
   A(dalloc(&c->q_build, 3 * n));
   A(dalloc(&c->rho_bar, S * n));
   A(dalloc(&c->rho_avg, S * n));

@@ -30,6 +30,7 @@ __global__ void k_cell_assign(const double* __restrict__ q, int64_t n, DevGrid g
   const int base = B.nsys ? B.cell_base[B.sys_of[i]] : 0;
   qf[i] = make_float4((float)q[i], (float)q[n + i], (float)q[2 * n + i], 0.f);
   int c3[3];
+  float rel[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double u = q[a * n + i] * g.invL[a];
@@ -37,8 +38,11 @@ __global__ void k_cell_assign(const double* __restrict__ q, int64_t n, DevGrid g
     int c = (int)((u - w) * g.nc[a]);
     c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
     c3[a] = c;
-    abs_cell[a * n + i] = (int)w * g.nc[a] + c;
+    const int ac = (int)w * g.nc[a] + c;
+    abs_cell[a * n + i] = ac;
+    rel[a] = (float)(q[a * n + i] - (double)ac * g.h[a]);  // position within its cell
   }
+  qf[n + i] = make_float4(rel[0], rel[1], rel[2], 0.f);
   int cell = base + (c3[0] * g.nc[1] + c3[1]) * g.nc[2] + c3[2];
   cell_of[i] = cell;
   cell_slot[i] = atomicAdd(&cell_count[cell], 1);
@@ -280,12 +284,19 @@ constexpr int kCellThreads = 128;
 
 struct CellStage {
   int ncand;
+  // Every axis has >= 3 cells of width >= r_list: then a pair within r_list
+  // has one image, that of the stencil cell, and the staged candidates carry
+  // their image code (cj = j | code << kCodeShift) and their position in the
+  // home cell's frame (cell-relative position + offset x cell width).
+  bool fast;
 };
 
-__device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGrid& g, const int* __restrict__ cell_start,
+__device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGrid& g, int64_t n,
+                                                const int* __restrict__ cell_start,
                                                 const int* __restrict__ cell_sites, const float4* __restrict__ qf,
-                                                float4* cq, int* cj, int* s_off, int* s_beg, int cand_cap,
-                                                int* __restrict__ flags) {
+                                                float4* cq, int* cj, int* s_off, int* s_beg, float* s_sh,
+                                                int cand_cap, int* __restrict__ flags) {
+  const bool fast = g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3;
   if (threadIdx.x == 0) {
     const Stencil st = make_stencil(cell - base, g);
     int k = 0, tot = 0;
@@ -295,6 +306,10 @@ __device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGri
           const int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
           s_beg[k] = cell_start[c];
           s_off[k] = tot;
+          // without duplicates index t of an axis is the offset t - 1, and k the image code
+          s_sh[3 * k + 0] = (float)(ax - 1) * g.h_f[0];
+          s_sh[3 * k + 1] = (float)(ay - 1) * g.h_f[1];
+          s_sh[3 * k + 2] = (float)(az - 1) * g.h_f[2];
           tot += cell_start[c + 1] - cell_start[c];
           ++k;
         }
@@ -310,11 +325,17 @@ __device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGri
     int k = 0;
     while (t >= s_off[k + 1]) ++k;
     const int j = cell_sites[s_beg[k] + (t - s_off[k])];
-    cj[t] = j;
-    cq[t] = qf[j];
+    if (fast) {
+      const float4 r = qf[n + j];
+      cj[t] = (int)((uint32_t)j | ((uint32_t)k << kCodeShift));
+      cq[t] = make_float4(r.x + s_sh[3 * k], r.y + s_sh[3 * k + 1], r.z + s_sh[3 * k + 2], 0.f);
+    } else {
+      cj[t] = j;
+      cq[t] = qf[j];
+    }
   }
   __syncthreads();
-  return CellStage{ncand};
+  return CellStage{ncand, fast};
 }
 
 // Decisions for home site i against staged candidate t (FP64 rule inside the band).
@@ -352,6 +373,31 @@ __device__ __forceinline__ CandResult test_cand(int64_t i, const double qi[3], c
   return r;
 }
 
+// The same decisions from home-frame FP32 positions (CellStage::fast): the
+// image is the stencil cell's, so no image search; FP64 inside the band.
+__device__ __forceinline__ CandResult test_cand_rel(int64_t i, const double qi[3], const float4& ri, int j,
+                                                    const float4& rj, const double* __restrict__ q, int64_t n,
+                                                    const DevGrid& g, float rl2f, float rb2f, float band, double rl2,
+                                                    double rb2, bool mob, int si, const uint8_t* __restrict__ sub) {
+  CandResult r{false, false, {0.f, 0.f, 0.f}};
+  if (j == (int)i) return r;
+  const float dx = rj.x - ri.x, dy = rj.y - ri.y, dz = rj.z - ri.z;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  int din = decide_f(r2, rl2f, band);
+  int dbo = decide_f(r2, rb2f, band);
+  if (din < 0 || (din > 0 && dbo < 0)) {
+    const PairTest pt = pair_test(qi, q, n, j, g);
+    din = pt.r2 < rl2;
+    dbo = pt.r2 < rb2;
+  }
+  r.in = din > 0;
+  if (r.in && mob) {
+    const int sj = sub ? sub[j] : 0;
+    r.bond = sj == si && dbo > 0;
+  }
+  return r;
+}
+
 __global__ void __launch_bounds__(kCellThreads) k_cell_count(
     const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
     int64_t n, DevGrid g0, Batch B, const int* __restrict__ cell_start, const int* __restrict__ cell_sites, double rl2,
@@ -359,6 +405,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
     int* __restrict__ max_row, int* __restrict__ flags) {
   extern __shared__ unsigned char smem[];
   __shared__ int s_off[28], s_beg[27];
+  __shared__ float s_sh[27 * 3];
   float4* cq = reinterpret_cast<float4*>(smem);
   int* cj = reinterpret_cast<int*>(cq + cand_cap);
   const int cell = blockIdx.x;
@@ -367,20 +414,25 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
   const int sys = B.nsys ? B.cell_sys[cell] : 0;
   const DevGrid g = B.nsys ? B.grids[sys] : g0;
   const int base = B.nsys ? B.cell_base[sys] : 0;
-  const CellStage cs = stage_cell(cell, base, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
+  const CellStage cs =
+      stage_cell(cell, base, g, n, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, s_sh, cand_cap, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float rl2f = (float)rl2, rb2f = (float)rb2;
   for (int h = hbeg + warp; h < hend; h += nwarps) {
     const int64_t i = cell_sites[h];
     const double qi[3] = {q[i], q[n + i], q[2 * n + i]};
-    const float4 qfi = qf[i];
+    const float4 qfi = cs.fast ? qf[n + i] : qf[i];
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
     int cnt = 0, bcnt = 0;
     for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
       const int t = t0 + lane;
       CandResult r{false, false, {0.f, 0.f, 0.f}};
-      if (t < cs.ncand) r = test_cand(i, qi, qfi, cj[t], cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, false);
+      if (t < cs.ncand) {
+        const int j = (int)((uint32_t)cj[t] & kIdxMask);
+        r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
+                    : test_cand(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, false);
+      }
       cnt += __popc(__ballot_sync(0xffffffffu, r.in));
       bcnt += __popc(__ballot_sync(0xffffffffu, r.bond));
     }
@@ -406,6 +458,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     int* __restrict__ row_max, int* __restrict__ flags) {
   extern __shared__ unsigned char smem[];
   __shared__ int s_off[28], s_beg[27];
+  __shared__ float s_sh[27 * 3];
   float4* cq = reinterpret_cast<float4*>(smem);
   int* cj = reinterpret_cast<int*>(cq + cand_cap);
   const int cell = blockIdx.x;
@@ -414,7 +467,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   const int sys = B.nsys ? B.cell_sys[cell] : 0;
   const DevGrid g = B.nsys ? B.grids[sys] : g0;
   const int base = B.nsys ? B.cell_base[sys] : 0;
-  const CellStage cs = stage_cell(cell, base, g, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, cand_cap, flags);
+  const CellStage cs =
+      stage_cell(cell, base, g, n, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, s_sh, cand_cap, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   // per warp: the row's entries and its sort keys (j << 1 | bond), 16-byte aligned
   const int stride = (max_row + 3) & ~3;
@@ -425,25 +479,26 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   for (int h = hbeg + warp; h < hend; h += nwarps) {
     const int64_t i = cell_sites[h];
     const double qi[3] = {q[i], q[n + i], q[2 * n + i]};
-    const float4 qfi = qf[i];
-    const int Ai[3] = {abs_cell[i], abs_cell[n + i], abs_cell[2 * n + i]};
+    const float4 qfi = cs.fast ? qf[n + i] : qf[i];
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
     int m = 0, nbond = 0;
     for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
       const int t = t0 + lane;
       CandResult r{false, false, {0.f, 0.f, 0.f}};
+      uint32_t ent = 0;
       int j = 0;
       if (t < cs.ncand) {
-        j = cj[t];
-        r = test_cand(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
+        ent = (uint32_t)cj[t];
+        j = (int)(ent & kIdxMask);
+        r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
+                    : test_cand(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
       }
-      uint32_t ent = 0;
-      if (r.in) {
+      if (r.in && !cs.fast) {
         int code = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          int sh = abs_cell[a * n + j] - Ai[a] - g.nc[a] * (int)r.k[a];
+          int sh = abs_cell[a * n + j] - abs_cell[a * n + i] - g.nc[a] * (int)r.k[a];
           sh = sh < -1 ? -1 : (sh > 1 ? 1 : sh);
           code = code * 3 + (sh + 1);
         }
