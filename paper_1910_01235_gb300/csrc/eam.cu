@@ -1477,26 +1477,22 @@ __global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const float4
     gsig.team_reduce(NL);
   }
   // Per-site tail: team lanes 0-2 the force components, lane 3 the width
-  // derivative with its thermal term, each from team lane 0's sums, so the
-  // float -> double conversions issue once per warp.
+  // derivative with its thermal term, so the float -> double conversions
+  // issue once per warp.  After the butterfly every team lane holds the
+  // whole sum (a lane's own rounding order: fixed, so runs repeat exactly).
   static_assert(NL >= 4, "one team lane per output");
-  const int src = (int)(threadIdx.x & 31) - lane;
-  float hi = 0.f, lo = 0.f;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float h = __shfl_sync(0xffffffffu, g[c].hi, src), l = __shfl_sync(0xffffffffu, g[c].lo, src);
-    if (lane == c) {
-      hi = h;
-      lo = l;
-    }
-  }
-  const float2 gp =
-      make_float2(__shfl_sync(0xffffffffu, gsig.hi, src), __shfl_sync(0xffffffffu, gsig.lo, src));
   if (!active || lane > 3) return;
   const int64_t n = A.n;
-  if (lane == 3) {
+  float hi = g[0].hi, lo = g[0].lo;
+  if (lane == 1) {
+    hi = g[1].hi;
+    lo = g[1].lo;
+  } else if (lane == 2) {
+    hi = g[2].hi;
+    lo = g[2].lo;
+  } else if (lane == 3) {
     const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)A.sigma[i];
-    hi = (gp.x - th) + gp.y;
+    hi = (gsig.hi - th) + gsig.lo;
     lo = 0.f;
   }
   const double v = (double)hi + (double)lo;
