@@ -325,15 +325,20 @@ __device__ __forceinline__ bool skin_violated(const Ctrl* c) {
 }
 
 // Uniform early exit of the relaxation chunk.  Returns true if the kernel must
-// stop.  One thread per block evaluates the test (its FP64 square root would
-// otherwise run once per thread on the slow FP64 pipe) and shares it; every
-// thread of the block must call this before any early return.
+// stop.  The skin test runs once per launch, on thread 0 of block 0 (on the
+// 1:64 FP64 pipe a test per block kept the FP64 pipe a quarter busy and held
+// every block at the barrier behind it); each block reads the halt flag
+// through one thread.  Blocks that start before block 0 sets the flag run the
+// pass on the old lists (valid arrays, so every access stays in bounds); a
+// halted pass is always evaluated again after the rebuild, so that output is
+// never used.  Every thread of the block must call this before any early
+// return.
 __device__ __forceinline__ bool chunk_halted(const PassArgs& A) {
   if (A.ctrl == nullptr) return false;
   __shared__ int halt;
   if (threadIdx.x == 0) {
     int h = A.ctrl->halted ? 1 : 0;
-    if (!h && A.check_skin && skin_violated(A.ctrl)) {
+    if (!h && blockIdx.x == 0 && A.check_skin && skin_violated(A.ctrl)) {
       A.ctrl->reason = kReasonRebuild;
       A.ctrl->halted = 1;
       h = 1;
