@@ -65,8 +65,10 @@ __global__ void __launch_bounds__(kRedThreads) k_fire_reduce(const double* __res
     P += -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
     vv += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
     ff += g0 * g0 + g1 * g1 + g2 * g2 + f3 * f3;
-    double gqn = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
-    fm = fmax(fm, fmax(gqn, fabs(f3)));
+    // the largest squared force component norm; its square root is taken
+    // once, by the logic kernel (sqrt is monotone and correctly rounded, so
+    // sqrt(max) == max(sqrt))
+    fm = fmax(fm, fmax(g0 * g0 + g1 * g1 + g2 * g2, f3 * f3));
     finite = finite && isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs[i]);
   }
   sh[0][tid] = P;
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(256) k_fire_logic(const double* __restrict__ p
   if (tid != 0) return;
   Ctrl& C = *ctrl;
   const double P = sh[0][0], vv = sh[1][0], ff = sh[2][0];
-  const double fmx = __longlong_as_double((long long)C.fmax_bits);
+  const double fmx = sqrt(__longlong_as_double((long long)C.fmax_bits));
   C.fmax = fmx;
   if (*flags & (kFlagGeometry | kFlagNonfinite)) {
     C.halted = 1;
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(256) k_fire_seg_reduce(const double* __restric
     P += -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
     vv += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
     ff += g0 * g0 + g1 * g1 + g2 * g2 + f3 * f3;
-    fm = fmax(fm, fmax(sqrt(g0 * g0 + g1 * g1 + g2 * g2), fabs(f3)));
+    fm = fmax(fm, fmax(g0 * g0 + g1 * g1 + g2 * g2, f3 * f3));  // squared; one sqrt per system below
     finite = finite && isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs[i]);
   }
   if (!finite) atomicOr(flags, kFlagNonfinite);
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(256) k_fire_seg_reduce(const double* __restric
     sf[sys].P = sh[0][0];
     sf[sys].vv = sh[1][0];
     sf[sys].ff = sh[2][0];
-    sf[sys].fmax = sh[3][0];
+    sf[sys].fmax = sqrt(sh[3][0]);
   }
 }
 
