@@ -448,13 +448,15 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
       for (int k = 0; k < S; ++k) {
         R sb = (R)0, sa = (R)0;
 #pragma unroll
-        for (int l = 0; l < S; ++l)
+        for (int l = 0; l < S; ++l) {
+          const int fo = P.f_of[k][l];
 #pragma unroll
           for (int v = 0; v < NF; ++v)
-            if (P.f_of[k][l] == v) {
+            if (fo == v) {
               sb += sj.x[l] * fst[v];
               sa += sj.x[l] * fav[v];
             }
+        }
         rb[k].add(sb);
         ra[k].add(sa);
       }
@@ -619,12 +621,15 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
       for (int k = 0; k < S; ++k)
 #pragma unroll
         for (int l = 0; l < S; ++l) {
+          // table entries read once (compared inside the unrolled loops they
+          // sent a copy of the tables to the stack)
+          const int po = P.phi_of[k][l], fo = P.f_of[k][l];
 #pragma unroll
           for (int u = 0; u < NP; ++u)
-            if (P.phi_of[k][l] == u) cphi[u] += si.x[k] * sj.x[l];
+            if (po == u) cphi[u] += si.x[k] * sj.x[l];
 #pragma unroll
           for (int v = 0; v < NF; ++v)
-            if (P.f_of[k][l] == v) {
+            if (fo == v) {
               cfa[v] += bi[k] * sj.x[l] + bj[k] * si.x[l];
               cfs[v] += ai[k] * sj.x[l] + aj[k] * si.x[l];
             }
@@ -753,13 +758,14 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
         R m = (R)0;
 #pragma unroll
         for (int l = 0; l < S; ++l) {
+          const int po = P.phi_of[k][l], fo = P.f_of[l][k];
 #pragma unroll
           for (int u = 0; u < NP; ++u)
-            if (P.phi_of[k][l] == u) m += sj.x[l] * aphi[u] * inv12;
+            if (po == u) m += sj.x[l] * aphi[u] * inv12;
           // density at j of species l from this site holding species k: f_lk
 #pragma unroll
           for (int v = 0; v < NF; ++v)
-            if (P.f_of[l][k] == v) m += aj[l] * fst[v] + bj[l] * af[v] * inv12;
+            if (fo == v) m += aj[l] * fst[v] + bj[l] * af[v] * inv12;
         }
         mu[k].add(m);
       }
@@ -1377,12 +1383,15 @@ __global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, Pass
   for (int k = 0; k < S; ++k)
 #pragma unroll
     for (int l = 0; l < S; ++l) {
+      // table entries read once (compared inside the unrolled loops they
+      // sent a copy of the tables to the stack)
+      const int po = P.phi_of[k][l], fo = P.f_of[k][l];
 #pragma unroll
       for (int u = 0; u < NP; ++u)
-        if (P.phi_of[k][l] == u) cphi[u] += si.x[k] * sj.x[l];
+        if (po == u) cphi[u] += si.x[k] * sj.x[l];
 #pragma unroll
       for (int v = 0; v < NF; ++v)
-        if (P.f_of[k][l] == v) {
+        if (fo == v) {
           cfa[v] += bi[k] * sj.x[l] + bj[k] * si.x[l];
           cfs[v] += ai[k] * sj.x[l] + aj[k] * si.x[l];
         }
