@@ -173,7 +173,7 @@ def test_sigma_to_zero_reproduces_static_eam(which):
 
 def test_perfect_lattice_reference_values():
     """Perfect FCC a = 3.6 A, x = 1 (values recomputed independently with
-    numpy while surveying the method): E_V/site -1.198691 eV at sigma -> 0
+    numpy, outside the oracle): E_V/site -1.198691 eV at sigma -> 0
     and -1.230738 eV at sigma = 0.1 A, dE_V/dsigma_i = -0.69263 eV/A."""
     s = W.config_vacancy_lattice(x0=1.0)
     s.x[:] = 1.0
