@@ -99,6 +99,7 @@ def lib():
             L.orc_pair_average_value.argtypes = [p, C.c_int, C.c_int, C.c_int, p, C.c_double, C.c_double]
             L.orc_pair_average_value.restype = C.c_double
             L.orc_free_energy.argtypes = [p, p, p, p, C.c_int] + [p] * 10
+            L.orc_free_energy_exact.argtypes = [p, p, p, p] + [p] * 6
             L.orc_diffuse_step.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double, C.c_double]
             L.orc_diffuse_step_res.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double,
                                                C.c_double, p, p, p, p]
@@ -253,6 +254,29 @@ def free_energy(sys, nb=None, mode=0, q=None, sigma=None, x=None, r_list=None):
     st = lib().orc_free_energy(C.byref(ref.s), C.byref(P), _ptr(off), _ptr(idx), int(mode),
                                *[_ptr(out[k]) for k in ("F4", "gq", "gs", "mu_ex", "mu", "rho_bar",
                                                         "rho_avg", "a", "b", "e")])
+    out["status"] = int(st)
+    return out
+
+
+def free_energy_exact(sys, nb=None, q=None, sigma=None, x=None, r_list=None):
+    """Free energy and gradients with the exact phase average of the
+    embedding term (App. B.2: App. A's third-degree rule over a site and its
+    neighbours inside r_cut, in place of the Taylor form Eq. F_taylor_mxe).
+    Returns a dict with status, F4, gq, gs, mu_ex, mu and emb [S, n] =
+    <F_k(rho_i^k)>."""
+    ref = _SysRef(sys, q, sigma, x)
+    n, S = sys.n, ref.x.shape[0]
+    if nb is None:
+        rl = r_list if r_list is not None else sys.pot.r_cut + np.sqrt(6.0) * float(ref.sigma.max()) + 0.2
+        st, off, idx = neighbors(ref.q, sys.L, rl)
+        assert st == OK, st
+    else:
+        off, idx = nb
+    P = make_potential(sys.pot)
+    out = dict(F4=np.zeros(4), gq=np.zeros((3, n)), gs=np.zeros(n), mu_ex=np.zeros((S, n)),
+               mu=np.zeros((S, n)), emb=np.zeros((S, n)))
+    st = lib().orc_free_energy_exact(C.byref(ref.s), C.byref(P), _ptr(off), _ptr(idx),
+                                     *[_ptr(out[k]) for k in ("F4", "gq", "gs", "mu_ex", "mu", "emb")])
     out["status"] = int(st)
     return out
 

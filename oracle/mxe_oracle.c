@@ -15,7 +15,8 @@
  *   neighbour sets        Sec. 4 / Algorithm 1 (neighbour list step), brute force
  *   quadrature nodes      App. A (third-degree rule, M = 2 N_q nodes, r^2 = N_q/2)
  *   thermalized EAM       App. B.2 (Eqs. EAM_mxe, F_taylor_mxe, EAM-Substitutional-ave,
- *                         EAM-density-substitutional-ave)
+ *                         EAM-density-substitutional-ave); the exact embedding average
+ *                         (App. A's rule over a site and its neighbours, before Eq. F_taylor)
  *   free energy           Sec. 2.1 (Eq. Grand-Canonical-Free-Energy) read per site as
  *                         <V_i> - 3 kB T_i ln sigma_i + kB T_i sum_k x ln x (vacancy included)
  *   gradients             derivatives of the above, written out term by term
@@ -639,6 +640,210 @@ int orc_free_energy(const orc_system *sys, const orc_potential *P,
     if (e_out) memcpy(e_out, e, sizeof(double) * S * n);
     free(rb); free(ra); free(A); free(B); free(e);
     free(site_EV); free(site_vib); free(site_mix);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact phase average of the embedding term (App. B.2: the third-degree rule
+ * of App. A applied to the many-body function F_k(rho_i), which the paper then
+ * replaces by its Taylor form, Eq. F_taylor_mxe).
+ *
+ * The rule of site i covers the N sites "inside the potential cut-off
+ * radius": i itself and every neighbour j with |qbar_j - qbar_i| < r_cut
+ * (the set J_i).  The many-body function is
+ *     F_k(rho_i^k),  rho_i^k = sum_{j in J_i} sum_l x_jl f_kl(|q_j - q_i|),
+ * a function of N_q = 3N coordinates.  The rule has M = 2 N_q nodes
+ * chi = +-r e_m, r^2 = N_q / 2, each with normalised weight 1/M; in physical
+ * units q - qbar = sqrt(2) sigma chi, so each node moves ONE site s of the
+ * rule by +-sigma_s sqrt(N_q) along one axis and leaves the others at their
+ * means:
+ *     <F_k(rho_i^k)> = (1/M) sum_nodes F_k(rho_i^k(node)).
+ * The free energy is that of orc_free_energy with every embedding term
+ * e_i^k replaced by <F_k(rho_i^k)>:
+ *     E_V = sum_i [1/2 sum_j sum_kl x_ik x_jl <phi_kl>_ij + sum_k x_ik <F_k(rho_i^k)>].
+ * Gradients, written out from the node sum (the rule's membership and N are
+ * held fixed: they change only where a mean distance crosses r_cut):
+ *   d/dq_j of F_k(rho(node)) = F_k'(rho(node)) sum_l x_jl f_kl'(r_ij) u_ij  (j in J_i),
+ *   and minus the sum of these for q_i (u_ij = (q_j - q_i)/r_ij at the node);
+ *   d/dsigma_s: the moved coordinate of a node moving s is qbar_s +- sigma_s
+ *   sqrt(N_q), so d/dsigma_s = +-sqrt(N_q) times the derivative along it;
+ *   d/dx_jl = x_ik (1/M) sum_nodes F_k'(rho(node)) f_kl(r_ij(node)),
+ *   d/dx_ik = <F_k(rho_i^k)>.
+ * GEOMETRY if a node distance is below ORC_RMIN or rho(node) <= ORC_RHO_MIN for
+ * an occupied element with an embedding energy.  Each thread accumulates the
+ * contributions of its sites in its own buffer; the buffers are added in
+ * thread order.  Outputs as orc_free_energy; emb_out [S][n] (optional)
+ * receives <F_k(rho_i^k)>.
+ */
+/* ------------------------------------------------------------------ */
+int orc_free_energy_exact(const orc_system *sys, const orc_potential *P,
+                          const int32_t *nb_off, const int32_t *nb_idx,
+                          double *F4, double *gq, double *gs, double *mu_ex, double *mu, double *emb_out)
+{
+    const int64_t n = sys->n;
+    const int S = sys->S;
+    if (S < 1 || S > ORC_MAXS || S != P->n_species) return ORC_ERR_ARG;
+    const double *q = sys->q, *sig = sys->sigma, *x = sys->x, *T = sys->T;
+
+    /* the pair terms, F_vib and F_mix: the same free energy with no embedding */
+    orc_potential P0 = *P;
+    for (int k = 0; k < ORC_MAXS; ++k) P0.E[k] = 0.0;
+    int status = orc_free_energy(sys, &P0, nb_off, nb_idx, 0, F4, gq, gs, mu_ex, NULL,
+                                 NULL, NULL, NULL, NULL, NULL);
+    if (status != ORC_OK && status != ORC_ERR_NONFINITE) return status;
+
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    const int64_t width = 4 + S;  /* per site: dF/dq (3), dF/dsigma, dE_V/dx (S) */
+    double *acc = (double *)calloc((size_t)(nthr * n * width + 1), sizeof(double));
+    double *emb = (double *)calloc((size_t)(S * n + 1), sizeof(double));
+    double *site_emb = (double *)calloc((size_t)(n + 1), sizeof(double));
+    int geometry = 0;
+#pragma omp parallel reduction(| : geometry)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *my = acc + (int64_t)tid * n * width;
+        int cap = 256;
+        int64_t *J = (int64_t *)malloc(sizeof(int64_t) * cap);
+        double *dbar = (double *)malloc(sizeof(double) * 3 * cap);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double qi[3];
+            load_q(q, n, i, qi);
+            /* the rule's sites: i and its neighbours inside r_cut */
+            int m = 0;
+            for (int32_t t = nb_off[i]; t < nb_off[i + 1]; ++t) {
+                int64_t j = nb_idx[t];
+                double qj[3], d[3];
+                load_q(q, n, j, qj);
+                min_image(sys->L, qi, qj, d);
+                if (!(sqrt(dist2(d)) < P->r_cut)) continue;
+                if (m == cap) {
+                    cap *= 2;
+                    J = (int64_t *)realloc(J, sizeof(int64_t) * cap);
+                    dbar = (double *)realloc(dbar, sizeof(double) * 3 * cap);
+                }
+                J[m] = j;
+                for (int c = 0; c < 3; ++c) dbar[3 * m + c] = d[c];
+                ++m;
+            }
+            const int N = m + 1;
+            const double Nq = 3.0 * N;
+            const int M = 2 * 3 * N;
+            const double w = 1.0 / (double)M;
+            const double hs = sqrt(Nq);   /* displacement / sigma of a node */
+            double e_site = 0.0;
+            for (int k = 0; k < S; ++k) {
+                double xik = x[k * n + i];
+                if (P->E[k] == 0.0) { emb[k * n + i] = 0.0; continue; }
+                double Fsum = 0.0;
+                /* node (s, a, pm): site s of the rule (0 = i, 1..m = J[s-1]) moved by
+                   pm sigma_s sqrt(N_q) along axis a */
+                for (int s_ = 0; s_ <= m; ++s_) {
+                    for (int a = 0; a < 3; ++a) {
+                        for (int pm = -1; pm <= 1; pm += 2) {
+                            double shift_i[3] = {0.0, 0.0, 0.0}, shift_s[3] = {0.0, 0.0, 0.0};
+                            int64_t site_s = (s_ == 0) ? i : J[s_ - 1];
+                            double h = pm * sig[site_s] * hs;
+                            if (s_ == 0) shift_i[a] = h;
+                            else shift_s[a] = h;
+                            /* density at the node */
+                            double rho = 0.0;
+                            for (int jj = 0; jj < m; ++jj) {
+                                int64_t j = J[jj];
+                                double v[3];
+                                for (int c = 0; c < 3; ++c)
+                                    v[c] = dbar[3 * jj + c] + (s_ == jj + 1 ? shift_s[c] : 0.0) - shift_i[c];
+                                double r = sqrt(dist2(v));
+                                if (r < ORC_RMIN) geometry = 1;
+                                for (int l = 0; l < S; ++l) {
+                                    double f, df;
+                                    f_fn(P, k, l, r, &f, &df);
+                                    rho += x[l * n + j] * f;
+                                }
+                            }
+                            if (!(rho > ORC_RHO_MIN)) {
+                                if (xik > 0.0) geometry = 1;
+                                continue;
+                            }
+                            double F, dF, d2F;
+                            embed_fn(P, k, rho, &F, &dF, &d2F);
+                            Fsum += F;
+                            /* derivatives of x_ik F_k(rho(node)) / M */
+                            double c0 = xik * dF * w;
+                            for (int jj = 0; jj < m; ++jj) {
+                                int64_t j = J[jj];
+                                double v[3];
+                                for (int c = 0; c < 3; ++c)
+                                    v[c] = dbar[3 * jj + c] + (s_ == jj + 1 ? shift_s[c] : 0.0) - shift_i[c];
+                                double r = sqrt(dist2(v));
+                                double gj = 0.0;
+                                for (int l = 0; l < S; ++l) {
+                                    double f, df;
+                                    f_fn(P, k, l, r, &f, &df);
+                                    gj += x[l * n + j] * df;
+                                    /* dE_V/dx_jl through rho_i^k */
+                                    my[j * width + 4 + l] += c0 * f;
+                                }
+                                for (int c = 0; c < 3; ++c) {
+                                    double gc = c0 * gj * v[c] / r;
+                                    my[j * width + c] += gc;   /* d/dq_j */
+                                    my[i * width + c] -= gc;   /* d/dq_i */
+                                }
+                                /* d/dsigma of the moved site: along axis a, +-sqrt(N_q) */
+                                double ga = c0 * gj * v[a] / r;
+                                if (s_ == 0) my[i * width + 3] -= ga * pm * hs;
+                                else if (s_ == jj + 1) my[j * width + 3] += ga * pm * hs;
+                            }
+                        }
+                    }
+                }
+                emb[k * n + i] = Fsum * w;
+                e_site += xik * emb[k * n + i];
+                /* dE_V/dx_ik through the factor x_ik */
+                my[i * width + 4 + k] += emb[k * n + i];
+            }
+            site_emb[i] = e_site;
+        }
+        free(J);
+        free(dbar);
+    }
+    if (geometry) {
+        free(acc); free(emb); free(site_emb);
+        return ORC_ERR_GEOMETRY;
+    }
+    for (int t = 1; t < nthr; ++t)
+        for (int64_t v = 0; v < n * width; ++v) acc[v] += acc[(int64_t)t * n * width + v];
+    double Eemb = pairwise_sum(site_emb, n);
+    F4[0] += Eemb;
+    F4[3] = F4[0] + F4[1] + F4[2];
+    status = isfinite(F4[3]) ? ORC_OK : ORC_ERR_NONFINITE;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) gq[c * n + i] += acc[i * width + c];
+        gs[i] += acc[i * width + 3];
+        double xv = 1.0;
+        for (int k = 0; k < S; ++k) xv -= x[k * n + i];
+        for (int k = 0; k < S; ++k) {
+            mu_ex[k * n + i] += acc[i * width + 4 + k];
+            if (mu) {
+                double kT = ORC_KB * T[i];
+                double lx = log(fmax(x[k * n + i], ORC_LOG_FLOOR));
+                double lv = log(fmax(xv, ORC_LOG_FLOOR));
+                mu[k * n + i] = mu_ex[k * n + i] + kT * (lx - lv);
+            }
+        }
+    }
+    for (int64_t v = 0; v < 3 * n && status == ORC_OK; ++v)
+        if (!isfinite(gq[v])) status = ORC_ERR_NONFINITE;
+    for (int64_t v = 0; v < n && status == ORC_OK; ++v)
+        if (!isfinite(gs[v])) status = ORC_ERR_NONFINITE;
+    if (emb_out) memcpy(emb_out, emb, sizeof(double) * S * n);
+    free(acc); free(emb); free(site_emb);
     return status;
 }
 
