@@ -103,9 +103,11 @@ def lib():
             L.orc_diffuse_step.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double, C.c_double]
             L.orc_diffuse_step_res.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double,
                                                C.c_double, p, p, p, p]
-            L.orc_relax.argtypes = [p, p, p, p, C.c_double, C.c_double, C.c_int, p, p, p]
+            L.orc_relax.argtypes = [p, p, p, p, C.c_double, C.c_double, C.c_int, p, p, p, C.c_int]
             L.orc_transport_step.argtypes = [C.c_int64, C.c_int, p, p, p, p, p, C.c_double, C.c_double,
                                              C.c_double, C.c_int, C.c_double, p]
+            L.orc_fire_quadratic.argtypes = [C.c_int64, p, p, C.c_int, p, p]
+            L.orc_fire_quadratic.restype = None
             L.orc_num_threads.argtypes = []
             _lib = L
         return _lib
@@ -318,8 +320,9 @@ def transport_step(sys, mu_ex, bond_csr, dt, host=-1, tau=0.0, v=None, x=None, n
     return int(st), xx, vv
 
 
-def relax(sys, ftol, max_iter, fire: FireParams | None = None, skin=0.2, q=None, sigma=None, x=None):
-    """FIRE relaxation of (q, sigma) at fixed x.  Returns
+def relax(sys, ftol, max_iter, fire: FireParams | None = None, skin=0.2, q=None, sigma=None, x=None, exact=False):
+    """FIRE relaxation of (q, sigma) at fixed x (exact: the exact embedding
+    average of free_energy_exact in place of the Taylor form).  Returns
     (status, iters, fmax, q_new, sigma_new)."""
     fire = fire or FireParams()
     ref = _SysRef(sys, q, sigma, x)
@@ -332,8 +335,22 @@ def relax(sys, ftol, max_iter, fire: FireParams | None = None, skin=0.2, q=None,
     fm = C.c_double(0.0)
     rl = sys.pot.r_cut + skin
     st = lib().orc_relax(C.byref(ref.s), _ptr(qq), _ptr(ss), C.byref(P), float(rl), float(ftol),
-                         int(max_iter), C.byref(fp), C.byref(it), C.byref(fm))
+                         int(max_iter), C.byref(fp), C.byref(it), C.byref(fm), 1 if exact else 0)
     return int(st), int(it.value), float(fm.value), qq, ss
+
+
+def fire_quadratic(kq, q0, iters, fire: FireParams | None = None):
+    """The relaxation's FIRE update on F = 1/2 sum kq q^2 (q [3, n]): the
+    trajectory [iters + 1, 3, n], the start first."""
+    fire = fire or FireParams()
+    q = _f64(q0).copy()
+    n = q.shape[1]
+    k = _f64(kq)
+    traj = np.zeros((iters + 1,) + q.shape)
+    fp = _Fire(fire.dt0, fire.dt_max, fire.f_inc, fire.f_dec, fire.alpha0, fire.f_alpha, fire.sigma_max,
+               fire.n_min, 0)
+    lib().orc_fire_quadratic(n, _ptr(k), _ptr(q), int(iters), C.byref(fp), _ptr(traj))
+    return traj
 
 
 def staggered(sys, n_steps, dt, ftol, max_iter, r_bond, fire=None, initial_relax=True, skin=0.2):

@@ -1037,9 +1037,94 @@ int orc_transport_step(int64_t n, int S, double *x, const double *T, const doubl
  *   grow without bound.  Global dot products and norms are pairwise sums.
  * On GEOMETRY / NONFINITE the input state is restored.                   */
 /* ------------------------------------------------------------------ */
+/* One FIRE update (Bitzek et al. 2006) of y = (q, sigma) from the forces
+ * f = (-gq, fs) (fs: the sigma force projected on [s_lo, s_hi]) at iteration
+ * `it`, in this order: power check P = f.v (it > 0): P > 0 counts a good step
+ * and, after n_min of them, raises dt (to dt_max at most) and lowers alpha;
+ * P <= 0 halves dt, resets alpha and zeroes v.  Then the semi-implicit Euler
+ * kick v += dt f, the mixing v = (1 - alpha) v + alpha |v| f / |f| (global
+ * norms), and the drift y += dt v; a sigma leaving the box is set to the
+ * bound with its velocity zeroed.  tmp: n doubles of scratch.              */
+typedef struct {
+    double dt, alpha;
+    int n_pos;
+} orc_fire_state;
+
+static void fire_update(int64_t n, double *q, double *sigma, double *vq, double *vs, const double *gq,
+                        const double *fs, double *tmp, int it, orc_fire_state *st, const orc_fire *fp,
+                        double s_lo, double s_hi)
+{
+    if (it > 0) {
+        for (int64_t i = 0; i < n; ++i)
+            tmp[i] = -(gq[i] * vq[i] + gq[n + i] * vq[n + i] + gq[2 * n + i] * vq[2 * n + i]) + fs[i] * vs[i];
+        double Pw = pairwise_sum(tmp, n);
+        if (Pw > 0.0) {
+            st->n_pos += 1;
+            if (st->n_pos > fp->n_min) {
+                st->dt = fmin(st->dt * fp->f_inc, fp->dt_max);
+                st->alpha = st->alpha * fp->f_alpha;
+            }
+        } else {
+            st->n_pos = 0;
+            st->dt = st->dt * fp->f_dec;
+            st->alpha = fp->alpha0;
+            memset(vq, 0, sizeof(double) * 3 * n);
+            memset(vs, 0, sizeof(double) * n);
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) vq[c * n + i] += st->dt * (-gq[c * n + i]);
+        vs[i] += st->dt * fs[i];
+    }
+    for (int64_t i = 0; i < n; ++i)
+        tmp[i] = vq[i] * vq[i] + vq[n + i] * vq[n + i] + vq[2 * n + i] * vq[2 * n + i] + vs[i] * vs[i];
+    double vnorm = sqrt(pairwise_sum(tmp, n));
+    for (int64_t i = 0; i < n; ++i)
+        tmp[i] = gq[i] * gq[i] + gq[n + i] * gq[n + i] + gq[2 * n + i] * gq[2 * n + i] + fs[i] * fs[i];
+    double fnorm = sqrt(pairwise_sum(tmp, n));
+    double mix = fnorm > 0.0 ? st->alpha * vnorm / fnorm : 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c)
+            vq[c * n + i] = (1.0 - st->alpha) * vq[c * n + i] + mix * (-gq[c * n + i]);
+        vs[i] = (1.0 - st->alpha) * vs[i] + mix * fs[i];
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) q[c * n + i] += st->dt * vq[c * n + i];
+        double sn = sigma[i] + st->dt * vs[i];
+        if (sn < s_lo || sn > s_hi) {
+            sn = sn < s_lo ? s_lo : s_hi;
+            vs[i] = 0.0;
+        }
+        sigma[i] = sn;
+    }
+}
+
+/* FIRE on the separable quadratic F = 1/2 sum_c kq_c q_c^2 over the 3n
+ * coordinates q (sigma fixed at 1 with no force), with the update above:
+ * the trajectory (iters + 1 rows of 3n positions, the start first) pins the
+ * step order of the relaxation on a case worked out by hand.               */
+void orc_fire_quadratic(int64_t n, const double *kq, double *q, int iters, const orc_fire *fp, double *traj)
+{
+    double *sigma = (double *)malloc(sizeof(double) * n);
+    double *vq = (double *)calloc(3 * n, sizeof(double));
+    double *vs = (double *)calloc(n, sizeof(double));
+    double *gq = (double *)malloc(sizeof(double) * 3 * n);
+    double *fs = (double *)calloc(n, sizeof(double));
+    double *tmp = (double *)malloc(sizeof(double) * n);
+    for (int64_t i = 0; i < n; ++i) sigma[i] = 1.0;
+    orc_fire_state st = {fp->dt0, fp->alpha0, 0};
+    memcpy(traj, q, sizeof(double) * 3 * n);
+    for (int it = 0; it < iters; ++it) {
+        for (int64_t c = 0; c < 3 * n; ++c) gq[c] = kq[c] * q[c];
+        fire_update(n, q, sigma, vq, vs, gq, fs, tmp, it, &st, fp, ORC_SIGMA_MIN, INFINITY);
+        memcpy(traj + (int64_t)(it + 1) * 3 * n, q, sizeof(double) * 3 * n);
+    }
+    free(sigma); free(vq); free(vs); free(gq); free(fs); free(tmp);
+}
+
 int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential *P,
               double r_list, double ftol, int max_iter, const orc_fire *fp,
-              int *iters_out, double *fmax_out)
+              int *iters_out, double *fmax_out, int exact_embedding)
 {
     const int64_t n = sys_in->n;
     const int S = sys_in->S;
@@ -1059,11 +1144,12 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
     int32_t *off = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
     int64_t cap = 64 * n + 64, npairs = 0;
     int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * cap);
-    double dt = fp->dt0, alpha = fp->alpha0, F4[4];
+    orc_fire_state fst = {fp->dt0, fp->alpha0, 0};
+    double F4[4];
     const double s_lo = ORC_SIGMA_MIN;
     const double s_hi = (fp->sigma_max > 0.0) ? fp->sigma_max : INFINITY;
     double *fs = (double *)malloc(sizeof(double) * n);
-    int n_pos = 0, status = ORC_OK, it = 0;
+    int status = ORC_OK, it = 0;
     double fmx = 0.0;
     for (it = 0;; ++it) {
         /* neighbour sets for the current widths: r_list covers r_cut + sqrt6 max sigma */
@@ -1077,8 +1163,12 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
             idx = (int32_t *)realloc(idx, sizeof(int32_t) * cap);
         }
         if (status != ORC_OK) break;
-        status = orc_free_energy(&sys, P, off, idx, 0, F4, gq, gs, mu_ex, NULL,
-                                 NULL, NULL, NULL, NULL, NULL);
+        /* the Taylor form of the embedding average, or the exact rule */
+        if (exact_embedding)
+            status = orc_free_energy_exact(&sys, P, off, idx, F4, gq, gs, mu_ex, NULL, NULL);
+        else
+            status = orc_free_energy(&sys, P, off, idx, 0, F4, gq, gs, mu_ex, NULL,
+                                     NULL, NULL, NULL, NULL, NULL);
         if (status != ORC_OK) break;
         fmx = 0.0;
         for (int64_t i = 0; i < n; ++i) {
@@ -1088,49 +1178,7 @@ int orc_relax(orc_system *sys_in, double *q, double *sigma, const orc_potential 
         }
         if (fmx <= ftol) break;
         if (it == max_iter) { status = ORC_ERR_NO_CONVERGE; break; }
-        if (it > 0) {
-            for (int64_t i = 0; i < n; ++i)
-                tmp[i] = -(gq[i] * vq[i] + gq[n + i] * vq[n + i] + gq[2 * n + i] * vq[2 * n + i]) + fs[i] * vs[i];
-            double Pw = pairwise_sum(tmp, n);
-            if (Pw > 0.0) {
-                n_pos += 1;
-                if (n_pos > fp->n_min) {
-                    dt = fmin(dt * fp->f_inc, fp->dt_max);
-                    alpha = alpha * fp->f_alpha;
-                }
-            } else {
-                n_pos = 0;
-                dt = dt * fp->f_dec;
-                alpha = fp->alpha0;
-                memset(vq, 0, sizeof(double) * 3 * n);
-                memset(vs, 0, sizeof(double) * n);
-            }
-        }
-        for (int64_t i = 0; i < n; ++i) {
-            for (int c = 0; c < 3; ++c) vq[c * n + i] += dt * (-gq[c * n + i]);
-            vs[i] += dt * fs[i];
-        }
-        for (int64_t i = 0; i < n; ++i)
-            tmp[i] = vq[i] * vq[i] + vq[n + i] * vq[n + i] + vq[2 * n + i] * vq[2 * n + i] + vs[i] * vs[i];
-        double vnorm = sqrt(pairwise_sum(tmp, n));
-        for (int64_t i = 0; i < n; ++i)
-            tmp[i] = gq[i] * gq[i] + gq[n + i] * gq[n + i] + gq[2 * n + i] * gq[2 * n + i] + fs[i] * fs[i];
-        double fnorm = sqrt(pairwise_sum(tmp, n));
-        double mix = fnorm > 0.0 ? alpha * vnorm / fnorm : 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            for (int c = 0; c < 3; ++c)
-                vq[c * n + i] = (1.0 - alpha) * vq[c * n + i] + mix * (-gq[c * n + i]);
-            vs[i] = (1.0 - alpha) * vs[i] + mix * fs[i];
-        }
-        for (int64_t i = 0; i < n; ++i) {
-            for (int c = 0; c < 3; ++c) q[c * n + i] += dt * vq[c * n + i];
-            double sn = sigma[i] + dt * vs[i];
-            if (sn < s_lo || sn > s_hi) {
-                sn = sn < s_lo ? s_lo : s_hi;
-                vs[i] = 0.0;
-            }
-            sigma[i] = sn;
-        }
+        fire_update(n, q, sigma, vq, vs, gq, fs, tmp, it, &fst, fp, s_lo, s_hi);
     }
     if (status != ORC_OK && status != ORC_ERR_NO_CONVERGE) {
         memcpy(q, q0, sizeof(double) * 3 * n);

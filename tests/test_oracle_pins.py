@@ -503,3 +503,52 @@ def test_reservoir_steady_state_detailed_balance():
     r = x_r / (1 - x_r) * np.exp(2 * beta * mu_r)
     np.testing.assert_allclose(x[0, layer], x_r, rtol=0, atol=0)
     np.testing.assert_allclose(x[0, ~layer], r / (1 + r), rtol=0, atol=1e-9)
+
+
+# ---------------------------------------------------------------- FIRE trajectory
+def test_fire_trajectory_worked_by_hand():
+    """The relaxation's FIRE update (Bitzek et al., PRL 97, 170201 (2006)) in
+    the order fixed for both implementations -- power check (from the second
+    iteration), kick v += dt f, mixing v <- (1 - a) v + a |v| f/|f|, drift
+    y += dt v -- on F = 1/2 (q_x^2 + 30 q_y^2 + 4 q_z^2) from (1, 1, 1), with
+    dt0 = 0.3, dt_max = 0.5, f_inc = 1.1, f_dec = 0.5, a0 = 0.2, f_a = 0.99,
+    n_min = 0.  The stiff y axis overshoots, so iterations 1 and 3 reset
+    (P <= 0: v = 0, dt halved, a = a0) and iterations 2 and 4 grow dt.  Each
+    iteration is written out below; a swapped kick/mixing/check order, a
+    wrong reset or a wrong mixing norm changes the positions at once."""
+    fp = O.FireParams(dt0=0.3, dt_max=0.5, f_inc=1.1, f_dec=0.5, alpha0=0.2, f_alpha=0.99, n_min=0)
+    k = np.array([1.0, 30.0, 4.0])
+    traj = O.fire_quadratic(k[:, None], np.ones((3, 1)), 5, fp)[:, :, 0]
+    nrm = np.linalg.norm
+
+    def mixed(v, f, a):
+        return (1.0 - a) * v + a * nrm(v) / nrm(f) * f
+
+    # iteration 0 (no power check): v and f are parallel, mixing keeps v
+    y0 = np.array([1.0, 1.0, 1.0])
+    f = -k * y0                                   # (-1, -30, -4)
+    v = mixed(0.0 + 0.3 * f, f, 0.2)              # (-0.3, -9, -1.2)
+    y1 = y0 + 0.3 * v
+    np.testing.assert_allclose(y1, [0.91, -1.7, 0.64], rtol=1e-15)
+    # iteration 1: P = f.v = 0.273 - 459 + 3.072 < 0 -> v = 0, dt = 0.15, a = 0.2
+    f = -k * y1
+    assert f @ v < 0
+    v = mixed(0.15 * f, f, 0.2)
+    y2 = y1 + 0.15 * v
+    np.testing.assert_allclose(y2, [0.889525, -0.5525, 0.5824], rtol=1e-14)
+    # iteration 2: P > 0 and n_pos = 1 > n_min -> dt = 0.165, a = 0.198
+    f = -k * y2
+    assert f @ v > 0
+    v = mixed(v + 0.165 * f, f, 0.198)
+    y3 = y2 + 0.165 * v
+    # iteration 3: the y axis overshoots again, P < 0 -> v = 0, dt = 0.0825, a = 0.2
+    f = -k * y3
+    assert f @ v < 0
+    v = mixed(0.0825 * f, f, 0.2)
+    y4 = y3 + 0.0825 * v
+    # iteration 4: P > 0 -> dt = 0.09075, a = 0.198
+    f = -k * y4
+    assert f @ v > 0
+    v = mixed(v + 0.09075 * f, f, 0.198)
+    y5 = y4 + 0.09075 * v
+    np.testing.assert_allclose(traj, np.array([y0, y1, y2, y3, y4, y5]), rtol=1e-13, atol=1e-15)
