@@ -51,6 +51,8 @@ from paper_1910_01235_gb300 import workloads as W  # noqa: E402
 METRIC = "site free-energy+gradient evals/s and diffusion steps/s, FP32-mixed vs FP64"
 WORKLOAD = "binary_alloy_fcc40_256k"
 FIRE_ITERS = 10
+DTYPES = {"fp64": "f64", "mixed": "f32 (f64 sums; mu from float-float node arithmetic)",
+          "ff": "f32 (float-float sums and mu)"}
 
 
 def dist_env():
@@ -176,6 +178,76 @@ def peak_fp32_ops(clock_mhz=2070.0):
     return 152 * 128 * clock_mhz * 1e6
 
 
+def peak_fp64_ops(clock_mhz=2070.0):
+    """FP64 pipe: the nominal 1.25 TFLOP/s of a GB300 (FMA = 2 flops) is 2
+    FP64 instructions per SM per cycle: 152 SMs x 2 x clock."""
+    return 152 * 2 * clock_mhz * 1e6
+
+
+def ncu_counter(kernel, name, record="counters_binary_alloy_256k.json"):
+    """A per-launch counter of `kernel` from a committed ncu capture of this
+    workload, or None when the kernel sources changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", record)
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256()
+    for f in d["source_files"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    k = d["kernels"].get(kernel)
+    if k is None or h.hexdigest()[:16] != d["source_digest"] or name not in k:
+        return None
+    return k[name]
+
+
+def kernel_shares(kern):
+    """Per kernel class: launches, total and mean device time, share of the step."""
+    shares = {}
+    tot_k = sum(v[1] for v in kern.values()) if kern else 0.0
+    for k_, (cnt, tms) in (kern or {}).items():
+        shares[k_] = {"launches": cnt, "total_ms": tms, "avg_ms": tms / cnt, "share": tms / tot_k if tot_k else None}
+    return shares
+
+
+def roofline_of(shares, npairs, S, n_phi, n_f, with_traffic):
+    """Roofline of the step's dominant kernel (largest share of the device
+    time).  FP32-pipe kernels: algorithmic operations per pair (ops_per_pair)
+    x pairs of one launch / mean launch time, against the FP32 lane count x
+    clock.  FP64 kernels: FP64-pipe instructions of one launch (ncu count of
+    the committed capture) / mean launch time, against the FP64 pipe's
+    instruction rate -- the pipe utilisation."""
+    if not shares:
+        return None
+    dom = max(shares, key=lambda k_: shares[k_]["total_ms"])
+    avg_s = shares[dom]["avg_ms"] / 1e3
+    fp64 = "64" in dom or dom.endswith("fp64") or dom.startswith("gradient_fp64") or dom.startswith("density_fp64")
+    out = {"bound": "alu", "kernel": dom, "kernel_avg_ms": shares[dom]["avg_ms"], "share": shares[dom]["share"]}
+    if fp64:
+        inst = ncu_counter(dom, "inst_fp64")
+        peak = peak_fp64_ops()
+        ach = inst / avg_s / 1e12 if inst else None
+        out.update({"achieved": ach, "peak": peak / 1e12, "unit": "T instructions/s (FP64 pipe)",
+                    "frac": ach / (peak / 1e12) if ach else None, "ops_per_launch": inst,
+                    "ops_basis": "FP64-pipe instructions of one launch (sm__inst_executed_pipe_fp64.sum, ncu)",
+                    "peak_note": "152 SMs x 2 FP64 instructions/cycle x 2070 MHz (nominal 1.25 TFLOP/s)"})
+    else:
+        opp = ops_per_pair(dom, n_phi, n_f, S)
+        peak = peak_fp32_ops()
+        ops_launch = units_per_launch(dom, npairs) * opp if opp else None
+        ach = ops_launch / avg_s / 1e12 if ops_launch else None
+        out.update({"achieved": ach, "peak": peak / 1e12, "unit": "Tops/s (FP32 pipe)",
+                    "frac": ach / (peak / 1e12) if ach else None, "ops_per_launch": ops_launch,
+                    "ops_basis": ("per unordered pair" if dom.startswith("pair") else
+                                  "per neighbour entry (full list: each unordered pair evaluated from both ends)"),
+                    "frac_half_list": ((ach / (peak / 1e12)) * (1.0 if dom.startswith("pair") else 0.5))
+                                      if ach else None,
+                    "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"})
+    out["traffic"] = ncu_traffic(dom) if with_traffic else None
+    out["traffic_unit"] = "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)"
+    return out
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this
     workload, or None when the kernel sources changed since the capture."""
@@ -283,8 +355,8 @@ def run_ours(args):
     results = {}
     clocks = None
     for p in precs:
-        steps = args.steps if p != "fp64" else max(1, min(args.steps, 3))
-        warm = args.warmup if p != "fp64" else max(3, min(args.warmup, 3))
+        steps = args.steps
+        warm = args.warmup if p != "fp64" else 3
         sampler = ClockSampler(local) if p == main_prec else None
         if sampler:
             sampler.start()
@@ -335,7 +407,7 @@ def run_ours(args):
         g.close()
         return tot / steps, h2d, d2h
 
-    e2e_ms, h2d, d2h = e2e(main_prec, max(1, min(args.steps, 5)))
+    e2e_ms, h2d, d2h = e2e(main_prec, args.steps)
     e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     if world > 1:
@@ -351,19 +423,15 @@ def run_ours(args):
     dp = sys0.pot
     n_phi = 3 if dp.cross_geomean else 2
     n_f = 2
-    # dominant kernel of the step: largest share of the per-class device time
-    shares = {}
-    tot_k = sum(v[1] for v in kern.values()) if kern else 0.0
-    for k_, (cnt, tms) in (kern or {}).items():
-        shares[k_] = {"launches": cnt, "total_ms": tms, "avg_ms": tms / cnt, "share": tms / tot_k if tot_k else None}
-    dom = max(shares, key=lambda k_: shares[k_]["total_ms"]) if shares else None
-    opp = ops_per_pair(dom, n_phi, n_f, sys0.S) if dom else None
-    peak_ops = peak_fp32_ops()
-    if dom and opp:
-        ops_launch = units_per_launch(dom, npairs) * opp
-        achieved = ops_launch / (shares[dom]["avg_ms"] / 1e3) / 1e12
-    else:
-        ops_launch, achieved = None, None
+    shares = kernel_shares(kern)
+    per_prec = {}
+    for p, r in results.items():
+        sh = kernel_shares(r[4])
+        per_prec[p] = {"value": aggregate_rate(evals_per_step, r[0], world), "unit": "site-evals/s",
+                       "ms_per_step": r[0], "steps": r[1], "warmup": r[2],
+                       "diffusion_steps_per_s": world * 1e3 / r[0], "pass_shape": list(r[5]),
+                       "dtype": DTYPES[p],
+                       "roofline": roofline_of(sh, r[3], sys0.S, n_phi, n_f, with_traffic=(p == "ff"))}
     line = {
         "metric": METRIC,
         "value": value,
@@ -375,7 +443,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "f32 (f64 sums, f64 mu)", "ff": "f32 (float-float sums and mu)"}[main_prec],
+        "dtype": DTYPES[main_prec],
         "data": "synthetic (seeded FCC binary alloy, random-init composition)",
         "config": {"workload": WORKLOAD, "sites": n, "species": 2, "fire_iters_per_step": K,
                    "evals_per_step": K + 2, "neighbor_pairs": npairs, "parallelism": f"replicas{world}",
@@ -383,27 +451,19 @@ def run_ours(args):
                    "pass_shape": {"lanes_per_site": shape[0], "threads_per_block": shape[1],
                                   "chosen_by": "--pass-shape" if args.pass_shape else "autotuner"}},
         "diffusion_steps_per_s": world * 1e3 / ms,
-        "precisions": {p: {"ms_per_step": r[0], "site_evals_per_s": aggregate_rate(evals_per_step, r[0], world),
-                           "steps": r[1], "pass_shape": list(r[5])} for p, r in results.items()},
         "kernels": shares,
         "e2e": {"value": aggregate_rate(evals_per_step, e2e_ms, world), "unit": "site-evals/s",
-                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s (FP32 pipe)", "frac": (achieved / (peak_ops / 1e12)) if achieved else None,
-                     "traffic": ncu_traffic(dom) if (dom and main_prec == "ff" and world >= 1) else None,
-                     "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)",
-                     "kernel_avg_ms": shares[dom]["avg_ms"] if dom else None,
-                     "ops_per_launch": ops_launch,
-                     "ops_basis": ("per unordered pair" if dom.startswith("pair") else
-                                   "per neighbour entry (full list: each unordered pair evaluated from both ends)"),
-                     "frac_half_list": ((achieved / (peak_ops / 1e12)) * (1.0 if dom.startswith("pair") else 0.5))
-                                       if achieved else None,
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"},
+                "ms_per_step": e2e_ms, "steps": args.steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": per_prec[main_prec]["roofline"],
         "clocks": clocks,
         "gpu_launches": None,
     }
     # kernels per step, counted by the library's launch timing
     line["gpu_launches"] = steps * sum(v["launches"] for v in shares.values())
+    # the metric's precision pair, one object per mode (FP32-mixed vs FP64)
+    line.update(per_prec)
+    if "fp64" in per_prec and main_prec != "fp64":
+        line["speedup_vs_fp64"] = per_prec["fp64"]["ms_per_step"] / ms
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sys0)
     print(json.dumps(line), flush=True)
@@ -493,7 +553,7 @@ def run_ensemble(args):
         "metric": METRIC, "value": aggregate_rate(evals_per_step, ms_step, world), "unit": "site-evals/s",
         "n_gpus": world, "steps": steps_per_run * len(times), "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "f32 (f64 sums, f64 mu)", "ff": "f32 (float-float sums and mu)"}[prec],
+        "dtype": DTYPES[prec],
         "data": "synthetic (seeded ensemble of FCC single-species lattices with vacancies)",
         "config": {"workload": "ensemble_512_systems", "systems": len(systems), "sites": n,
                    "fire_iters_per_step": K, "evals_per_step": K + 2, "steps_per_graph_run": steps_per_run,
@@ -554,10 +614,7 @@ def run_unrolled_grad(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    nphi, nf, terms, phi_of, f_of = g.potential_terms()
-    theta = W.theta_of(s.pot)
-    base = s.pot
-    grad = M.chain_to_parameters(dterm, lambda th: W.binary_from_theta(th, base), theta, phi_of, f_of, nphi, nf)
+    grad = M.element_param_grad(s.pot, dterm).reshape(-1)
     L = float((w * g.x.cpu().numpy()).sum())
     g.close()
     line = {"metric": "unrolled-gradient runs/s (20 staggered steps forward + reverse sweep)",
@@ -631,12 +688,67 @@ def run_slab(args):
     line = {"metric": "diffusion steps/s (free energy + gradients + chemical potentials, then the Euler step)",
             "value": world * 1e3 / ms, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "f32 (f64 sums, f64 mu)", "ff": "f32 (float-float sums and mu)"}[prec],
+            "dtype": DTYPES[prec],
             "data": "synthetic (seeded FCC host + octahedral solute slab)",
             "config": {"workload": "interstitial_slab_100x100x50_4M", "sites": s.n, "neighbor_pairs": npairs,
                        "precision": prec, "l2": "working set > L2, not flushed"},
             "site_evals_per_s": world * s.n / (ms / 1e3), "dt": dt,
             "device_memory_bytes": int(footprint), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- embedding average
+def run_embedding(args):
+    """The paper's Taylor form of the embedding average (Eq. F_taylor_mxe)
+    against the exact third-degree rule over each site and its neighbours
+    inside r_cut (App. B.2), both evaluated by the library in FP64 at the same
+    state: the 500-site vacancy lattice and the 256,000-site binary alloy.
+    Reports the differences in E_V, dF/dq, dF/dsigma and mu^ex, and the time
+    of one free-energy evaluation in each form."""
+    import torch
+
+    from paper_1910_01235_gb300 import mxe as M
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = {}
+    for name, sysf in (("vacancy_lattice_fcc5_500", W.config_vacancy_lattice),
+                       ("binary_alloy_fcc40_256k", W.config_binary_alloy)):
+        s = sysf()
+        res = {}
+        for mode in ("taylor", "exact"):
+            g = M.MxeSystem(s, "fp64", device=dev)
+            g.set_embedding(mode)
+            g.build_neighbors()
+            for _ in range(max(1, args.warmup)):
+                g.free_energy_grad()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.free_energy_grad()
+            e1.record()
+            torch.cuda.synchronize()
+            res[mode] = dict(F4=g.F4.cpu().numpy(), gq=g.gq.cpu().numpy(), gs=g.gs.cpu().numpy(),
+                             mu=g.mu_ex.cpu().numpy(), ms=e0.elapsed_time(e1))
+            g.close()
+        t, e = res["taylor"], res["exact"]
+        out[name] = {
+            "sites": s.n,
+            "E_V_per_site_taylor": t["F4"][0] / s.n, "E_V_per_site_exact": e["F4"][0] / s.n,
+            "dE_V_per_site": (e["F4"][0] - t["F4"][0]) / s.n,
+            "max_abs_d_dFdq": float(np.abs(e["gq"] - t["gq"]).max()),
+            "max_abs_dFdq": float(np.abs(e["gq"]).max()),
+            "max_abs_d_dFdsigma": float(np.abs(e["gs"] - t["gs"]).max()),
+            "max_abs_d_mu_ex": float(np.abs(e["mu"] - t["mu"]).max()),
+            "ms_eval_taylor": t["ms"], "ms_eval_exact": e["ms"]}
+    line = {"metric": "embedding-average difference, exact rule minus Taylor form (FP64)",
+            "value": out["binary_alloy_fcc40_256k"]["dE_V_per_site"], "unit": "eV/site",
+            "n_gpus": world, "steps": 1, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic (seeded FCC lattices)", "vs_baseline": None,
+            "config": {"workload": "embedding_average_taylor_vs_exact"}, "workloads": out}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -684,7 +796,8 @@ def main():
     ap.add_argument("--fire-iters", type=int, default=FIRE_ITERS)
     ap.add_argument("--quick", action="store_true", help="main precision only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="binary", choices=["binary", "ensemble", "unrolled_grad", "slab4m"])
+    ap.add_argument("--workload", default="binary",
+                    choices=["binary", "ensemble", "unrolled_grad", "slab4m", "embedding"])
     ap.add_argument("--ensemble-steps", type=int, default=ENSEMBLE_STEPS)
     ap.add_argument("--pass-shape", default="", help="lanes,threads of the passes (default: autotuned)")
     args = ap.parse_args()
@@ -698,6 +811,8 @@ def main():
         run_unrolled_grad(args)
     elif args.workload == "slab4m":
         run_slab(args)
+    elif args.workload == "embedding":
+        run_embedding(args)
     else:
         run_ours(args)
 

@@ -313,6 +313,28 @@ MXE_API mxe_status mxe_run_staggered(mxe_ctx *ctx, mxe_state *state, int32_t n_s
 MXE_API mxe_status mxe_autotune(mxe_ctx *ctx, const mxe_state *state, int32_t *lanes_out, int32_t *threads_out);
 MXE_API mxe_status mxe_set_pass_shape(mxe_ctx *ctx, int32_t lanes, int32_t threads);
 
+/* Phase average of the embedding term (App. B.2).
+ *  MXE_EMBED_TAYLOR (default): the Taylor form Eq. F_taylor_mxe,
+ *    <F_k(rho_i)> ~ F_k(rho_bar_i) + F_k'(rho_bar_i)(<rho_i> - rho_bar_i).
+ *  MXE_EMBED_EXACT: the third-degree rule of App. A applied to the many-body
+ *    function itself (the form the paper states before replacing it by its
+ *    Taylor expansion).  Site i's rule covers the N_i sites inside the
+ *    potential cut-off: i and every neighbour j with |qbar_j - qbar_i| <
+ *    r_cut; rho_i^k = sum over those j of sum_l x_jl f_kl(r_ij); N_q = 3 N_i
+ *    coordinates, M = 2 N_q nodes of weight 1/M, each moving one site s of
+ *    the rule by +-sigma_s sqrt(N_q) along one axis:
+ *      <F_k(rho_i^k)> = (1/M) sum_nodes F_k(rho_i^k(node)).
+ *    The rule's membership is fixed by the mean positions, so F is piecewise
+ *    smooth: it jumps where a mean distance crosses r_cut.  Every call then
+ *    uses this average (energies, gradients, chemical potentials, mxe_relax,
+ *    mxe_run_staggered); the derivative calls (mxe_tangent,
+ *    mxe_unrolled_grad) return MXE_ERR_ARG.  Allocates the rule data (9 S + 1
+ *    values per site) on first use.  GEOMETRY also when a node density is
+ *    <= 1e-12 for an occupied element with an embedding energy.              */
+#define MXE_EMBED_TAYLOR 0
+#define MXE_EMBED_EXACT 1
+MXE_API mxe_status mxe_set_embedding(mxe_ctx *ctx, int32_t mode);
+
 /* ---------------------------------------------------------------------------
  * Derivatives of the staggered scheme (second order).
  *
@@ -327,6 +349,21 @@ MXE_API mxe_status mxe_set_pass_shape(mxe_ctx *ctx, int32_t lanes, int32_t threa
  * caller maps them to its own parameters by the chain rule.                 */
 MXE_API mxe_status mxe_potential_terms(mxe_ctx *ctx, int32_t *n_phi, int32_t *n_f, double *terms,
                                        int32_t *phi_of, int32_t *f_of);
+
+/* Chain rule from the term sensitivities to per-element parameters (App.
+ * B.2 analytic forms).  For tables with the element structure -- element e
+ * has a pair term A_e exp(-p_e (r/r0_e - 1)) S(r), the density from an
+ * e-neighbour is xi_e exp(-q_e (r/r0_e - 1)) S(r) at every site (same r0_e),
+ * and the cross pair of two elements is their geometric mean (S = 2) -- the
+ * parameters theta_e = (A_e, p_e, q_e, r0_e) enter the radial terms only
+ * through c = ln A + exponent and lambda = exponent / r0 (the cross pair: the
+ * mean of the two elements' c and lambda).  Given dterm (host [2 T]:
+ * dL/dc_u then dL/dlambda_u, in the term order of mxe_potential_terms, as
+ * mxe_tangent and mxe_unrolled_grad report them), writes out (host [S][4])
+ * = dL/d(A_e, p_e, q_e, r0_e) with the closed-form Jacobian.  Host
+ * arithmetic only (no context, no device).  MXE_ERR_ARG for tables without
+ * that structure (or Lennard-Jones terms).                                   */
+MXE_API mxe_status mxe_element_param_grad(const mxe_potential *pot, const double *dterm, double *out);
 
 /* Forward-mode pass (FP64 in every precision mode): the gradients of the
  * free energy and their directional derivatives along a tangent (dq [3][n],
@@ -453,7 +490,9 @@ MXE_API mxe_status mxe_timing_read(mxe_ctx *ctx, int32_t max_entries, char *name
  * the process exits; it bounds n to MXE_NOALLOC_MAX_SITES(S), and a larger n
  * (or S outside 1..2) returns MXE_ERR_ARG before any GPU work.  The first
  * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call shares
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process: a process that resets a device
+ * (cudaDeviceReset) must not call this entry point on it again.  Every call shares
  * the array and it keeps the last call's contents: the flag words are cleared
  * at the start of each call and the per-site scratch is written before it is
  * read, but calls that overlap on the GPU (other streams, other host threads)

@@ -45,6 +45,11 @@ struct mxe_ctx {
   mxe_box box{};
   mxe_potential pot{};
   DevPot dp{};
+  DevPot dp_pair{};  // the potential with every embedding switched off (pair terms alone)
+  // embedding average: 0 the Taylor form (Eq. F_taylor_mxe), 1 the exact rule
+  int embedding = 0;
+  double* emb_buf = nullptr;  // rule data of the exact average: (9 S) [n] doubles
+  int* emb_nrule = nullptr;   // [n]
   DevGrid grid{};
 
   // cell grid
@@ -75,12 +80,13 @@ struct mxe_ctx {
   bool have_list = false;
   double r_list = 0, skin = 0.2, r_bond = 0, sigma_max_build = 0;
   double* q_build = nullptr;
-  // unordered-pair index and records of the half-list float-float passes
+  // unordered-pair index and records of the half-list passes (contexts whose
+  // potential the pair kernels support)
   int *first_gt = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
-  int *pair_i = nullptr, *pair_t = nullptr, *pid = nullptr;           // [pairs], [pairs], [entries]
-  float2* pair_buf = nullptr;                                         // [pairs][pair_record_len]
-  int* pair_rev = nullptr;                                            // [pairs] entry of the other end
-  float4 *ent_dens = nullptr, *ent_frc = nullptr;                     // [entries] FP32 relaxation records
+  int4* pair_rec = nullptr;  // [pairs] (i, entry of j with its image code, entry index, reverse entry index)
+  int* pid = nullptr;        // [entries] pair of every entry
+  double* pair_buf = nullptr;  // [pairs][pair_record_len] 8-byte values (float pairs or doubles)
+  void *ent_dens = nullptr, *ent_frc = nullptr;  // [entries] relaxation records (relax_record_bytes each)
   bool relax_records = false;  // allocate them (first relaxation of the context, then with every list growth)
   int64_t pair_cap = 0, n_upairs = 0;
   // rows of a fill without a count pass, at a fixed stride
@@ -91,7 +97,7 @@ struct mxe_ctx {
   // per-site work arrays
   double *rho_bar = nullptr, *rho_avg = nullptr, *a = nullptr, *b = nullptr, *e = nullptr;
   float4 *pos32 = nullptr, *x32 = nullptr, *ab32 = nullptr;
-  float4 *pos32lo = nullptr, *x32lo = nullptr, *ab32lo = nullptr;  // float-float remainders (FF mode)
+  float4 *pos32lo = nullptr, *x32lo = nullptr, *ab32lo = nullptr;  // float-float remainders (FP32 modes)
   double *gq = nullptr, *gs = nullptr, *mu_ex = nullptr;
   double* site_E = nullptr;
   double* partials = nullptr;
@@ -233,6 +239,12 @@ cudaError_t dalloc(T** p, int64_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
 }
 
+cudaError_t dalloc_bytes(void** p, int64_t bytes) {
+  *p = nullptr;
+  if (bytes <= 0) bytes = 16;
+  return cudaMalloc(p, (size_t)bytes);
+}
+
 template <typename T>
 void dfree(T*& p) {
   if (p) cudaFree((void*)p);
@@ -320,6 +332,11 @@ mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
       if (v == -2) return MXE_ERR_ARG;
       d.f_of[k][l] = (int8_t)v;
     }
+  d.tab = (S == 2 && d.n_phi == 3 && d.n_f == 2 && d.phi_of[0][0] == 0 && d.phi_of[0][1] == 1 &&
+           d.phi_of[1][0] == 1 && d.phi_of[1][1] == 2 && d.f_of[0][0] == 0 && d.f_of[1][0] == 0 &&
+           d.f_of[0][1] == 1 && d.f_of[1][1] == 1)
+              ? 1
+              : 0;
   d.rs = p.r_switch;
   d.rc = p.r_cut;
   d.inv_w = 1.0 / (p.r_cut - p.r_switch);
@@ -332,6 +349,10 @@ mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
   d.dS_scale_ff = ff(-30.0 * d.inv_w);
   return MXE_OK;
 }
+
+// The context keeps an unordered-pair index of its lists (and evaluates the
+// pairs once) when the pair kernels support its potential.
+bool has_pair_index(const mxe_ctx* c) { return pair_kernels_supported(c->dp); }
 
 bool state_ok(const mxe_ctx* c, const mxe_state* s) {
   return s && s->n == c->n && (c->n == 0 || (s->q && s->sigma && s->x && s->T));
@@ -350,6 +371,7 @@ void fill_pass(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
   A.nb_off = c->nb_off;
   A.nb_ent = c->nb_ent;
   A.n = c->n;
+  A.n_ent = c->n_pairs;
   A.rho_bar = c->rho_bar;
   A.rho_avg = c->rho_avg;
   A.a = c->a;
@@ -484,6 +506,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, B, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
   CK(TIMED("build_misc", launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st)));
   CK(TIMED("build_misc", launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st)));
+  CK(TIMED("build_misc", launch_cell_sort(ncell, c->cell_start, c->cell_sites, st)));
   // largest stencil candidate set: the cell-staged kernels need it in shared memory
   CK(cudaMemsetAsync(c->max_row, 0, 2 * sizeof(int), st));
   CK(TIMED("build_misc", launch_cand_max(ncell, g, B, c->cell_start, c->max_row + 1, st)));
@@ -545,23 +568,20 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     CK(dalloc(&c->nb_ent, cap));
     c->nb_cap = cap;
   }
-  if (c->precision == MXE_FP32_FF && (npairs > c->pair_cap || !c->pid)) {
+  const bool pairs = has_pair_index(c);
+  if (pairs && (npairs > c->pair_cap || !c->pid)) {
     dfree(c->pid);
-    dfree(c->pair_i);
-    dfree(c->pair_t);
+    dfree(c->pair_rec);
     dfree(c->pair_buf);
     const int64_t cap = std::max<int64_t>(c->nb_cap, npairs);
     CK(dalloc(&c->pid, cap));
-    CK(dalloc(&c->pair_i, cap / 2 + 64));
-    CK(dalloc(&c->pair_t, cap / 2 + 64));
+    CK(dalloc(&c->pair_rec, cap / 2 + 64));
     CK(dalloc(&c->pair_buf, (cap / 2 + 64) * (int64_t)pair_record_len(c->dp)));
-    dfree(c->pair_rev);
     dfree(c->ent_dens);
     dfree(c->ent_frc);
-    CK(dalloc(&c->pair_rev, cap / 2 + 64));
     if (c->relax_records) {
-      CK(dalloc(&c->ent_dens, cap));
-      CK(dalloc(&c->ent_frc, cap));
+      CK(dalloc_bytes(&c->ent_dens, cap * (int64_t)relax_record_bytes(c->precision)));
+      CK(dalloc_bytes(&c->ent_frc, cap * (int64_t)relax_record_bytes(c->precision)));
     }
     c->pair_cap = cap;
   }
@@ -585,12 +605,17 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
                                            c->cell_start, c->cell_sites, c->abs_cell, rl2, rb2, band, c->nb_off,
                                            c->nb_ent, c->bd_off, c->bd_idx, max_row, st)));
   }
-  if (c->precision == MXE_FP32_FF) {
+  if (pairs) {
     if (npairs % 2) return MXE_ERR_NBR_OVERFLOW;  // a symmetric list has every pair twice
     CK(TIMED("build_misc", launch_pair_count(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_cnt, st)));
     CK(TIMED("build_misc", launch_scan(c->pair_cnt, c->pair_off, n, c->totals + 3, (int*)c->scan_tmp, c->scan_len, st)));
-    CK(TIMED("build_misc", launch_pair_fill(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_off, npairs / 2, c->pair_i,
-                                            c->pair_t, c->pair_rev, c->pid, c->flags, st)));
+    CK(TIMED("build_misc", launch_pair_fill(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_off, npairs / 2,
+                                            c->pair_rec, c->pid, c->flags, st)));
+    // every pair record is written only if each row's tail owns exactly half
+    // of the entries (a symmetric list): check before any pair kernel runs
+    CK(cudaMemcpyAsync(c->totals_h + 3, c->totals + 3, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c->totals_h[3] != npairs / 2) return MXE_ERR_NBR_OVERFLOW;
     c->n_upairs = npairs / 2;
   }
   CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
@@ -606,57 +631,118 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   return MXE_OK;
 }
 
-// The FP32 force passes run on the half list: float-float context, pair index
-// and relaxation records present (allocated by the first relaxation).
-bool half_list_forces(const mxe_ctx* c) {
-  return c->precision == MXE_FP32_FF && c->pid && c->ent_dens && c->ent_frc && relax32_pairs_supported(c->dp);
+// The force passes run on the half list: pair index and relaxation records
+// present (the records are allocated by the first relaxation).
+bool half_list_forces(const mxe_ctx* c) { return has_pair_index(c) && c->pid && c->ent_dens && c->ent_frc; }
+
+EmbArgs emb_args(mxe_ctx* c) {
+  EmbArgs E;
+  const int64_t n = c->n, S = c->S;
+  E.rhob = c->emb_buf;
+  E.rown = c->emb_buf + S * n;
+  E.fsum = c->emb_buf + 7 * S * n;
+  E.emb = c->emb_buf + 8 * S * n;
+  E.nrule = c->emb_nrule;
+  return E;
+}
+
+// The exact embedding average: the rule data of every site, then the
+// derivatives, added to what the pair passes left in A (energies, gradients,
+// chemical potentials, whichever A carries).
+mxe_status enqueue_emb_exact(mxe_ctx* c, const PassArgs& A, bool fp64) {
+  const EmbArgs E = emb_args(c);
+  CK(TIMED(fp64 ? "emb_nodes_fp64" : "emb_nodes_fp32",
+           launch_emb_exact(false, fp64, c->nl, c->dp, c->grid, A, E, c->stream)));
+  if (A.gq || A.gs || A.mu_ex || A.mu)
+    CK(TIMED(fp64 ? "emb_grad_fp64" : "emb_grad_fp32",
+             launch_emb_exact(true, fp64, c->nl, c->dp, c->grid, A, E, c->stream)));
+  return MXE_OK;
+}
+
+// Class names of the half-list kernels in the event timing.
+const char* relax_pair_name(bool force, int prec) {
+  if (prec == MXE_FP64) return force ? "pair64_force" : "pair64_density";
+  return force ? "pair32_force" : "pair32_density";
+}
+const char* relax_gather_name(bool force, int prec) {
+  if (prec == MXE_FP64) return force ? "gather64_force" : "gather64_density";
+  if (prec == MXE_FP32_MIXED) return force ? "gather32_force_mixed" : "gather32_density_mixed";
+  return force ? "gather32_force" : "gather32_density";
+}
+const char* accurate_gather_name(bool mu, int prec) {
+  if (prec == MXE_FP64) return mu ? "mu_gather_fp64" : "density_gather_fp64";
+  if (prec == MXE_FP32_MIXED) return mu ? "mu_gather_mixed" : "density_gather_mixed";
+  return mu ? "mu_gather_ff" : "density_gather_ff";
 }
 
 // Free energy and gradients.  want_mu: the chemical potentials are requested.
-// The FP32 modes evaluate mu (and then the energies) with more accurate
-// density and chemical-potential passes -- FP64 in MXE_FP32_MIXED, float-float
-// in MXE_FP32_FF: the flux step takes differences of neighbouring mu, so their
-// absolute error must stay far below kB T * 1e-7.  Forces and the relaxation
-// use the FP32 passes.
+// With a pair index, the accurate pass evaluates each unordered pair once
+// (geometry records: float-float node arithmetic in the FP32 modes, FP64 in
+// FP64 contexts), then gathers the densities and the chemical potentials and
+// energies per site (sums in float-float for MXE_FP32_FF, FP64 otherwise):
+// the flux step takes differences of neighbouring mu, so their absolute
+// error must stay far below kB T * 1e-7.  Forces and the relaxation use the
+// relaxation pair passes (FP32 node arithmetic in the FP32 modes).
 mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want_mu) {
   cudaStream_t st = c->stream;
-  const bool fp32 = c->precision != MXE_FP64;
-  if (!fp32) {
-    CK(TIMED(cls_name("density", 0), launch_density(0, c->nl, c->dp, c->grid, A, st)));
-    CK(TIMED(cls_name("gradient", 0, want_mu ? kGradAll : kGradForce), launch_gradient(0, want_mu ? kGradAll : kGradForce, c->nl, c->dp, c->grid, A, st)));
-    return MXE_OK;
-  }
-  const bool ffm = c->precision == MXE_FP32_FF;
-  CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32,
-                 ffm && want_mu ? c->pos32lo : nullptr, ffm && want_mu ? c->x32lo : nullptr, st)));
-  if (!want_mu) {
-    CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
-    CK(TIMED(cls_name("gradient", c->precision, kGradForce), launch_gradient(c->precision, kGradForce, c->nl, c->dp, c->grid, A, st)));
-    return MXE_OK;
-  }
-  if (ffm) {
-    // float-float: pair averages once per unordered pair, then per-site gathers
-    CK(TIMED("pair_ff", launch_pair_ff(c->dp, c->grid, A, c->pair_i, c->pair_t, c->n_upairs, c->pair_buf, st)));
-    CK(TIMED("density_gather_ff", launch_pair_gather(false, c->nl, c->dp, A, c->pid, c->pair_buf, c->n_upairs, st)));
-    CK(TIMED("mu_gather_ff", launch_pair_gather(true, c->nl, c->dp, A, c->pid, c->pair_buf, c->n_upairs, st)));
+  const int prec = c->precision;
+  const bool fp32 = prec != MXE_FP64;
+  const bool hl = has_pair_index(c) && c->pid;
+  // with the exact embedding average the pair passes run without embedding
+  const DevPot& PP = c->embedding ? c->dp_pair : c->dp;
+  if (fp32)
+    CK(TIMED("pack", launch_pack(s->q, s->sigma, s->x, c->abs_cell, c->n, c->S, c->grid, c->B, c->pos32, c->x32,
+                   hl && want_mu ? c->pos32lo : nullptr, hl && want_mu ? c->x32lo : nullptr, st)));
+  if (!hl) {  // full-list passes
+    if (!fp32) {
+      CK(TIMED(cls_name("density", 0), launch_density(0, c->nl, PP, c->grid, A, st)));
+      CK(TIMED(cls_name("gradient", 0, want_mu ? kGradAll : kGradForce),
+               launch_gradient(0, want_mu ? kGradAll : kGradForce, c->nl, PP, c->grid, A, st)));
+      return c->embedding ? enqueue_emb_exact(c, A, true) : MXE_OK;
+    }
+    if (!want_mu) {
+      CK(TIMED(cls_name("density", prec), launch_density(prec, c->nl, PP, c->grid, A, st)));
+      CK(TIMED(cls_name("gradient", prec, kGradForce), launch_gradient(prec, kGradForce, c->nl, PP, c->grid, A, st)));
+      return c->embedding ? enqueue_emb_exact(c, A, false) : MXE_OK;
+    }
+    CK(TIMED(cls_name("density", 0), launch_density(0, c->nl, PP, c->grid, A, st)));
+    CK(TIMED(cls_name("gradient", 0, kGradMu), launch_gradient(0, kGradMu, c->nl, PP, c->grid, A, st)));
+    CK(TIMED("pack_ab", launch_pack_ab(c->a, c->b, c->n, c->S, c->ab32, st)));
   } else {
-    CK(TIMED(cls_name("density", 0), launch_density(0, c->nl, c->dp, c->grid, A, st)));
-    CK(TIMED(cls_name("gradient", 0, kGradMu), launch_gradient(0, kGradMu, c->nl, c->dp, c->grid, A, st)));
+    if (fp32 && !want_mu) {
+      // forces and energies from the FP32 passes alone (energies to ~1e-6)
+      CK(TIMED(cls_name("density", prec), launch_density(prec, c->nl, PP, c->grid, A, st)));
+      CK(TIMED(cls_name("gradient", prec, kGradForce), launch_gradient(prec, kGradForce, c->nl, PP, c->grid, A, st)));
+      return c->embedding ? enqueue_emb_exact(c, A, false) : MXE_OK;
+    }
+    PassArgs G = A;
+    if (!fp32) {  // FP64: no packed records
+      G.ab32 = nullptr;
+      G.ab32lo = nullptr;
+    }
+    CK(TIMED(prec == MXE_FP64 ? "pair_geo64" : "pair_ff",
+             launch_pair_geo(prec, PP, c->grid, G, c->pair_rec, c->n_upairs, c->pair_buf, st)));
+    CK(TIMED(accurate_gather_name(false, prec),
+             launch_pair_gather(prec, false, c->nl, PP, G, c->pid, c->pair_buf, c->n_upairs, st)));
+    CK(TIMED(accurate_gather_name(true, prec),
+             launch_pair_gather(prec, true, c->nl, PP, G, c->pid, c->pair_buf, c->n_upairs, st)));
   }
-  if (!ffm) CK(TIMED("pack_ab", launch_pack_ab(c->a, c->b, c->n, c->S, c->ab32, st)));  // the float-float pass packs them itself
   if (A.gq != nullptr || A.gs != nullptr) {
     PassArgs F = A;
     F.site_E = nullptr;  // energies already come from the accurate pass
     if (half_list_forces(c)) {
       // the relaxation's force pass: each unordered pair once, then the gather
-      CK(TIMED("pair32_force", launch_relax32_pair(true, c->dp, c->grid, F, c->pair_i, c->pair_t, c->pair_rev,
-                                                    c->n_upairs, c->ent_dens, c->ent_frc, st)));
-      CK(TIMED("gather32_force", launch_relax32_gather(true, c->nl, c->dp, F, c->ent_dens, c->ent_frc, st)));
+      CK(TIMED(relax_pair_name(true, prec), launch_relax_pair(prec, true, PP, c->grid, F, c->pair_rec,
+                                                               c->n_upairs, c->ent_dens, c->ent_frc, st)));
+      CK(TIMED(relax_gather_name(true, prec),
+               launch_relax_gather(prec, true, c->nl, PP, F, c->ent_dens, c->ent_frc, st)));
     } else {
-      CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, F, st)));
+      CK(TIMED(cls_name("gradient", prec, kGradForceNoE),
+               launch_gradient(prec, kGradForceNoE, c->nl, PP, c->grid, F, st)));
     }
   }
-  return MXE_OK;
+  // the accurate pass: the exact average in FP64
+  return c->embedding ? enqueue_emb_exact(c, A, true) : MXE_OK;
 }
 
 mxe_fire_params fire_params_or_default(const mxe_fire_params* fire) {
@@ -693,16 +779,17 @@ void relax_pass_args(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
 }
 
 // The per-entry records of the half-list relaxation passes are allocated by
-// the first relaxation of a float-float context (outside any stream capture)
-// and kept, resized with the lists, from then on.
+// the first relaxation of a context with a pair index (outside any stream
+// capture) and kept, resized with the lists, from then on.
 mxe_status ensure_relax_records(mxe_ctx* c) {
-  if (c->precision != MXE_FP32_FF || !c->pid || !relax32_pairs_supported(c->dp)) return MXE_OK;
+  if (!has_pair_index(c) || !c->pid) return MXE_OK;
   c->relax_records = true;
   if (c->ent_dens && c->ent_frc) return MXE_OK;
   dfree(c->ent_dens);
   dfree(c->ent_frc);
-  CK(dalloc(&c->ent_dens, c->pair_cap));
-  CK(dalloc(&c->ent_frc, c->pair_cap));
+  const int64_t bytes = c->pair_cap * (int64_t)relax_record_bytes(c->precision);
+  CK(dalloc_bytes(&c->ent_dens, bytes));
+  CK(dalloc_bytes(&c->ent_frc, bytes));
   return MXE_OK;
 }
 
@@ -711,17 +798,28 @@ mxe_status ensure_relax_records(mxe_ctx* c) {
 // full-list passes.
 mxe_status enqueue_force_passes(mxe_ctx* c, const PassArgs& A) {
   cudaStream_t st = c->stream;
+  const DevPot& PP = c->embedding ? c->dp_pair : c->dp;
   if (half_list_forces(c)) {
     // each unordered pair once: pair kernel, then the per-site gather
-    CK(TIMED("pair32_density", launch_relax32_pair(false, c->dp, c->grid, A, c->pair_i, c->pair_t, c->pair_rev,
-                                                    c->n_upairs, c->ent_dens, c->ent_frc, st)));
-    CK(TIMED("gather32_density", launch_relax32_gather(false, c->nl, c->dp, A, c->ent_dens, c->ent_frc, st)));
-    CK(TIMED("pair32_force", launch_relax32_pair(true, c->dp, c->grid, A, c->pair_i, c->pair_t, c->pair_rev,
-                                                  c->n_upairs, c->ent_dens, c->ent_frc, st)));
-    CK(TIMED("gather32_force", launch_relax32_gather(true, c->nl, c->dp, A, c->ent_dens, c->ent_frc, st)));
+    const int prec = c->precision;
+    CK(TIMED(relax_pair_name(false, prec), launch_relax_pair(prec, false, PP, c->grid, A, c->pair_rec,
+                                                              c->n_upairs, c->ent_dens, c->ent_frc, st)));
+    CK(TIMED(relax_gather_name(false, prec),
+             launch_relax_gather(prec, false, c->nl, PP, A, c->ent_dens, c->ent_frc, st)));
+    CK(TIMED(relax_pair_name(true, prec), launch_relax_pair(prec, true, PP, c->grid, A, c->pair_rec,
+                                                             c->n_upairs, c->ent_dens, c->ent_frc, st)));
+    CK(TIMED(relax_gather_name(true, prec),
+             launch_relax_gather(prec, true, c->nl, PP, A, c->ent_dens, c->ent_frc, st)));
   } else {
-    CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, c->dp, c->grid, A, st)));
-    CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, c->dp, c->grid, A, st)));
+    CK(TIMED(cls_name("density", c->precision), launch_density(c->precision, c->nl, PP, c->grid, A, st)));
+    CK(TIMED(cls_name("gradient", c->precision, kGradForceNoE), launch_gradient(c->precision, kGradForceNoE, c->nl, PP, c->grid, A, st)));
+  }
+  if (c->embedding) {
+    PassArgs F = A;  // forces only
+    F.mu_ex = nullptr;
+    F.mu = nullptr;
+    F.site_E = nullptr;
+    return enqueue_emb_exact(c, F, c->precision == MXE_FP64);
   }
   return MXE_OK;
 }
@@ -1095,6 +1193,10 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
   if (!c) return MXE_ERR_OOM;
   mxe_status ms = make_devpot(*pot, c->dp);
   if (ms == MXE_OK && c->dp.lj && precision != MXE_FP64) ms = MXE_ERR_ARG;  // FP64 passes only
+  if (ms == MXE_OK) {
+    c->dp_pair = c->dp;
+    for (int k = 0; k < kMaxS; ++k) c->dp_pair.E[k] = 0.0;
+  }
   if (ms != MXE_OK) {
     delete c;
     return ms;
@@ -1141,13 +1243,15 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
     A(dalloc(&c->x32, n));
     A(dalloc(&c->ab32, 2 * n));
   }
-  if (precision == MXE_FP32_FF) {
+  if (has_pair_index(c)) {
     A(dalloc(&c->first_gt, n));
     A(dalloc(&c->pair_cnt, n));
     A(dalloc(&c->pair_off, n + 1));
-    A(dalloc(&c->pos32lo, n));
-    A(dalloc(&c->x32lo, n));
-    A(dalloc(&c->ab32lo, 2 * n));
+    if (precision != MXE_FP64) {
+      A(dalloc(&c->pos32lo, n));
+      A(dalloc(&c->x32lo, n));
+      A(dalloc(&c->ab32lo, 2 * n));
+    }
   }
   A(init_ff_exp_table());
   A(dalloc(&c->gq, 3 * n));
@@ -1223,16 +1327,16 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   dfree(c->tan_buf);
+  dfree(c->emb_buf);
+  dfree(c->emb_nrule);
   dfree(c->first_gt);
   dfree(c->pair_cnt);
   dfree(c->pair_off);
-  dfree(c->pair_i);
-  dfree(c->pair_t);
+  dfree(c->pair_rec);
   dfree(c->pid);
   dfree(c->pair_buf);
   dfree(c->rows_tmp);
   dfree(c->brows_tmp);
-  dfree(c->pair_rev);
   dfree(c->ent_dens);
   dfree(c->ent_frc);
   dfree(c->v_new);
@@ -1404,10 +1508,62 @@ mxe_status mxe_potential_terms(mxe_ctx* c, int32_t* n_phi, int32_t* n_f, double*
   return MXE_OK;
 }
 
+mxe_status mxe_element_param_grad(const mxe_potential* pot, const double* dterm, double* out) {
+  if (!pot || !dterm || !out) return MXE_ERR_ARG;
+  DevPot d;
+  mxe_status ms = make_devpot(*pot, d);
+  if (ms != MXE_OK) return ms;
+  const mxe_potential& p = *pot;
+  const int S = p.n_species, T = d.n_phi + d.n_f;
+  if (p.lj || (S > 1 && !p.cross_geomean)) return MXE_ERR_ARG;
+  // the element structure: the density from an l-neighbour is l's own term,
+  // whose length scale is l's pair length scale
+  for (int k = 0; k < S; ++k)
+    for (int l = 0; l < S; ++l)
+      if (p.f_xi[k][l] != p.f_xi[l][l] || p.f_q[k][l] != p.f_q[l][l] || p.f_r0[k][l] != p.f_r0[l][l] ||
+          p.f_r0[l][l] != p.phi_r0[l][l])
+        return MXE_ERR_ARG;
+  for (int e = 0; e < 4 * S; ++e) out[e] = 0.0;
+  std::vector<char> seen(T, 0);
+  // dL/dtheta_e = sum over terms u of dL/dc_u dc_u/dtheta_e + dL/dlambda_u dlambda_u/dtheta_e
+  auto add = [&](int e, double dc_dA, double dc_dp, double dc_dq, double dl_dp, double dl_dq, double dl_dr0, int u) {
+    const double gc = dterm[u], gl = dterm[T + u];
+    out[4 * e + 0] += gc * dc_dA;
+    out[4 * e + 1] += gc * dc_dp + gl * dl_dp;
+    out[4 * e + 2] += gc * dc_dq + gl * dl_dq;
+    out[4 * e + 3] += gl * dl_dr0;
+  };
+  for (int k = 0; k < S; ++k)
+    for (int l = k; l < S; ++l) {
+      const int u = d.phi_of[k][l];
+      if (u < 0 || seen[u]) continue;
+      seen[u] = 1;
+      // c = ln A_e + p_e, lambda = p_e / r0_e; the geometric-mean cross pair
+      // averages the two elements' c and lambda
+      const double wgt = (k == l) ? 1.0 : 0.5;
+      const int els[2] = {k, l};
+      for (int t = 0; t < (k == l ? 1 : 2); ++t) {
+        const int e = els[t];
+        const double A = p.phi_A[e][e], pe = p.phi_p[e][e], r0 = p.phi_r0[e][e];
+        add(e, wgt / A, wgt, 0.0, wgt / r0, 0.0, -wgt * pe / (r0 * r0), u);
+      }
+    }
+  for (int k = 0; k < S; ++k)
+    for (int l = 0; l < S; ++l) {
+      const int v = d.f_of[k][l];
+      if (v < 0 || seen[d.n_phi + v]) continue;
+      seen[d.n_phi + v] = 1;
+      // c = ln xi_l + q_l, lambda = q_l / r0_l
+      const double q = p.f_q[l][l], r0 = p.phi_r0[l][l];
+      add(l, 0.0, 0.0, 1.0, 0.0, 1.0 / r0, -q / (r0 * r0), d.n_phi + v);
+    }
+  return MXE_OK;
+}
+
 mxe_status mxe_tangent(mxe_ctx* c, const mxe_state* s, const double* dq_dev, const double* dsigma_dev,
                        const double* dx_dev, double* dFdq_dev, double* dFdsigma_dev, double* mu_ex_dev,
                        double* dFdq_t_dev, double* dFdsigma_t_dev, double* mu_ex_t_dev, double* dterm_dev) {
-  if (!c || !state_ok(c, s) || c->dp.lj) return MXE_ERR_ARG;
+  if (!c || !state_ok(c, s) || c->dp.lj || c->embedding) return MXE_ERR_ARG;
   if (!c->have_list) return MXE_ERR_STATE;
   Guard gd(c->device);
   mxe_status ms = ensure_tangent(c);
@@ -1439,7 +1595,7 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
   if (!c || !state_ok(c, s) || n_steps < 0 || every < 1 || !w_dev || !dterm_host || !(cg_tol > 0.0) ||
       cg_max < 1 || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm) || !(ftol >= 0.0) || max_iter < 0)
     return MXE_ERR_ARG;
-  if (c->precision != MXE_FP64 || c->fix_x_mask || c->fix_mu_mask || c->dp.lj) return MXE_ERR_ARG;
+  if (c->precision != MXE_FP64 || c->fix_x_mask || c->fix_mu_mask || c->dp.lj || c->embedding) return MXE_ERR_ARG;
   if (!c->have_list) return MXE_ERR_STATE;
   Guard gd(c->device);
   mxe_status ms = ensure_tangent(c);
@@ -1861,6 +2017,18 @@ mxe_status mxe_autotune(mxe_ctx* c, const mxe_state* s, int32_t* lanes_out, int3
   if (fl != MXE_OK) return fl;
   if (lanes_out) *lanes_out = c->nl;
   if (threads_out) *threads_out = c->tpb;
+  return MXE_OK;
+}
+
+mxe_status mxe_set_embedding(mxe_ctx* c, int32_t mode) {
+  if (!c || (mode != MXE_EMBED_TAYLOR && mode != MXE_EMBED_EXACT)) return MXE_ERR_ARG;
+  Guard gd(c->device);
+  if (mode == MXE_EMBED_EXACT && !c->emb_buf) {
+    CK(dalloc(&c->emb_buf, 9 * (int64_t)c->S * c->n));
+    CK(dalloc(&c->emb_nrule, c->n));
+  }
+  c->embedding = mode;
+  c->list_gen += 1;  // a captured staggered step is captured again
   return MXE_OK;
 }
 

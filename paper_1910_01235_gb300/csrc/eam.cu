@@ -487,7 +487,9 @@ __global__ void __launch_bounds__(256, MXE_DENSITY_MIN_BLOCKS) k_density(DevPot 
         const float2 b2 = rb[k].get_pair(), a2 = ra[k].get_pair();
         const float rf = b2.x + b2.y;
         const float df = fmaf(a2.x, 1.0f / 12.0f, -b2.x) + fmaf(a2.y, 1.0f / 12.0f, -b2.y);
-        if (rf > (float)kRhoMin) {
+        if (P.E[k] == 0.0) {
+          // no embedding energy for this element
+        } else if (rf > (float)kRhoMin) {
           const float Ef = (float)P.E[k];
           const float isq = rsqrt_approx(rf);
           const float dF = -0.5f * Ef * isq;
@@ -836,37 +838,110 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
   if (flag) atomicOr(A.flags, flag);
 }
 
-// ---------------------------------------------------------------- half-list float-float passes
+// ---------------------------------------------------------------- half-list accurate passes
 // The averages <phi_u>_ij, <f_v>_ij and the static f_v(r_ij) of a pair depend
 // only on its geometry and are the same from both ends (the node set of
-// App. A is symmetric in i and j).  k_pair_ff evaluates them once per
-// unordered pair (one thread per pair) into a record of C float pairs:
+// App. A is symmetric in i and j).  k_pair_geo evaluates them once per
+// unordered pair (one thread per pair) into a record of C values:
 // [f_v static (n_f) | sum over the 12 nodes of f_v (n_f) | of phi_u (n_phi)];
 // k_pair_density / k_pair_mu gather the records over every site's full row
-// (entry t -> pair pid[t]) and finish exactly as the float-float density
-// and chemical-potential passes do.
-template <int S>
-__global__ void __launch_bounds__(128) k_pair_ff(DevPot P, DevGrid g0, PassArgs A, const int* __restrict__ pair_i,
-                                                 const int* __restrict__ pair_t, int64_t npair,
-                                                 float2* __restrict__ buf, int C) {
-  using R = ff;
+// (entry t -> pair pid[t]) and finish exactly as the density and
+// chemical-potential passes do.  Node arithmetic R: float-float (records of
+// float pairs; the FP32 modes) or FP64 (records of doubles).
+// The record of unordered pair p: owner site i, the entry of j in row i (j with
+// its image code), that entry's index tp and the index tr of the reverse
+// entry (i in row j).  The records are built from the current lists, so they
+// are consistent with them by construction; every index is still bounded
+// (a bad record sets the overflow flag and the pair is skipped).  Building
+// with MXE_DEBUG_CHECKS also checks that tp and tr lie in their rows.
+struct PairRef {
+  int64_t i, j;
+  uint32_t code;
+  int tp, tr;
+};
+__device__ __forceinline__ bool load_pair(const PassArgs& A, const int4* __restrict__ rec, int64_t p, PairRef& r) {
+  const int4 v = __ldg(&rec[p]);
+  r.i = v.x;
+  r.j = (uint32_t)v.y & kIdxMask;
+  r.code = (uint32_t)v.y >> kCodeShift;
+  r.tp = v.z;
+  r.tr = v.w;
+  bool ok = (uint64_t)(uint32_t)v.x < (uint64_t)A.n && (uint64_t)r.j < (uint64_t)A.n &&
+            (uint64_t)(uint32_t)v.z < (uint64_t)A.n_ent && (uint64_t)(uint32_t)v.w < (uint64_t)A.n_ent;
+#ifdef MXE_DEBUG_CHECKS
+  ok = ok && r.tp >= A.nb_off[r.i] && r.tp < A.nb_off[r.i + 1] && A.nb_ent[r.tp] == (uint32_t)v.y &&
+       r.tr >= A.nb_off[r.j] && r.tr < A.nb_off[r.j + 1] && (A.nb_ent[r.tr] & kIdxMask) == (uint32_t)r.i;
+#endif
+  if (!ok) atomicOr(A.flags, kFlagOverflow);
+  return ok;
+}
+
+template <typename R>
+struct GeoRec;
+template <>
+struct GeoRec<ff> {
+  using T = float2;
+  static __device__ __forceinline__ T put(ff v) { return make_float2(v.hi, v.lo); }
+  static __device__ __forceinline__ ff get(const T* __restrict__ rec, int c) {
+    const float2 v = __ldg(&rec[c]);
+    return ff(v.x, v.y);
+  }
+};
+template <>
+struct GeoRec<double> {
+  using T = double;
+  static __device__ __forceinline__ T put(double v) { return v; }
+  static __device__ __forceinline__ double get(const T* __restrict__ rec, int c) { return __ldg(&rec[c]); }
+};
+
+// site data of the accurate passes: float-float records (PREC 3) or FP64 state
+template <typename R>
+struct GeoPrec;
+template <>
+struct GeoPrec<ff> {
+  static constexpr int P = 3;
+};
+template <>
+struct GeoPrec<double> {
+  static constexpr int P = 0;
+};
+
+// a radial term at a node: exponential terms in R (float-float: with the
+// exponential's table in shared memory); thermalized Lennard-Jones pair terms
+// (FP64 contexts only) through rad_pair
+__device__ __forceinline__ ff geo_term(const RadialFn& F, ff r, const float2* T) {
+  return ff_exp(F.lnA_kappa_ff - F.lambda_ff * r, T);
+}
+__device__ __forceinline__ double geo_term(const RadialFn& F, double r, const float2*) { return rad_raw(F, r); }
+__device__ __forceinline__ ff pair_term(const RadialFn& F, ff r, const float2* T) { return geo_term(F, r, T); }
+__device__ __forceinline__ double pair_term(const RadialFn& F, double r, const float2*) {
+  double e, mde;
+  rad_pair(F, r, e, mde);
+  return e;
+}
+
+template <int S, typename R>
+__global__ void __launch_bounds__(128) k_pair_geo(DevPot P, DevGrid g0, PassArgs A,
+                                                  const int4* __restrict__ pair_rec, int64_t npair,
+                                                  typename GeoRec<R>::T* __restrict__ buf, int C) {
+  constexpr int PR = GeoPrec<R>::P;
+  // the float-float exponential's table, in shared memory (read by the
+  // halt check's barrier below before any use)
+  __shared__ float2 s_exp[32];
+  if (threadIdx.x < 32) s_exp[threadIdx.x] = make_float2(c_exp_table.hi[threadIdx.x], c_exp_table.lo[threadIdx.x]);
+  if (A.ctrl == nullptr) __syncthreads();
   if (chunk_halted(A)) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npair) return;
-  const int64_t i = pair_i[p];
-  const int tp = pair_t[p];
-  if (i < 0 || i >= A.n || tp < A.nb_off[i] || tp >= A.nb_off[i + 1]) {  // index not built for this list
-    atomicOr(A.flags, kFlagOverflow);
-    return;
-  }
-  const uint32_t ent = A.nb_ent[tp];
-  const int64_t j = ent & kIdxMask;
+  PairRef pr_;
+  if (!load_pair(A, pair_rec, p, pr_)) return;
+  const int64_t i = pr_.i, j = pr_.j;
   const DevGrid gs = site_grid(g0, A.batch, i);
-  SiteData<3, S> si, sj;
+  SiteData<PR, S> si, sj;
   load_site(A, i, si);
   load_site(A, j, sj);
   R d[3];
-  separation(gs, si, sj, ent >> kCodeShift, d);
+  separation(gs, si, sj, pr_.code, d);
   const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
   const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   int bad = D2 < (R)(kRMin * kRMin);
@@ -891,28 +966,29 @@ __global__ void __launch_bounds__(128) k_pair_ff(DevPot P, DevGrid g0, PassArgs 
   }
   // one term at a time over the points (rolled: one copy of the float-float
   // exponential in the loop body)
-  float2* o = buf + p * (int64_t)C;
+  typename GeoRec<R>::T* o = buf + p * (int64_t)C;
 #pragma unroll 1
   for (int v = 0; v < P.n_f; ++v) {
-    R acc(0.f, 0.f);
+    R acc = (R)0;
 #pragma unroll 1
-    for (int k = 0; k < 12; ++k) acc += rad_raw(P.f[v], pr[k]) * pw[k];
-    const R st = rad_raw(P.f[v], pr[12]) * pw[12];
-    o[v] = make_float2(st.hi, st.lo);
-    o[P.n_f + v] = make_float2(acc.hi, acc.lo);
+    for (int k = 0; k < 12; ++k) acc += geo_term(P.f[v], pr[k], s_exp) * pw[k];
+    const R st = geo_term(P.f[v], pr[12], s_exp) * pw[12];
+    o[v] = GeoRec<R>::put(st);
+    o[P.n_f + v] = GeoRec<R>::put(acc);
   }
 #pragma unroll 1
   for (int u = 0; u < P.n_phi; ++u) {
-    R acc(0.f, 0.f);
+    R acc = (R)0;
 #pragma unroll 1
-    for (int k = 0; k < 12; ++k) acc += rad_raw(P.phi[u], pr[k]) * pw[k];
-    o[2 * P.n_f + u] = make_float2(acc.hi, acc.lo);
+    for (int k = 0; k < 12; ++k) acc += pair_term(P.phi[u], pr[k], s_exp) * pw[k];
+    o[2 * P.n_f + u] = GeoRec<R>::put(acc);
   }
   if (bad) atomicOr(A.flags, kFlagGeometry);
 }
 
-// per-site sums of the gathers in float-float on the FP32 pipe (a conversion
-// to FP64 per term would load GB300's slow FP64 pipe)
+// per-site sums of the float-float gathers in float-float on the FP32 pipe (a
+// conversion to FP64 per term would load GB300's slow FP64 pipe); the mixed
+// and FP64 contexts sum in FP64 (AccD)
 struct AccF2 {
   ff v;
   __device__ __forceinline__ void zero() { v = ff(0.f, 0.f); }
@@ -926,21 +1002,30 @@ struct AccF2 {
   }
 };
 
-__device__ __forceinline__ ff ld_ff(const float2* __restrict__ rec, int c) {
-  const float2 v = __ldg(&rec[c]);
-  return ff(v.x, v.y);
+// molar fractions of a neighbour in the accurate passes
+template <int S>
+__device__ __forceinline__ void load_x(const PassArgs& A, int64_t j, ff x[S]) {
+  const float4 X = __ldg(&A.x32[j]), Xl = __ldg(&A.x32lo[j]);
+  const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
+#pragma unroll
+  for (int k = 0; k < S; ++k) x[k] = ff(xs[k], xl[k]);
+}
+template <int S>
+__device__ __forceinline__ void load_x(const PassArgs& A, int64_t j, double x[S]) {
+#pragma unroll
+  for (int k = 0; k < S; ++k) x[k] = __ldg(&A.x[k * A.n + j]);
 }
 
-template <int S, int NL>
+template <int S, int NL, typename R, typename Acc>
 __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, const int* __restrict__ pid,
-                                                      const float2* __restrict__ buf, int C, int64_t npair) {
-  using R = ff;
+                                                      const typename GeoRec<R>::T* __restrict__ buf, int C,
+                                                      int64_t npair) {
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
   const int lane = (int)(tid % NL);
   const bool active = i < A.n;
-  AccF2 rb[S], ra[S];
+  Acc rb[S], ra[S];
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     rb[k].zero();
@@ -956,21 +1041,18 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
         atomicOr(A.flags, kFlagOverflow);
         continue;
       }
-      const float2* rec = buf + (int64_t)pp * C;
-      SiteData<3, S> sj;
-      const float4 X = __ldg(&A.x32[j]), Xl = __ldg(&A.x32lo[j]);
-      const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
-#pragma unroll
-      for (int k = 0; k < S; ++k) sj.x[k] = ff(xs[k], xl[k]);
+      const typename GeoRec<R>::T* rec = buf + (int64_t)pp * C;
+      R xj[S];
+      load_x<S>(A, j, xj);
 #pragma unroll
       for (int k = 0; k < S; ++k) {
-        R sb(0.f, 0.f), sa(0.f, 0.f);
+        R sb = (R)0, sa = (R)0;
 #pragma unroll
         for (int l = 0; l < S; ++l) {
           const int v = P.f_of[k][l];
           if (v < 0) continue;
-          sb += sj.x[l] * ld_ff(rec, v);
-          sa += sj.x[l] * ld_ff(rec, P.n_f + v);
+          sb += xj[l] * GeoRec<R>::get(rec, v);
+          sa += xj[l] * GeoRec<R>::get(rec, P.n_f + v);
         }
         rb[k].add(sb);
         ra[k].add(sa);
@@ -990,14 +1072,14 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
   // Every lane reaches every shuffle.
   static_assert(S <= 2 && NL >= S, "one team lane per species");
   const int src = (int)(threadIdx.x & 31) - lane;
-  ff rbk(0.f, 0.f), rak(0.f, 0.f);
+  double rbar = 0.0, rsum = 0.0;
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const ff wb(__shfl_sync(0xffffffffu, rb[k].v.hi, src), __shfl_sync(0xffffffffu, rb[k].v.lo, src));
-    const ff wa(__shfl_sync(0xffffffffu, ra[k].v.hi, src), __shfl_sync(0xffffffffu, ra[k].v.lo, src));
+    const double wb = __shfl_sync(0xffffffffu, rb[k].get(), src);
+    const double wa = __shfl_sync(0xffffffffu, ra[k].get(), src);
     if (lane == k) {
-      rbk = wb;
-      rak = wa;
+      rbar = wb;
+      rsum = wa;
     }
   }
   const int64_t n = A.n;
@@ -1006,11 +1088,12 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
   if (mine) {
     const int k = lane;
     const double Ek = (S > 1 && k == 1) ? P.E[S > 1 ? 1 : 0] : P.E[0];
-    const double rbar = ff_to_double(rbk);
-    const double ravg = ff_to_double(rak) * (1.0 / 12.0);
+    const double ravg = rsum * (1.0 / 12.0);
     const double xk = A.x[k * n + i];
     double e = 0.0, ak = 0.0, bk = 0.0;
-    if (rbar > kRhoMin) {
+    if (Ek == 0.0) {
+      // no embedding energy for this element
+    } else if (rbar > kRhoMin) {
       const double sq = sqrt(rbar);
       const double F = -Ek * sq;
       const double dF = -Ek / (2.0 * sq);
@@ -1031,6 +1114,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
     lak = (float)(ak - (double)abk);
     lbk = (float)(bk - (double)bbk);
   }
+  if (A.ab32 == nullptr) return;  // FP64 contexts: no packed records
   // the packed FP32 (a, b) records of both species, written by team lane 0
   float ab[4] = {abk, bbk, 0.f, 0.f}, lo[4] = {lak, lbk, 0.f, 0.f};
   if (S > 1) {
@@ -1041,31 +1125,28 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
   }
   if (!active || lane != 0) return;
   A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
-  A.ab32lo[2 * i] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+  if (A.ab32lo) A.ab32lo[2 * i] = make_float4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-template <int S, int NL>
+template <int S, int NL, typename R, typename Acc>
 __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int* __restrict__ pid,
-                                                 const float2* __restrict__ buf, int C, int64_t npair) {
-  using R = ff;
+                                                 const typename GeoRec<R>::T* __restrict__ buf, int C,
+                                                 int64_t npair) {
+  constexpr int PR = GeoPrec<R>::P;
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
   const int lane = (int)(tid % NL);
   const bool active = i < A.n;
-  AccF2 mu[S], epair;
+  Acc mu[S], epair;
   epair.zero();
 #pragma unroll
   for (int k = 0; k < S; ++k) mu[k].zero();
   if (active) {
-    SiteData<3, S> si;
-    {
-      const float4 X = __ldg(&A.x32[i]), Xl = __ldg(&A.x32lo[i]);
-      const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
-#pragma unroll
-      for (int k = 0; k < S; ++k) si.x[k] = ff(xs[k], xl[k]);
-    }
+    R xi[S];
+    load_x<S>(A, i, xi);
     const R inv12 = (R)(1.0 / 12.0);
+    const R half = (R)0.5;
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
     for (int t = beg + lane; t < end; t += NL) {
       const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
@@ -1074,35 +1155,30 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
         atomicOr(A.flags, kFlagOverflow);
         continue;
       }
-      const float2* rec = buf + (int64_t)pp * C;
-      SiteData<3, S> sj;
-      {
-        const float4 X = __ldg(&A.x32[j]), Xl = __ldg(&A.x32lo[j]);
-        const float xs[4] = {X.x, X.y, X.z, X.w}, xl[4] = {Xl.x, Xl.y, Xl.z, Xl.w};
-#pragma unroll
-        for (int k = 0; k < S; ++k) sj.x[k] = ff(xs[k], xl[k]);
-      }
+      const typename GeoRec<R>::T* rec = buf + (int64_t)pp * C;
+      R xj[S];
+      load_x<S>(A, j, xj);
       R aj[S], bj[S];
-      load_ab(A, j, aj, bj, (SiteData<3, S>*)nullptr);
-      R ep(0.f, 0.f);
+      load_ab(A, j, aj, bj, (SiteData<PR, S>*)nullptr);
+      R ep = (R)0;
 #pragma unroll
       for (int k = 0; k < S; ++k) {
-        R m(0.f, 0.f);
+        R m = (R)0;
 #pragma unroll
         for (int l = 0; l < S; ++l) {
           const int u = P.phi_of[k][l];
           if (u >= 0) {
-            const R ph = ld_ff(rec, 2 * P.n_f + u);
-            m += sj.x[l] * ph * inv12;
-            ep += si.x[k] * sj.x[l] * ph;
+            const R ph = GeoRec<R>::get(rec, 2 * P.n_f + u);
+            m += xj[l] * ph * inv12;
+            ep += xi[k] * xj[l] * ph;
           }
           // density at j of species l from this site holding species k: f_lk
           const int v = P.f_of[l][k];
-          if (v >= 0) m += aj[l] * ld_ff(rec, v) + bj[l] * ld_ff(rec, P.n_f + v) * inv12;
+          if (v >= 0) m += aj[l] * GeoRec<R>::get(rec, v) + bj[l] * GeoRec<R>::get(rec, P.n_f + v) * inv12;
         }
         mu[k].add(m);
       }
-      epair.add(ff(0.5f, 0.f) * inv12 * ep);
+      epair.add(half * inv12 * ep);
     }
   }
   if (NL > 1) {
@@ -1117,10 +1193,10 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
   // those of team lane 0; every lane reaches every shuffle.
   static_assert(NL >= S + 2, "one team lane per logarithm");
   const int src = (int)(threadIdx.x & 31) - lane;
-  ff mk(0.f, 0.f);
+  double mk = 0.0;
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const ff w(__shfl_sync(0xffffffffu, mu[k].v.hi, src), __shfl_sync(0xffffffffu, mu[k].v.lo, src));
+    const double w = __shfl_sync(0xffffffffu, mu[k].get(), src);
     if (lane == k) mk = w;
   }
   const int64_t n = A.n;
@@ -1144,7 +1220,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
   bool finite = true;
   if (active && lane < S) {
     const double kT = kKB * A.T[i];
-    const double m = ff_to_double(mk) + A.e[lane * n + i];
+    const double m = mk + A.e[lane * n + i];
     finite = isfinite(m);
     if (A.mu_ex) A.mu_ex[lane * n + i] = m;
     if (A.mu) A.mu[lane * n + i] = m + kT * (L - lv);
@@ -1157,6 +1233,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
 #pragma unroll
     for (int k = 0; k <= S; ++k) tk[k] = __shfl_sync(0xffffffffu, t, src + k);
     const double Ls = __shfl_sync(0xffffffffu, L, src + S + 1);
+    const double ept = __shfl_sync(0xffffffffu, epair.get(), src);
     if (active && lane == 0) {
       const double kT = kKB * A.T[i];
       double mix = 0.0, emb = 0.0;
@@ -1167,7 +1244,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
         emb += x * A.e[k * n + i];
       }
       if (xv > 0.0) mix += tk[S];
-      const double EV = epair.get() + emb;
+      const double EV = ept + emb;
       const double Fv = -3.0 * kT * Ls;
       const double Fm = kT * mix;
       A.site_E[i] = EV;
@@ -1179,47 +1256,88 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
   if (!finite) atomicOr(A.flags, kFlagNonfinite);
 }
 
-// ---------------------------------------------------------------- half-list FP32 relaxation passes
-// The relaxation's density and force passes in the FP32-with-float-float-sums
-// mode, each unordered pair evaluated once:
-//  k_pair32_density: f_v(r_ij) and the sum of f_v over the 12 nodes (both
-//    symmetric in i, j) -> dens[p] (float4, n_f <= 2);
-//  k_gather32_density: per site the sums over its row, then the embedding
-//    coefficients (a, b) as the lean density pass writes them;
-//  k_pair32_force: with the pair's weights (x, a, b of both sites) the force
+// ---------------------------------------------------------------- half-list relaxation passes
+// The relaxation's density and force passes, each unordered pair evaluated
+// once (PREC 1, 2: FP32 node arithmetic, float4 records; PREC 0: FP64, records
+// of four doubles):
+//  k_pair_rdensity: f_v(r_ij) and the sum of f_v over the 12 nodes (both
+//    symmetric in i, j), weighted by the other site's fractions, written to
+//    both entries of the pair;
+//  k_gather_rdensity: per site the sums over its row (float-float in PREC 2,
+//    FP64 otherwise), then the embedding coefficients (a, b): packed FP32
+//    records (PREC 1, 2) or the FP64 arrays (PREC 0);
+//  k_pair_rforce: with the pair's weights (x, a, b of both sites) the force
 //    on the row-owner site i, F_i = -(d T + U / 12), d = q_j - q_i (the other
 //    site receives -F_i: the pair functions are symmetric), and the width
 //    derivatives of both sites (over the nodes that move i and those that
-//    move j) -> frc[p] = (F_i, dF/dsigma_i part), gsj[p] = dF/dsigma_j part;
-//  k_gather32_force: per site the signed sums, then the thermal term.
-template <int S>
-__global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, PassArgs A,
-                                                        const int* __restrict__ pair_i,
-                                                        const int* __restrict__ pair_t,
-                                                        const int* __restrict__ pair_rev, int64_t npair,
-                                                        float4* __restrict__ dens) {
-  using R = float;
+//    move j), written to the two entries of the pair;
+//  k_gather_rforce: per site the sums over its row, then the thermal term.
+struct alignas(32) Dbl4 {
+  double x, y, z, w;
+};
+
+template <typename R>
+struct Rec4;
+template <>
+struct Rec4<float> {
+  using T = float4;
+  static __device__ __forceinline__ T make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+  static __device__ __forceinline__ void load(const T* __restrict__ p, float v[4]) {
+    const float4 r = __ldg(p);
+    v[0] = r.x;
+    v[1] = r.y;
+    v[2] = r.z;
+    v[3] = r.w;
+  }
+};
+template <>
+struct Rec4<double> {
+  using T = Dbl4;
+  static __device__ __forceinline__ T make(double a, double b, double c, double d) { return Dbl4{a, b, c, d}; }
+  static __device__ __forceinline__ void load(const T* __restrict__ p, double v[4]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 r0 = __ldg(q), r1 = __ldg(q + 1);
+    v[0] = r0.x;
+    v[1] = r0.y;
+    v[2] = r1.x;
+    v[3] = r1.y;
+  }
+};
+
+// per-site sums of the relaxation gathers: float-float in PREC 2, FP64 otherwise
+template <int PREC>
+struct RelaxAcc {
+  using T = AccD;
+};
+template <>
+struct RelaxAcc<2> {
+  using T = AccFF;
+};
+
+template <int PREC, int S, int TAB>
+__global__ void __launch_bounds__(128) k_pair_rdensity(DevPot P, DevGrid g0, PassArgs A,
+                                                       const int4* __restrict__ pair_rec, int64_t npair,
+                                                       typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens) {
+  using R = typename Traits<PREC>::R;
+  using RT = Rec4<R>;
+  using TB = Tables<TAB>;
   constexpr int NF = S * S;
   if (chunk_halted(A)) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npair) return;
-  const int64_t i = pair_i[p];
-  const int tp = pair_t[p];
-  if (i < 0 || i >= A.n || tp < A.nb_off[i] || tp >= A.nb_off[i + 1]) {
-    atomicOr(A.flags, kFlagOverflow);
-    return;
-  }
-  const uint32_t ent = A.nb_ent[tp];
-  const int64_t j = ent & kIdxMask;
+  PairRef pr_;
+  if (!load_pair(A, pair_rec, p, pr_)) return;
+  const int64_t i = pr_.i, j = pr_.j;
+  const int tp = pr_.tp, tr = pr_.tr;
   const DevGrid gs = site_grid(g0, A.batch, i);
-  SiteData<2, S> si, sj;
+  SiteData<PREC, S> si, sj;
   load_site(A, i, si);
   load_site(A, j, sj);
   R d[3];
-  separation(gs, si, sj, ent >> kCodeShift, d);
+  separation(gs, si, sj, pr_.code, d);
   const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
   const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  const R near = (R)kRMin + fmaxf(s_i, s_j);
+  const R near = (R)kRMin + (s_i < s_j ? s_j : s_i);
   R fst[NF], fav[NF];
   {
     R r, rinv, Sw, dS;
@@ -1227,8 +1345,8 @@ __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, Pa
     sw(P, r, Sw, dS);
 #pragma unroll
     for (int v = 0; v < NF; ++v) {
-      fst[v] = v < P.n_f ? rad_raw(P.f[v], r) * Sw : 0.f;
-      fav[v] = 0.f;
+      fst[v] = v < TB::n_f(P) ? rad_raw(P.f[v], r) * Sw : (R)0;
+      fav[v] = (R)0;
     }
   }
 #pragma unroll
@@ -1237,7 +1355,7 @@ __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, Pa
     const R base = D2 + s * s;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const R tw = 2.f * s * d[a];
+      const R tw = (R)2 * s * d[a];
 #pragma unroll
       for (int pm = 0; pm < 2; ++pm) {
         const R r2 = pm == 0 ? base + tw : base - tw;
@@ -1246,16 +1364,16 @@ __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, Pa
         sw(P, r, Sw, dS);
 #pragma unroll
         for (int v = 0; v < NF; ++v)
-          if (v < P.n_f) fav[v] += rad_raw(P.f[v], r) * Sw;
+          if (v < TB::n_f(P)) fav[v] += rad_raw(P.f[v], r) * Sw;
       }
     }
   }
-  int bad = 0;
+  int bad = D2 < (R)(kRMin * kRMin);
   if (D2 < near * near) {  // rare: the exact node distances
     for (int site = 0; site < 2; ++site) {
       const R s = site == 0 ? s_i : s_j;
       for (int a = 0; a < 3; ++a) {
-        const R base = D2 + s * s, tw = 2.f * s * d[a];
+        const R base = D2 + s * s, tw = (R)2 * s * d[a];
         bad |= (base + tw) < (R)(kRMin * kRMin);
         bad |= (base - tw) < (R)(kRMin * kRMin);
       }
@@ -1263,12 +1381,12 @@ __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, Pa
   }
   // each entry receives its own site's density contributions from the other
   // site: (rho_bar^0, rho_bar^1, <rho>^0, <rho>^1) x 12 for the average
-  float ci[4] = {0.f, 0.f, 0.f, 0.f}, cj[4] = {0.f, 0.f, 0.f, 0.f};
+  R ci[4] = {(R)0, (R)0, (R)0, (R)0}, cj[4] = {(R)0, (R)0, (R)0, (R)0};
 #pragma unroll
   for (int k = 0; k < S; ++k)
 #pragma unroll
     for (int l = 0; l < S; ++l) {
-      const int v = P.f_of[k][l];
+      const int v = TB::f(P, k, l);
 #pragma unroll
       for (int w = 0; w < NF; ++w)
         if (v == w) {
@@ -1278,22 +1396,22 @@ __global__ void __launch_bounds__(128) k_pair32_density(DevPot P, DevGrid g0, Pa
           cj[2 + k] += si.x[l] * fav[w];
         }
     }
-  const int tr = pair_rev[p];
-  dens[tp] = make_float4(ci[0], ci[1], ci[2], ci[3]);
-  if (tr >= A.nb_off[j] && tr < A.nb_off[j + 1]) dens[tr] = make_float4(cj[0], cj[1], cj[2], cj[3]);
-  else bad |= 2;
-  if (bad & 1) atomicOr(A.flags, kFlagGeometry);
-  if (bad & 2) atomicOr(A.flags, kFlagOverflow);
+  dens[tp] = RT::make(ci[0], ci[1], ci[2], ci[3]);
+  dens[tr] = RT::make(cj[0], cj[1], cj[2], cj[3]);
+  if (bad) atomicOr(A.flags, kFlagGeometry);
 }
 
-template <int S, int NL>
-__global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, const float4* __restrict__ dens) {
+template <int PREC, int S, int NL>
+__global__ void __launch_bounds__(256) k_gather_rdensity(DevPot P, PassArgs A,
+                                                         const typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens) {
+  using R = typename Traits<PREC>::R;
+  using Acc = typename RelaxAcc<PREC>::T;
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
   const int lane = (int)(tid % NL);
   const bool active = i < A.n;
-  AccFF rb[S], ra[S];
+  Acc rb[S], ra[S];
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     rb[k].zero();
@@ -1303,12 +1421,13 @@ __global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, 
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
 #pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
-      const float4 rec = __ldg(&dens[t]);
-      rb[0].add(rec.x);
-      ra[0].add(rec.z);
+      R rec[4];
+      Rec4<R>::load(&dens[t], rec);
+      rb[0].add(rec[0]);
+      ra[0].add(rec[2]);
       if (S > 1) {
-        rb[S > 1 ? 1 : 0].add(rec.y);
-        ra[S > 1 ? 1 : 0].add(rec.w);
+        rb[S > 1 ? 1 : 0].add(rec[1]);
+        ra[S > 1 ? 1 : 0].add(rec[3]);
       }
     }
   }
@@ -1321,71 +1440,95 @@ __global__ void __launch_bounds__(256) k_gather32_density(DevPot P, PassArgs A, 
   }
   if (!active || lane != 0) return;
   int flag = 0;
-  float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const float4 X = A.x32[i];
-  const float xs[4] = {X.x, X.y, X.z, X.w};
+  const int64_t n = A.n;
+  if constexpr (PREC == 0) {
+    // FP64 embedding coefficients, as the FP64 density pass forms them
 #pragma unroll
-  for (int k = 0; k < S; ++k) {
-    const float2 b2 = rb[k].get_pair(), a2 = ra[k].get_pair();
-    const float rf = b2.x + b2.y;
-    const float df = fmaf(a2.x, 1.0f / 12.0f, -b2.x) + fmaf(a2.y, 1.0f / 12.0f, -b2.y);
-    if (rf > (float)kRhoMin) {
-      const float Ef = (float)P.E[k];
-      const float isq = rsqrt_approx(rf);
-      const float dF = -0.5f * Ef * isq;
-      const float d2F = 0.25f * Ef * isq * isq * isq;
-      ab[2 * k] = xs[k] * d2F * df;
-      ab[2 * k + 1] = xs[k] * dF;
-    } else {
-      flag |= kFlagGeometry;
+    for (int k = 0; k < S; ++k) {
+      const double rbar = rb[k].get();
+      const double ravg = ra[k].get() * (1.0 / 12.0);
+      const double xk = A.x[k * n + i];
+      double ak = 0.0, bk = 0.0;
+      if (P.E[k] == 0.0) {
+        // no embedding energy for this element
+      } else if (rbar > kRhoMin) {
+        const double sq = sqrt(rbar);
+        const double dF = -P.E[k] / (2.0 * sq);
+        const double d2F = P.E[k] / (4.0 * rbar * sq);
+        ak = xk * d2F * (ravg - rbar);
+        bk = xk * dF;
+      } else {
+        flag |= kFlagGeometry;
+      }
+      A.a[k * n + i] = ak;
+      A.b[k * n + i] = bk;
     }
+  } else {
+    float ab[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float4 X = A.x32[i];
+    const float xs[4] = {X.x, X.y, X.z, X.w};
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const float2 b2 = rb[k].get_pair(), a2 = ra[k].get_pair();
+      const float rf = b2.x + b2.y;
+      const float df = fmaf(a2.x, 1.0f / 12.0f, -b2.x) + fmaf(a2.y, 1.0f / 12.0f, -b2.y);
+      if (P.E[k] == 0.0) {
+        // no embedding energy for this element
+      } else if (rf > (float)kRhoMin) {
+        const float Ef = (float)P.E[k];
+        const float isq = rsqrt_approx(rf);
+        const float dF = -0.5f * Ef * isq;
+        const float d2F = 0.25f * Ef * isq * isq * isq;
+        ab[2 * k] = xs[k] * d2F * df;
+        ab[2 * k + 1] = xs[k] * dF;
+      } else {
+        flag |= kFlagGeometry;
+      }
+    }
+    A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
   }
-  A.ab32[2 * i] = make_float4(ab[0], ab[1], ab[2], ab[3]);
   if (flag) atomicOr(A.flags, flag);
 }
 
-template <int S>
-__global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, PassArgs A,
-                                                      const int* __restrict__ pair_i, const int* __restrict__ pair_t,
-                                                      const int* __restrict__ pair_rev, int64_t npair,
-                                                      float4* __restrict__ frc) {
-  using R = float;
+template <int PREC, int S, int TAB>
+__global__ void __launch_bounds__(128) k_pair_rforce(DevPot P, DevGrid g0, PassArgs A,
+                                                     const int4* __restrict__ pair_rec, int64_t npair,
+                                                     typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc) {
+  using R = typename Traits<PREC>::R;
+  using RT = Rec4<R>;
+  using TB = Tables<TAB>;
   constexpr int NF = S * S;
   constexpr int NP = S * (S + 1) / 2;
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npair) return;
-  const int64_t i = pair_i[p];
-  const int tp = pair_t[p];
-  if (i < 0 || i >= A.n || tp < A.nb_off[i] || tp >= A.nb_off[i + 1]) {
-    atomicOr(A.flags, kFlagOverflow);
-    return;
-  }
-  const uint32_t ent = A.nb_ent[tp];
-  const int64_t j = ent & kIdxMask;
+  PairRef pr_;
+  if (!load_pair(A, pair_rec, p, pr_)) return;
+  const int64_t i = pr_.i, j = pr_.j;
+  const int tp = pr_.tp, tr = pr_.tr;
   const DevGrid gs = site_grid(g0, A.batch, i);
-  SiteData<2, S> si, sj;
+  SiteData<PREC, S> si, sj;
   load_site(A, i, si);
   load_site(A, j, sj);
   R ai[S], bi[S], aj[S], bj[S];
-  load_ab(A, i, ai, bi, (SiteData<2, S>*)nullptr);
-  load_ab(A, j, aj, bj, (SiteData<2, S>*)nullptr);
+  load_ab(A, i, ai, bi, (SiteData<PREC, S>*)nullptr);
+  load_ab(A, j, aj, bj, (SiteData<PREC, S>*)nullptr);
   R d[3];
-  separation(gs, si, sj, ent >> kCodeShift, d);
+  separation(gs, si, sj, pr_.code, d);
   const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
   const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   R cphi[NP], cfa[NF], cfs[NF];
 #pragma unroll
-  for (int u = 0; u < NP; ++u) cphi[u] = 0.f;
+  for (int u = 0; u < NP; ++u) cphi[u] = (R)0;
 #pragma unroll
-  for (int v = 0; v < NF; ++v) cfa[v] = cfs[v] = 0.f;
+  for (int v = 0; v < NF; ++v) cfa[v] = cfs[v] = (R)0;
 #pragma unroll
   for (int k = 0; k < S; ++k)
 #pragma unroll
     for (int l = 0; l < S; ++l) {
       // table entries read once (compared inside the unrolled loops they
       // sent a copy of the tables to the stack)
-      const int po = P.phi_of[k][l], fo = P.f_of[k][l];
+      const int po = TB::phi(P, k, l), fo = TB::f(P, k, l);
 #pragma unroll
       for (int u = 0; u < NP; ++u)
         if (po == u) cphi[u] += si.x[k] * sj.x[l];
@@ -1396,33 +1539,33 @@ __global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, Pass
           cfs[v] += ai[k] * sj.x[l] + aj[k] * si.x[l];
         }
     }
-  R clphi[NP], clf[NF];
+  R clphi[NP], clf[NF];  // weights times decay rates (factored derivative)
 #pragma unroll
-  for (int u = 0; u < NP; ++u) clphi[u] = cphi[u] * P.phi[u].lam_f;
+  for (int u = 0; u < NP; ++u) clphi[u] = cphi[u] * rad_lam(P.phi[u], s_i);
 #pragma unroll
-  for (int v = 0; v < NF; ++v) clf[v] = cfa[v] * P.f[v].lam_f;
+  for (int v = 0; v < NF; ++v) clf[v] = cfa[v] * rad_lam(P.f[v], s_i);
   R Gs;
   {
     R r, rinv, Sw, dS;
     r_from_r2(D2, r, rinv);
     sw(P, r, Sw, dS);
-    Gs = 0.f;
+    Gs = (R)0;
 #pragma unroll
     for (int v = 0; v < NF; ++v)
-      if (v < P.n_f) {
+      if (v < TB::n_f(P)) {
         const R e = rad_raw(P.f[v], r);
-        Gs += cfs[v] * (e * (dS - P.f[v].lam_f * Sw));
+        Gs += cfs[v] * (e * (dS - rad_lam(P.f[v], r) * Sw));
       }
     Gs *= rinv;
   }
-  R T = 0.f, U[3] = {0.f, 0.f, 0.f}, Vs[2] = {0.f, 0.f};
+  R T = (R)0, U[3] = {(R)0, (R)0, (R)0}, Vs[2] = {(R)0, (R)0};
 #pragma unroll
   for (int site = 0; site < 2; ++site) {
     const R s = site == 0 ? s_i : s_j;
     const R base = D2 + s * s;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const R tw = 2.f * s * d[a];
+      const R tw = (R)2 * s * d[a];
       R w2[2];
 #pragma unroll
       for (int pm = 0; pm < 2; ++pm) {
@@ -1430,17 +1573,24 @@ __global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, Pass
         R r, rinv, Sw, dS;
         r_from_r2(r2, r, rinv);
         sw(P, r, Sw, dS);
-        R A1 = 0.f, A2 = 0.f;
+        R A1 = (R)0, A2 = (R)0;
 #pragma unroll
         for (int u = 0; u < NP; ++u)
-          if (u < P.n_phi) {
-            const R e = rad_raw(P.phi[u], r);
-            A1 += cphi[u] * e;
-            A2 += clphi[u] * e;
+          if (u < TB::n_phi(P)) {
+            if constexpr (PREC == 0) {
+              double e, mde;  // exponential or Lennard-Jones term and minus its derivative
+              rad_pair(P.phi[u], r, e, mde);
+              A1 += cphi[u] * e;
+              A2 += cphi[u] * mde;
+            } else {
+              const R e = rad_raw(P.phi[u], r);
+              A1 += cphi[u] * e;
+              A2 += clphi[u] * e;
+            }
           }
 #pragma unroll
         for (int v = 0; v < NF; ++v)
-          if (v < P.n_f) {
+          if (v < TB::n_f(P)) {
             const R e = rad_raw(P.f[v], r);
             A1 += cfa[v] * e;
             A2 += clf[v] * e;
@@ -1452,25 +1602,26 @@ __global__ void __launch_bounds__(128) k_pair32_force(DevPot P, DevGrid g0, Pass
       Vs[site] += sqrt6<R>() * ((d[a] + s) * w2[0] - (d[a] - s) * w2[1]);
     }
   }
-  const R inv12 = 1.0f / 12.0f;
+  const R inv12 = (R)(1.0 / 12.0);
   const R Tt = T * inv12 + Gs;
   // this entry: the force on i and its width derivative; the reverse entry:
   // the force on j (Newton's third law) and j's width derivative
-  const float Fx = -(d[0] * Tt + U[0] * inv12), Fy = -(d[1] * Tt + U[1] * inv12), Fz = -(d[2] * Tt + U[2] * inv12);
-  frc[tp] = make_float4(Fx, Fy, Fz, Vs[0] * inv12);
-  const int tr = pair_rev[p];
-  if (tr >= A.nb_off[j] && tr < A.nb_off[j + 1]) frc[tr] = make_float4(-Fx, -Fy, -Fz, Vs[1] * inv12);
-  else atomicOr(A.flags, kFlagOverflow);
+  const R Fx = -(d[0] * Tt + U[0] * inv12), Fy = -(d[1] * Tt + U[1] * inv12), Fz = -(d[2] * Tt + U[2] * inv12);
+  frc[tp] = RT::make(Fx, Fy, Fz, Vs[0] * inv12);
+  frc[tr] = RT::make(-Fx, -Fy, -Fz, Vs[1] * inv12);
 }
 
-template <int S, int NL>
-__global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const float4* __restrict__ frc) {
+template <int PREC, int S, int NL>
+__global__ void __launch_bounds__(256) k_gather_rforce(PassArgs A,
+                                                       const typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc) {
+  using R = typename Traits<PREC>::R;
+  using Acc = typename RelaxAcc<PREC>::T;
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
   const int lane = (int)(tid % NL);
   const bool active = i < A.n;
-  AccFF g[3], gsig;
+  Acc g[3], gsig;
 #pragma unroll
   for (int c = 0; c < 3; ++c) g[c].zero();
   gsig.zero();
@@ -1478,11 +1629,12 @@ __global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const float4
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
 #pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
-      const float4 f = __ldg(&frc[t]);
-      g[0].add(f.x);
-      g[1].add(f.y);
-      g[2].add(f.z);
-      gsig.add(f.w);
+      R f[4];
+      Rec4<R>::load(&frc[t], f);
+      g[0].add(f[0]);
+      g[1].add(f[1]);
+      g[2].add(f[2]);
+      gsig.add(f[3]);
     }
   }
   if (NL > 1) {
@@ -1491,31 +1643,580 @@ __global__ void __launch_bounds__(256) k_gather32_force(PassArgs A, const float4
     gsig.team_reduce(NL);
   }
   // Per-site tail: team lanes 0-2 the force components, lane 3 the width
-  // derivative with its thermal term, so the float -> double conversions
-  // issue once per warp.  After the butterfly every team lane holds the
-  // whole sum (a lane's own rounding order: fixed, so runs repeat exactly).
+  // derivative with its thermal term, so the conversions and the FP64 division
+  // issue once per warp.  After the butterfly every team lane holds the whole
+  // sum (a lane's own rounding order: fixed, so runs repeat exactly).
   static_assert(NL >= 4, "one team lane per output");
   if (!active || lane > 3) return;
   const int64_t n = A.n;
-  float hi = g[0].hi, lo = g[0].lo;
-  if (lane == 1) {
-    hi = g[1].hi;
-    lo = g[1].lo;
-  } else if (lane == 2) {
-    hi = g[2].hi;
-    lo = g[2].lo;
-  } else if (lane == 3) {
-    const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)A.sigma[i];
-    hi = (gsig.hi - th) + gsig.lo;
-    lo = 0.f;
+  double v;
+  if constexpr (PREC == 0) {
+    v = lane == 0 ? g[0].get() : lane == 1 ? g[1].get() : lane == 2 ? g[2].get()
+                  : gsig.get() - 3.0 * kKB * A.T[i] / A.sigma[i];
+  } else {
+    float2 h = g[0].get_pair();
+    if (lane == 1) h = g[1].get_pair();
+    else if (lane == 2) h = g[2].get_pair();
+    else if (lane == 3) {
+      // FP32 modes: the thermal term in FP32 (no FP64 division)
+      const float2 gp = gsig.get_pair();
+      const float th = 3.0f * (float)kKB * (float)A.T[i] / (float)A.sigma[i];
+      h = make_float2((gp.x - th) + gp.y, 0.f);
+    }
+    v = (double)h.x + (double)h.y;
   }
-  const double v = (double)hi + (double)lo;
   if (lane < 3) {
     if (A.gq) A.gq[lane * n + i] = v;
   } else if (A.gs) {
     A.gs[i] = v;
   }
   if (!isfinite(v)) atomicOr(A.flags, kFlagNonfinite);
+}
+
+// ---------------------------------------------------------------- exact embedding average
+// App. B.2 (before Eq. F_taylor): the third-degree rule of App. A applied to the
+// many-body function F_k(rho_i^k), rho_i^k = sum_{j in J_i} sum_l x_jl f_kl(r_ij),
+// over the N_i sites of site i's rule: i and its neighbours J_i closer than
+// r_cut at the mean positions.  N_q = 3 N_i, M_i = 2 N_q nodes of weight 1/M_i,
+// each moving one site s by +-sigma_s sqrt(N_q) along one axis.  The pair terms
+// come from the ordinary passes with the embedding switched off; these two
+// passes add the embedding terms.
+//  k_emb_nodes (per site i): N_i, rho_bar_i (rule members at the mean), the six
+//    densities at the nodes that move i, then over the members j the six nodes
+//    that move j (rho = rho_bar - x_j f(r_bar) + x_j f(r_node)): <F_k> and the
+//    sum of F_k' over all M_i nodes.
+//  k_emb_grad (per site m, a gather): the derivatives of sum_i x_ik <F_k(rho_i^k)>
+//    w.r.t. q_m, sigma_m and x_m from m's own rule and from the rule of every
+//    member j of J_m (m is a member of J_j): in j's rule only the nodes that
+//    move j (densities stored by the first pass) or m (recomputed) change r_jm;
+//    every other node leaves r_jm at its mean and contributes F' summed as
+//    the stored total minus those twelve.
+template <typename R>
+struct EmbPrec {
+  static constexpr int P = 0;
+};
+template <>
+struct EmbPrec<float> {
+  static constexpr int P = 1;
+};
+
+// density term f_kl(r) and its derivative
+template <typename R>
+__device__ __forceinline__ void f_val(const DevPot& P, int v, R r, R Sw, R dS, R& f, R& df) {
+  const R e = rad_raw(P.f[v], r);
+  f = e * Sw;
+  df = e * (dS - rad_lam(P.f[v], r) * Sw);
+}
+
+// F_k(rho) = -E_k sqrt(rho) and F_k'(rho)
+__device__ __forceinline__ void embed_F(double E, double rho, double& F, double& dF) {
+  const double sq = sqrt(rho);
+  F = -E * sq;
+  dF = -E / (2.0 * sq);
+}
+__device__ __forceinline__ void embed_F(double E, float rho, double& F, double& dF) {
+  const float is = rsqrt_approx(rho);
+  F = (double)(-(float)E * rho * is);
+  dF = (double)(-0.5f * (float)E * is);
+}
+
+template <int S, int NL, typename R>
+__global__ void __launch_bounds__(256) k_emb_nodes(DevPot P, DevGrid g0, PassArgs A, EmbArgs E) {
+  constexpr int PR = EmbPrec<R>::P;
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = i < A.n;
+  const R rc2 = (R)(P.rc * P.rc);
+  const R rmin2 = (R)(kRMin * kRMin);
+  int bad = 0;
+  SiteData<PR, S> si;
+  DevGrid gs = g0;
+  int beg = 0, end = 0;
+  if (active) {
+    gs = site_grid(g0, A.batch, i);
+    load_site(A, i, si);
+    beg = A.nb_off[i];
+    end = A.nb_off[i + 1];
+  }
+  // members of the rule
+  int cnt = 0;
+  for (int t = beg + lane; t < end; t += NL) {
+    const uint32_t ent = __ldg(&A.nb_ent[t]);
+    SiteData<PR, S> sj;
+    load_site(A, ent & kIdxMask, sj);
+    R d[3];
+    separation(gs, si, sj, ent >> kCodeShift, d);
+    cnt += (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < rc2;
+  }
+  for (int o = NL >> 1; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  const int N = cnt + 1;
+  const R hs = sqrt((R)(3 * N));
+  const R hi = active ? si.sig * hs : (R)0;
+  // densities at the mean and at the six nodes that move i
+  double rb[S], ro[S][6];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    rb[k] = 0.0;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) ro[k][v] = 0.0;
+  }
+  for (int t = beg + lane; t < end; t += NL) {
+    const uint32_t ent = __ldg(&A.nb_ent[t]);
+    SiteData<PR, S> sj;
+    load_site(A, ent & kIdxMask, sj);
+    R d[3];
+    separation(gs, si, sj, ent >> kCodeShift, d);
+    const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(D2 < rc2)) continue;
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+    bad |= D2 < rmin2;
+#pragma unroll
+    for (int k = 0; k < S; ++k)
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        const int v = P.f_of[k][l];
+        if (v < 0) continue;
+        R f, df;
+        f_val(P, v, r, Sw, dS, f, df);
+        rb[k] += (double)(sj.x[l] * f);
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        const R h = pm == 0 ? hi : -hi;  // node: q_i + h e_a, so d_a -> d_a - h
+        const R r2 = D2 - (R)2 * h * d[a] + h * h;
+        bad |= r2 < rmin2;
+        R rn, rinvn, Swn, dSn;
+        r_from_r2(r2, rn, rinvn);
+        sw(P, rn, Swn, dSn);
+#pragma unroll
+        for (int k = 0; k < S; ++k)
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            const int v = P.f_of[k][l];
+            if (v < 0) continue;
+            R f, df;
+            f_val(P, v, rn, Swn, dSn, f, df);
+            ro[k][2 * a + pm] += (double)(sj.x[l] * f);
+          }
+      }
+  }
+  for (int o = NL >> 1; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      rb[k] += __shfl_xor_sync(0xffffffffu, rb[k], o);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) ro[k][v] += __shfl_xor_sync(0xffffffffu, ro[k][v], o);
+    }
+  }
+  // the nodes that move a member j: rho = rho_bar - x_j f(r_bar) + x_j f(r_node)
+  double Fs[S], Ts[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) Fs[k] = Ts[k] = 0.0;
+  double xi[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) xi[k] = active ? A.x[k * A.n + i] : 0.0;
+  for (int t = beg + lane; t < end; t += NL) {
+    const uint32_t ent = __ldg(&A.nb_ent[t]);
+    SiteData<PR, S> sj;
+    load_site(A, ent & kIdxMask, sj);
+    R d[3];
+    separation(gs, si, sj, ent >> kCodeShift, d);
+    const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(D2 < rc2)) continue;
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+    double base[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      base[k] = rb[k];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        const int v = P.f_of[k][l];
+        if (v < 0) continue;
+        R f, df;
+        f_val(P, v, r, Sw, dS, f, df);
+        base[k] -= (double)(sj.x[l] * f);
+      }
+    }
+    const R hj = sj.sig * hs;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        const R h = pm == 0 ? hj : -hj;  // node: q_j + h e_a
+        const R r2 = D2 + (R)2 * h * d[a] + h * h;
+        bad |= r2 < rmin2;
+        R rn, rinvn, Swn, dSn;
+        r_from_r2(r2, rn, rinvn);
+        sw(P, rn, Swn, dSn);
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+          if (P.E[k] == 0.0) continue;
+          double rho = base[k];
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            const int v = P.f_of[k][l];
+            if (v < 0) continue;
+            R f, df;
+            f_val(P, v, rn, Swn, dSn, f, df);
+            rho += (double)(sj.x[l] * f);
+          }
+          if (rho > kRhoMin) {
+            double F, dF;
+            embed_F(P.E[k], (R)rho, F, dF);
+            Fs[k] += F;
+            Ts[k] += dF;
+          } else if (xi[k] > 0.0) {
+            bad = 1;
+          }
+        }
+      }
+  }
+  for (int o = NL >> 1; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      Fs[k] += __shfl_xor_sync(0xffffffffu, Fs[k], o);
+      Ts[k] += __shfl_xor_sync(0xffffffffu, Ts[k], o);
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (!active || lane != 0) return;
+  const int64_t n = A.n;
+  const double invM = 1.0 / (6.0 * N);
+  double eV = 0.0;
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    double F = Fs[k], T = Ts[k];
+    if (P.E[k] != 0.0) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        if (ro[k][v] > kRhoMin) {
+          double Fo, dFo;
+          embed_F(P.E[k], (R)ro[k][v], Fo, dFo);
+          F += Fo;
+          T += dFo;
+        } else if (xi[k] > 0.0) {
+          bad = 1;
+        }
+      }
+    }
+    E.rhob[k * n + i] = rb[k];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) E.rown[(6 * k + v) * n + i] = ro[k][v];
+    E.fsum[k * n + i] = T;
+    E.emb[k * n + i] = F * invM;
+    eV += xi[k] * F * invM;
+  }
+  E.nrule[i] = N;
+  if (A.site_E) A.site_E[i] += eV;
+  if (bad) atomicOr(A.flags, kFlagGeometry);
+}
+
+template <int S, int NL, typename R>
+__global__ void __launch_bounds__(256) k_emb_grad(DevPot P, DevGrid g0, PassArgs A, EmbArgs E) {
+  constexpr int PR = EmbPrec<R>::P;
+  if (A.ctrl != nullptr && A.ctrl->halted) return;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t m = tid / NL;
+  const int lane = (int)(tid % NL);
+  const bool active = m < A.n;
+  const int64_t n = A.n;
+  const R rc2 = (R)(P.rc * P.rc);
+  SiteData<PR, S> sm;
+  DevGrid gs = g0;
+  int beg = 0, end = 0, Nm = 1;
+  double xm[S], rbm[S], wown[S][6];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    xm[k] = rbm[k] = 0.0;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) wown[k][v] = 0.0;
+  }
+  if (active) {
+    gs = site_grid(g0, A.batch, m);
+    load_site(A, m, sm);
+    beg = A.nb_off[m];
+    end = A.nb_off[m + 1];
+    Nm = E.nrule[m];
+    const double invM = 1.0 / (6.0 * Nm);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      xm[k] = A.x[k * n + m];
+      rbm[k] = E.rhob[k * n + m];
+      if (P.E[k] == 0.0) continue;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const double ro = E.rown[(6 * k + v) * n + m];
+        double F = 0.0, dF = 0.0;
+        if (ro > kRhoMin) embed_F(P.E[k], (R)ro, F, dF);
+        wown[k][v] = xm[k] * dF * invM;  // weight of the node in d/dq
+      }
+    }
+  }
+  const R hsm = sqrt((R)(3 * Nm));
+  const R hm = active ? sm.sig * hsm : (R)0;
+  const double invMm = 1.0 / (6.0 * Nm);
+  // static density gradient G_m^k = sum_{j in J_m} sum_l x_jl f_kl'(r) d / r
+  double G[S][3];
+#pragma unroll
+  for (int k = 0; k < S; ++k) G[k][0] = G[k][1] = G[k][2] = 0.0;
+  for (int t = beg + lane; t < end; t += NL) {
+    const uint32_t ent = __ldg(&A.nb_ent[t]);
+    SiteData<PR, S> sj;
+    load_site(A, ent & kIdxMask, sj);
+    R d[3];
+    separation(gs, sm, sj, ent >> kCodeShift, d);
+    const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(D2 < rc2)) continue;
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      R s = (R)0;
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        const int v = P.f_of[k][l];
+        if (v < 0) continue;
+        R f, df;
+        f_val(P, v, r, Sw, dS, f, df);
+        s += sj.x[l] * df;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) G[k][c] += (double)(s * d[c] * rinv);
+    }
+  }
+  for (int o = NL >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < S; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) G[k][c] += __shfl_xor_sync(0xffffffffu, G[k][c], o);
+  double g[3] = {0.0, 0.0, 0.0}, gsig = 0.0, mu[S], wsum[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) mu[k] = wsum[k] = 0.0;
+  for (int t = beg + lane; t < end; t += NL) {
+    const uint32_t ent = __ldg(&A.nb_ent[t]);
+    const int64_t j = ent & kIdxMask;
+    SiteData<PR, S> sj;
+    load_site(A, j, sj);
+    R d[3];  // q_j - q_m
+    separation(gs, sm, sj, ent >> kCodeShift, d);
+    const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(D2 < rc2)) continue;
+    R r, rinv, Sw, dS;
+    r_from_r2(D2, r, rinv);
+    sw(P, r, Sw, dS);
+    // f_kl(r_bar), f_kl'(r_bar) for every species pair
+    R fb[S][S], dfb[S][S];
+#pragma unroll
+    for (int k = 0; k < S; ++k)
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        const int v = P.f_of[k][l];
+        fb[k][l] = dfb[k][l] = (R)0;
+        if (v >= 0) f_val(P, v, r, Sw, dS, fb[k][l], dfb[k][l]);
+      }
+    // (1) m's rule, the nodes that move m: q_m + h e_a, so d_a -> d_a - h
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        const R h = pm == 0 ? hm : -hm;
+        R v3[3] = {d[0], d[1], d[2]};
+        v3[a] -= h;
+        const R r2 = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+        R rn, rinvn, Swn, dSn;
+        r_from_r2(r2, rn, rinvn);
+        sw(P, rn, Swn, dSn);
+        double w = 0.0;  // sum_k w_own sum_l x_jl f_kl'(r_node) / r_node
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+          R s = (R)0;
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            const int v = P.f_of[k][l];
+            if (v < 0) continue;
+            R f, df;
+            f_val(P, v, rn, Swn, dSn, f, df);
+            s += sj.x[l] * df;
+          }
+          w += wown[k][2 * a + pm] * (double)(s * rinvn);
+        }
+        // d rho / d q_m = -sum x f' v / r;  d/dsigma_m along a: times +-sqrt(N_q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c] -= w * (double)v3[c];
+        gsig -= w * (double)v3[a] * (double)(pm == 0 ? hsm : -hsm);
+      }
+    // (2) m's rule, the nodes that move j: q_j + h e_a, h = sigma_j sqrt(3 N_m)
+    {
+      const R hj = sj.sig * hsm;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int pm = 0; pm < 2; ++pm) {
+          const R h = pm == 0 ? hj : -hj;
+          R v3[3] = {d[0], d[1], d[2]};
+          v3[a] += h;
+          const R r2 = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+          R rn, rinvn, Swn, dSn;
+          r_from_r2(r2, rn, rinvn);
+          sw(P, rn, Swn, dSn);
+#pragma unroll
+          for (int k = 0; k < S; ++k) {
+            if (P.E[k] == 0.0) continue;
+            double rho = rbm[k];
+            R sn = (R)0, sb = (R)0;
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+              const int v = P.f_of[k][l];
+              if (v < 0) continue;
+              R f, df;
+              f_val(P, v, rn, Swn, dSn, f, df);
+              rho += (double)(sj.x[l] * (f - fb[k][l]));
+              sn += sj.x[l] * df;
+              sb += sj.x[l] * dfb[k][l];
+            }
+            double F = 0.0, dF = 0.0;
+            if (rho > kRhoMin) embed_F(P.E[k], (R)rho, F, dF);
+            const double w = xm[k] * dF * invMm;
+            wsum[k] += w;  // times -G_m^k after the row
+            // + x_j f'(r_bar) d / r_bar - x_j f'(r_node) v / r_node
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g[c] += w * (double)(sb * d[c] * rinv - sn * v3[c] * rinvn);
+          }
+        }
+    }
+    // j's rule (m is a member): its data from the first pass
+    const int Nj = E.nrule[j];
+    const R hsj = sqrt((R)(3 * Nj));
+    const double invMj = 1.0 / (6.0 * Nj);
+    double xj[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) xj[k] = A.x[k * n + j];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      if (P.E[k] == 0.0 || xj[k] == 0.0) continue;
+      double used = 0.0;  // F' of the twelve nodes handled here
+      // (3) the nodes that move j: q_j + h e_a; from m's side the separation
+      // q_m - q_j(node) = -(d + h e_a), so r from d_a + h
+      const R hjj = sj.sig * hsj;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int pm = 0; pm < 2; ++pm) {
+          const R h = pm == 0 ? hjj : -hjj;
+          R v3[3] = {-d[0], -d[1], -d[2]};  // q_m - q_j at the node
+          v3[a] -= h;
+          const R r2 = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+          R rn, rinvn, Swn, dSn;
+          r_from_r2(r2, rn, rinvn);
+          sw(P, rn, Swn, dSn);
+          const double ro = E.rown[(6 * k + 2 * a + pm) * n + j];
+          double F = 0.0, dF = 0.0;
+          if (ro > kRhoMin) embed_F(P.E[k], (R)ro, F, dF);
+          used += dF;
+          const double w = xj[k] * dF * invMj;
+          R sn = (R)0;
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            const int v = P.f_of[k][l];
+            if (v < 0) continue;
+            R f, df;
+            f_val(P, v, rn, Swn, dSn, f, df);
+            sn += (R)xm[l] * df;
+            mu[l] += w * (double)f;
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) g[c] += w * (double)(sn * v3[c] * rinvn);
+        }
+      // (4) the nodes that move m in j's rule: q_m + h e_a, h = sigma_m sqrt(3 N_j)
+      const double rbj = E.rhob[k * n + j];
+      const R hmj = sm.sig * hsj;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int pm = 0; pm < 2; ++pm) {
+          const R h = pm == 0 ? hmj : -hmj;
+          R v3[3] = {-d[0], -d[1], -d[2]};
+          v3[a] += h;
+          const R r2 = v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2];
+          R rn, rinvn, Swn, dSn;
+          r_from_r2(r2, rn, rinvn);
+          sw(P, rn, Swn, dSn);
+          double rho = rbj;
+          R sn = (R)0;
+          R fn[S];
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            const int v = P.f_of[k][l];
+            fn[l] = (R)0;
+            if (v < 0) continue;
+            R f, df;
+            f_val(P, v, rn, Swn, dSn, f, df);
+            fn[l] = f;
+            rho += xm[l] * (double)(f - fb[k][l]);
+            sn += (R)xm[l] * df;
+          }
+          double F = 0.0, dF = 0.0;
+          if (rho > kRhoMin) embed_F(P.E[k], (R)rho, F, dF);
+          used += dF;
+          const double w = xj[k] * dF * invMj;
+#pragma unroll
+          for (int l = 0; l < S; ++l) mu[l] += w * (double)fn[l];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) g[c] += w * (double)(sn * v3[c] * rinvn);
+          gsig += w * (double)(sn * v3[a] * rinvn) * (double)(pm == 0 ? hsj : -hsj);
+        }
+      // (5) every other node of j's rule: r_jm at its mean
+      const double w = xj[k] * (E.fsum[k * n + j] - used) * invMj;
+      R sb = (R)0;
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        sb += (R)xm[l] * dfb[k][l];
+        mu[l] += w * (double)fb[k][l];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[c] -= w * (double)(sb * d[c] * rinv);
+    }
+  }
+  for (int o = NL >> 1; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] += __shfl_xor_sync(0xffffffffu, g[c], o);
+    gsig += __shfl_xor_sync(0xffffffffu, gsig, o);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      mu[k] += __shfl_xor_sync(0xffffffffu, mu[k], o);
+      wsum[k] += __shfl_xor_sync(0xffffffffu, wsum[k], o);
+    }
+  }
+  if (!active || lane != 0) return;
+#pragma unroll
+  for (int k = 0; k < S; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] -= wsum[k] * G[k][c];
+  bool finite = isfinite(g[0]) && isfinite(g[1]) && isfinite(g[2]) && isfinite(gsig);
+  if (A.gq) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.gq[c * n + m] += g[c];
+  }
+  if (A.gs) A.gs[m] += gsig;
+  if (A.mu_ex || A.mu) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const double v = mu[k] + E.emb[k * n + m];
+      finite = finite && isfinite(v);
+      if (A.mu_ex) A.mu_ex[k * n + m] += v;
+      if (A.mu) A.mu[k * n + m] += v;
+    }
+  }
+  if (!finite) atomicOr(A.flags, kFlagNonfinite);
 }
 
 // ---------------------------------------------------------------- K7: pack
@@ -1752,98 +2453,175 @@ cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, d
 
 int pair_record_len(const DevPot& P) { return (2 * P.n_f + P.n_phi + 3) & ~3; }
 
-cudaError_t launch_pair_ff(const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i, const int* pair_t,
-                           int64_t npair, float2* buf, cudaStream_t s) {
-  if (npair == 0) return cudaSuccess;
+namespace {
+template <typename R>
+cudaError_t pair_geo_t(const DevPot& P, const DevGrid& g, const PassArgs& A, const int4* pair_rec, int64_t npair,
+                       void* buf, cudaStream_t s) {
   const int C = pair_record_len(P);
   const unsigned blocks = (unsigned)((npair + 127) / 128);
+  using T = typename GeoRec<R>::T;
   switch (P.S) {
-    case 1: k_pair_ff<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, buf, C); break;
-    case 2: k_pair_ff<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, npair, buf, C); break;
+    case 1: k_pair_geo<1, R><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
+    case 2: k_pair_geo<2, R><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
+}  // namespace
+
+cudaError_t launch_pair_geo(int precision, const DevPot& P, const DevGrid& g, const PassArgs& A,
+                            const int4* pair_rec, int64_t npair, void* buf, cudaStream_t s) {
+  if (npair == 0) return cudaSuccess;
+  if (precision == 0) return pair_geo_t<double>(P, g, A, pair_rec, npair, buf, s);
+  if (P.lj) return cudaErrorInvalidValue;  // Lennard-Jones terms: FP64 passes only
+  return pair_geo_t<ff>(P, g, A, pair_rec, npair, buf, s);
+}
 
 namespace {
-template <int S, int NL>
-cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf, int C,
+template <int S, int NL, typename R, typename Acc>
+cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const int* pid, const void* buf, int C,
                           int64_t npair, cudaStream_t s) {
   const int threads = A.tpb > 0 ? A.tpb : 256;
   const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
-  if (mu) k_pair_mu<S, NL><<<blocks, threads, 0, s>>>(P, A, pid, buf, C, npair);
-  else k_pair_density<S, NL><<<blocks, threads, 0, s>>>(P, A, pid, buf, C, npair);
+  using T = typename GeoRec<R>::T;
+  if (mu) k_pair_mu<S, NL, R, Acc><<<blocks, threads, 0, s>>>(P, A, pid, (const T*)buf, C, npair);
+  else k_pair_density<S, NL, R, Acc><<<blocks, threads, 0, s>>>(P, A, pid, (const T*)buf, C, npair);
   return cudaGetLastError();
 }
-template <int S>
-cudaError_t pair_gather_s(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
+template <int S, int NL>
+cudaError_t pair_gather_p(int precision, bool mu, const DevPot& P, const PassArgs& A, const int* pid, const void* buf,
                           int C, int64_t npair, cudaStream_t s) {
+  switch (precision) {
+    case 0: return pair_gather_t<S, NL, double, AccD>(mu, P, A, pid, buf, C, npair, s);
+    case 1: return pair_gather_t<S, NL, ff, AccD>(mu, P, A, pid, buf, C, npair, s);
+    case 2: return pair_gather_t<S, NL, ff, AccF2>(mu, P, A, pid, buf, C, npair, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int S>
+cudaError_t pair_gather_s(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid,
+                          const void* buf, int C, int64_t npair, cudaStream_t s) {
   switch (nl) {
-    case 4: return pair_gather_t<S, 4>(mu, P, A, pid, buf, C, npair, s);
-    case 8: return pair_gather_t<S, 8>(mu, P, A, pid, buf, C, npair, s);
-    case 16: return pair_gather_t<S, 16>(mu, P, A, pid, buf, C, npair, s);
+    case 4: return pair_gather_p<S, 4>(precision, mu, P, A, pid, buf, C, npair, s);
+    case 8: return pair_gather_p<S, 8>(precision, mu, P, A, pid, buf, C, npair, s);
+    case 16: return pair_gather_p<S, 16>(precision, mu, P, A, pid, buf, C, npair, s);
     default: return cudaErrorInvalidValue;
   }
 }
 }  // namespace
 
-cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
-                               int64_t npair, cudaStream_t s) {
+cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid,
+                               const void* buf, int64_t npair, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   const int C = pair_record_len(P);
   switch (P.S) {
-    case 1: return pair_gather_s<1>(mu, nl, P, A, pid, buf, C, npair, s);
-    case 2: return pair_gather_s<2>(mu, nl, P, A, pid, buf, C, npair, s);
+    case 1: return pair_gather_s<1>(precision, mu, nl, P, A, pid, buf, C, npair, s);
+    case 2: return pair_gather_s<2>(precision, mu, nl, P, A, pid, buf, C, npair, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 namespace {
-template <int S, int NL>
-cudaError_t relax32_gather_t(bool force, const DevPot& P, const PassArgs& A, const float4* dens, const float4* frc,
-                             cudaStream_t s) {
+template <int PREC, int S, int NL>
+cudaError_t relax_gather_t(bool force, const DevPot& P, const PassArgs& A, const void* dens, const void* frc,
+                           cudaStream_t s) {
+  using T = typename Rec4<typename Traits<PREC>::R>::T;
   const int threads = A.tpb > 0 ? A.tpb : 256;
   const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
-  if (force) k_gather32_force<S, NL><<<blocks, threads, 0, s>>>(A, frc);
-  else k_gather32_density<S, NL><<<blocks, threads, 0, s>>>(P, A, dens);
+  if (force) k_gather_rforce<PREC, S, NL><<<blocks, threads, 0, s>>>(A, (const T*)frc);
+  else k_gather_rdensity<PREC, S, NL><<<blocks, threads, 0, s>>>(P, A, (const T*)dens);
   return cudaGetLastError();
 }
-template <int S>
-cudaError_t relax32_gather_s(bool force, int nl, const DevPot& P, const PassArgs& A, const float4* dens,
-                             const float4* frc, cudaStream_t s) {
+template <int PREC, int S>
+cudaError_t relax_gather_s(bool force, int nl, const DevPot& P, const PassArgs& A, const void* dens, const void* frc,
+                           cudaStream_t s) {
   switch (nl) {
-    case 4: return relax32_gather_t<S, 4>(force, P, A, dens, frc, s);
-    case 8: return relax32_gather_t<S, 8>(force, P, A, dens, frc, s);
-    case 16: return relax32_gather_t<S, 16>(force, P, A, dens, frc, s);
+    case 4: return relax_gather_t<PREC, S, 4>(force, P, A, dens, frc, s);
+    case 8: return relax_gather_t<PREC, S, 8>(force, P, A, dens, frc, s);
+    case 16: return relax_gather_t<PREC, S, 16>(force, P, A, dens, frc, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int PREC>
+cudaError_t relax_gather_p(bool force, int nl, const DevPot& P, const PassArgs& A, const void* dens, const void* frc,
+                           cudaStream_t s) {
+  if (P.S == 1) return relax_gather_s<PREC, 1>(force, nl, P, A, dens, frc, s);
+  return relax_gather_s<PREC, 2>(force, nl, P, A, dens, frc, s);
+}
+template <int PREC>
+cudaError_t relax_pair_p(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int4* pair_rec,
+                         int64_t npair, void* dens, void* frc, cudaStream_t s) {
+  using T = typename Rec4<typename Traits<PREC>::R>::T;
+  const unsigned blocks = (unsigned)((npair + 127) / 128);
+  if (force) {
+    if (P.S == 1) k_pair_rforce<PREC, 1, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
+    else if (P.tab == 1) k_pair_rforce<PREC, 2, 1><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
+    else k_pair_rforce<PREC, 2, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
+  } else {
+    if (P.S == 1) k_pair_rdensity<PREC, 1, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
+    else if (P.tab == 1) k_pair_rdensity<PREC, 2, 1><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
+    else k_pair_rdensity<PREC, 2, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+namespace {
+template <int S, int NL, typename R>
+cudaError_t emb_t(bool second, const DevPot& P, const DevGrid& g, const PassArgs& A, const EmbArgs& E,
+                  cudaStream_t s) {
+  const int threads = A.tpb > 0 ? A.tpb : 256;
+  const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
+  if (second) k_emb_grad<S, NL, R><<<blocks, threads, 0, s>>>(P, g, A, E);
+  else k_emb_nodes<S, NL, R><<<blocks, threads, 0, s>>>(P, g, A, E);
+  return cudaGetLastError();
+}
+template <int S, typename R>
+cudaError_t emb_nl(bool second, int nl, const DevPot& P, const DevGrid& g, const PassArgs& A, const EmbArgs& E,
+                   cudaStream_t s) {
+  switch (nl) {
+    case 4: return emb_t<S, 4, R>(second, P, g, A, E, s);
+    case 8: return emb_t<S, 8, R>(second, P, g, A, E, s);
+    case 16: return emb_t<S, 16, R>(second, P, g, A, E, s);
     default: return cudaErrorInvalidValue;
   }
 }
 }  // namespace
 
-bool relax32_pairs_supported(const DevPot& P) { return P.S <= 2 && P.n_f <= 2; }
-
-cudaError_t launch_relax32_pair(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i,
-                                const int* pair_t, const int* pair_rev, int64_t npair, float4* dens, float4* frc,
-                                cudaStream_t s) {
-  if (A.n == 0 || npair == 0) return cudaSuccess;
-  if (!relax32_pairs_supported(P)) return cudaErrorInvalidValue;
-  const unsigned blocks = (unsigned)((npair + 127) / 128);
-  if (force) {
-    if (P.S == 1) k_pair32_force<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, frc);
-    else k_pair32_force<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, frc);
-  } else {
-    if (P.S == 1) k_pair32_density<1><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, dens);
-    else k_pair32_density<2><<<blocks, 128, 0, s>>>(P, g, A, pair_i, pair_t, pair_rev, npair, dens);
-  }
-  return cudaGetLastError();
+cudaError_t launch_emb_exact(bool second, bool fp64, int nl, const DevPot& P, const DevGrid& g, const PassArgs& A,
+                             const EmbArgs& E, cudaStream_t s) {
+  if (A.n == 0) return cudaSuccess;
+  if (P.S == 1) return fp64 ? emb_nl<1, double>(second, nl, P, g, A, E, s) : emb_nl<1, float>(second, nl, P, g, A, E, s);
+  if (P.S == 2) return fp64 ? emb_nl<2, double>(second, nl, P, g, A, E, s) : emb_nl<2, float>(second, nl, P, g, A, E, s);
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const float4* dens,
-                                  const float4* frc, cudaStream_t s) {
+bool pair_kernels_supported(const DevPot& P) { return P.S <= 2 && P.n_f <= 2; }
+
+size_t relax_record_bytes(int precision) { return precision == 0 ? sizeof(Dbl4) : sizeof(float4); }
+
+cudaError_t launch_relax_pair(int precision, bool force, const DevPot& P, const DevGrid& g, const PassArgs& A,
+                              const int4* pair_rec, int64_t npair, void* dens, void* frc, cudaStream_t s) {
+  if (A.n == 0 || npair == 0) return cudaSuccess;
+  if (!pair_kernels_supported(P)) return cudaErrorInvalidValue;
+  switch (precision) {
+    case 0: return relax_pair_p<0>(force, P, g, A, pair_rec, npair, dens, frc, s);
+    case 1: return relax_pair_p<1>(force, P, g, A, pair_rec, npair, dens, frc, s);
+    case 2: return relax_pair_p<2>(force, P, g, A, pair_rec, npair, dens, frc, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_relax_gather(int precision, bool force, int nl, const DevPot& P, const PassArgs& A,
+                                const void* dens, const void* frc, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
-  if (!relax32_pairs_supported(P)) return cudaErrorInvalidValue;
-  if (P.S == 1) return relax32_gather_s<1>(force, nl, P, A, dens, frc, s);
-  return relax32_gather_s<2>(force, nl, P, A, dens, frc, s);
+  if (!pair_kernels_supported(P)) return cudaErrorInvalidValue;
+  switch (precision) {
+    case 0: return relax_gather_p<0>(force, nl, P, A, dens, frc, s);
+    case 1: return relax_gather_p<1>(force, nl, P, A, dens, frc, s);
+    case 2: return relax_gather_p<2>(force, nl, P, A, dens, frc, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace mxe

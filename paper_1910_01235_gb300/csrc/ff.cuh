@@ -106,7 +106,9 @@ struct FFExpTable {
 };
 
 // exp(x) for |x| <~ 80 (inputs of the radial terms are far smaller).
-__device__ __forceinline__ ff ff_exp(ff x, const FFExpTable& T) {
+// tab(j) returns 2^(j/32) as a float pair.
+template <typename Tab>
+__device__ __forceinline__ ff ff_exp_t(ff x, const Tab& tab) {
   // ln2/32 = c1 + c2 + c3: c1 has 12 significant bits, so n * c1 is exact for
   // |n| < 2^12 (|x| < 88); c2 and c3 are the next float-sized pieces.
   const float kInvLn2x32 = 46.16624069213867f;           // 32 / ln 2
@@ -131,10 +133,25 @@ __device__ __forceinline__ ff ff_exp(ff x, const FFExpTable& T) {
   r2.lo *= 0.5f;
   ff p = ff_add_f(r2, tail) + r;
   p = ff_add_f(p, 1.0f);
-  const ff t = ff{T.hi[j], T.lo[j]};
+  const ff t = tab(j);
   p = p * t;
   const float sc = ldexpf(1.0f, m);
   return ff{p.hi * sc, p.lo * sc};
+}
+
+// with the table in constant memory (uniform indices are broadcast, distinct
+// ones are served one after another)
+__device__ __forceinline__ ff ff_exp(ff x, const FFExpTable& T) {
+  return ff_exp_t(x, [&](int j) { return ff{T.hi[j], T.lo[j]}; });
+}
+
+// with the table copied to shared memory as 32 (hi, lo) pairs: the 32 entries
+// fall in distinct banks, so lanes with different indices read in one pass
+__device__ __forceinline__ ff ff_exp(ff x, const float2* T) {
+  return ff_exp_t(x, [&](int j) {
+    const float2 v = T[j];
+    return ff{v.x, v.y};
+  });
 }
 
 }  // namespace mxe

@@ -55,9 +55,31 @@ struct DevPot {
   int8_t phi_of[kMaxS][kMaxS];   // species pair -> distinct phi term (-1: zero)
   int8_t f_of[kMaxS][kMaxS];     // species pair -> distinct f term (-1: zero)
   double E[kMaxS];
+  int tab;                       // 1: the binary alloy pattern below, 0: general tables
   double rs, rc, inv_w;          // switch start, cutoff, 1/(rc - rs)
   float rs_f, rc_f, inv_w_f, dS_scale_f;
   ff rs_ff, inv_w_ff, dS_scale_ff;
+};
+
+// Species-pair tables known at compile time.  Pattern 1 is the usual binary
+// EAM alloy: two like pair terms and one cross term, numbered in the order
+// the distinct terms are found (phi_of = {{0, 1}, {1, 2}}), and a density
+// that depends only on the neighbour's species (f_of[k][l] = l); the kernels
+// specialised for it fold every table lookup and run no loop over absent
+// terms.
+template <int TAB>
+struct Tables {
+  static __device__ __forceinline__ int phi(const DevPot& P, int k, int l) { return P.phi_of[k][l]; }
+  static __device__ __forceinline__ int f(const DevPot& P, int k, int l) { return P.f_of[k][l]; }
+  static __device__ __forceinline__ int n_phi(const DevPot& P) { return P.n_phi; }
+  static __device__ __forceinline__ int n_f(const DevPot& P) { return P.n_f; }
+};
+template <>
+struct Tables<1> {
+  static __device__ __forceinline__ constexpr int phi(const DevPot&, int k, int l) { return k + l; }
+  static __device__ __forceinline__ constexpr int f(const DevPot&, int, int l) { return l; }
+  static __device__ __forceinline__ constexpr int n_phi(const DevPot&) { return 3; }
+  static __device__ __forceinline__ constexpr int n_f(const DevPot&) { return 2; }
 };
 
 // Box / cell grid for positions and image codes.
@@ -129,6 +151,8 @@ cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, con
                                int* cell_slot, int* cell_count, int* abs_cell, float4* qf, cudaStream_t s);
 cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slot, const int* cell_start,
                               int* cell_sites, cudaStream_t s);
+// each cell's sites in increasing index
+cudaError_t launch_cell_sort(int64_t ncell, const int* cell_start, int* cell_sites, cudaStream_t s);
 cudaError_t launch_nbr_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
                              const DevGrid& g, const Batch& B, const int* cell_of, const int* cell_start, const int* cell_sites,
                              double rl2, double rb2, float band, int* nb_cnt, int* bd_cnt, int* max_row,
@@ -154,13 +178,15 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
                              int* flags, cudaStream_t s);
 // unordered-pair index of a symmetric list: first_gt[i] = first entry of row i
 // with j > i, cnt[i] = entries from there to the row's end; after a scan of
-// cnt into pair_off: pair p = (pair_i[p], entry pair_t[p]), and pid[t] = the
-// pair of every entry t (kFlagOverflow if the list is not symmetric)
+// cnt into pair_off: pair p has the record pair_rec[p] = (i, entry of j in row
+// i with its image code, that entry's index, the index of the reverse entry),
+// and pid[t] = the pair of every entry t (kFlagOverflow if the list is not
+// symmetric)
 cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* first_gt, int* cnt,
                               cudaStream_t s);
 cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
-                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pair_rev, int* pid,
-                             int* flags, cudaStream_t s);
+                             const int* pair_off, int64_t npair, int4* pair_rec, int* pid, int* flags,
+                             cudaStream_t s);
 // fill without a count pass: rows at a fixed stride (the previous build's
 // longest row plus a margin), counts and the longest row; then the scan of the
 // counts and the compaction into the CSR (a longer row: count + fill instead)
@@ -197,6 +223,7 @@ struct PassArgs {
   const int* nb_off;
   const uint32_t* nb_ent;
   int64_t n;
+  int64_t n_ent;    // neighbour entries of the list (bound of every entry index)
   // pass-1 outputs / pass-2 inputs
   double* rho_bar;
   double* rho_avg;
@@ -223,23 +250,42 @@ cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid
 enum { kGradAll = 0, kGradForce = 1, kGradMu = 2, kGradForceNoE = 3 };
 cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                             cudaStream_t s);
-// half-list float-float passes: records of pair_record_len(P) float pairs per
-// unordered pair, then the density (mu = false) or chemical-potential gather
+// half-list accurate passes: records of pair_record_len(P) values per
+// unordered pair (float pairs: float-float node arithmetic of the FP32 modes;
+// doubles: FP64 contexts), then the density (mu = false) or
+// chemical-potential gather (per-site sums in float-float for MXE_FP32_FF,
+// FP64 otherwise)
 int pair_record_len(const DevPot& P);
-cudaError_t launch_pair_ff(const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i, const int* pair_t,
-                           int64_t npair, float2* buf, cudaStream_t s);
-cudaError_t launch_pair_gather(bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid, const float2* buf,
-                               int64_t npair, cudaStream_t s);
-// half-list FP32 relaxation passes (FP32 node math, float-float sums): the
-// pair kernel writes each pair's record to both of its entries (pair_t[p],
-// pair_rev[p]); the gather then reads its own row: density (force = false:
-// a, b packed into ab32) or forces (dF/dq, dF/dsigma); dens, frc: [entries]
-bool relax32_pairs_supported(const DevPot& P);
-cudaError_t launch_relax32_pair(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int* pair_i,
-                                const int* pair_t, const int* pair_rev, int64_t npair, float4* dens, float4* frc,
-                                cudaStream_t s);
-cudaError_t launch_relax32_gather(bool force, int nl, const DevPot& P, const PassArgs& A, const float4* dens,
-                                  const float4* frc, cudaStream_t s);
+cudaError_t launch_pair_geo(int precision, const DevPot& P, const DevGrid& g, const PassArgs& A,
+                            const int4* pair_rec, int64_t npair, void* buf, cudaStream_t s);
+cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid,
+                               const void* buf, int64_t npair, cudaStream_t s);
+// half-list relaxation passes (FP32 node math in the FP32 modes, FP64 in FP64
+// contexts): the pair kernel writes each pair's record to both of its entries
+// (pair_t[p], pair_rev[p]); the gather then reads its own row: density (force
+// = false: a, b packed into ab32, or the FP64 arrays a, b) or forces (dF/dq,
+// dF/dsigma); dens, frc: [entries] records of relax_record_bytes(precision)
+bool pair_kernels_supported(const DevPot& P);
+size_t relax_record_bytes(int precision);
+cudaError_t launch_relax_pair(int precision, bool force, const DevPot& P, const DevGrid& g, const PassArgs& A,
+                              const int4* pair_rec, int64_t npair, void* dens, void* frc, cudaStream_t s);
+cudaError_t launch_relax_gather(int precision, bool force, int nl, const DevPot& P, const PassArgs& A,
+                                const void* dens, const void* frc, cudaStream_t s);
+// exact phase average of the embedding term (App. B.2: App. A's rule over a
+// site and its neighbours inside r_cut): per-site rule data of the first pass,
+// read by the second
+struct EmbArgs {
+  double* rhob;   // [S][n] density at the mean positions (rule members only)
+  double* rown;   // [6 S][n] density at the six nodes that move the site itself
+  double* fsum;   // [S][n] sum over all M nodes of F_k'(rho(node))
+  double* emb;    // [S][n] <F_k(rho)>
+  int* nrule;     // [n] sites of the rule (the site and its members)
+};
+// node arithmetic in FP64 (fp64 = true) or FP32 (per-site sums in FP64); the
+// second pass adds dF/dq, dF/dsigma and dE_V/dx into A.gq, A.gs, A.mu_ex (and
+// A.mu), the first adds the embedding energy into A.site_E
+cudaError_t launch_emb_exact(bool second, bool fp64, int nl, const DevPot& P, const DevGrid& g, const PassArgs& A,
+                             const EmbArgs& E, cudaStream_t s);
 cudaError_t launch_pack_ab(const double* a, const double* b, int64_t n, int S, float4* ab32, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* site_E, int64_t n, double* partials, double* F4, cudaStream_t s);
 // batches: F4 [nsys][4], one block per system in a fixed order

@@ -10,8 +10,10 @@
 // (the band bounds the position rounding, the image choice and the rounding
 // of |d|^2; outside it the FP32 and FP64 decisions agree).
 // One warp handles one site: lanes sweep the candidates of the distinct
-// neighbouring cells, accepted entries are compacted into shared memory with
-// ballots and placed in j order by rank counting.  Each entry stores j in the
+// neighbouring cells and accepted entries are compacted with ballots.  The
+// cell-staged kernels visit a block's candidates in increasing j (sorted once
+// per block), so the compaction is the row in j order; the warp-per-site
+// fallback places entries in j order by rank counting.  Each entry stores j in the
 // low 27 bits and the periodic image code (cell offset in {-1,0,1}^3) above it,
 // which the FP32 kernels use to rebuild d from cell-relative positions.
 #include <cuda_runtime.h>
@@ -53,6 +55,24 @@ __global__ void k_cell_place(int64_t n, const int* __restrict__ cell_of, const i
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   cell_sites[cell_start[cell_of[i]] + cell_slot[i]] = (int)i;
+}
+
+// Each cell's sites in increasing index (the slots above come from atomics):
+// one thread per cell, insertion sort of its ~15 sites.  The cell-staged fill
+// then stages every stencil cell as a sorted run.
+__global__ void k_cell_sort(int64_t ncell, const int* __restrict__ cell_start, int* __restrict__ cell_sites) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int b = cell_start[c], e = cell_start[c + 1];
+  for (int u = b + 1; u < e; ++u) {
+    const int v = cell_sites[u];
+    int w = u - 1;
+    while (w >= b && cell_sites[w] > v) {
+      cell_sites[w + 1] = cell_sites[w];
+      --w;
+    }
+    cell_sites[w + 1] = v;
+  }
 }
 
 // The distinct cells of the 3x3x3 stencil around `cell` (duplicates removed
@@ -444,6 +464,41 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
   }
 }
 
+// The staged candidates in increasing j: the 27 stencil cells are staged as
+// runs that are each sorted (k_cell_sort), and every candidate j is distinct
+// (each site sits in one cell, the stencil's cells are distinct), so a
+// candidate's place in the merged order is the sum over the runs of the
+// number of keys below it (a binary search per run).  Each candidate is
+// copied to its place in (cq2, cj2).
+__device__ __forceinline__ int run_lower_bound(const int* cj, int beg, int end, uint32_t key) {
+  while (beg < end) {
+    const int mid = (beg + end) >> 1;
+    if (((uint32_t)cj[mid] & kIdxMask) < key) beg = mid + 1;
+    else end = mid;
+  }
+  return beg;
+}
+
+__device__ __forceinline__ void merge_stage(const float4* cq, const int* cj, int ncand, const int* s_off,
+                                            float4* cq2, int* cj2) {
+  for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
+    const uint32_t key = (uint32_t)cj[t] & kIdxMask;
+    int rank = 0;
+#pragma unroll 1
+    for (int r = 0; r < 27; ++r) {
+      const int b = s_off[r], e = min(s_off[r + 1], ncand);
+      if (b >= e) continue;
+      rank += run_lower_bound(cj, b, e, key) - b;
+    }
+    cq2[rank] = cq[t];
+    cj2[rank] = cj[t];
+  }
+  __syncthreads();
+}
+
+// The candidates are visited in increasing j (merge_stage), so the ballot
+// compaction of the accepted ones is the row in j order: entries go straight
+// to nb_ent (bonds to bd_idx), each ballot round a coalesced run.
 // DIRECT: no count pass before: row i goes to nb_ent[i * max_row ...] (max_row
 // = the stride, from the previous build) with its counts in nb_cnt / bd_cnt
 // and the longest row in *row_max; a row longer than the stride is cut and
@@ -461,6 +516,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   __shared__ float s_sh[27 * 3];
   float4* cq = reinterpret_cast<float4*>(smem);
   int* cj = reinterpret_cast<int*>(cq + cand_cap);
+  float4* cq2 = reinterpret_cast<float4*>(cj + cand_cap + ((4 - (cand_cap & 3)) & 3));  // 16-byte aligned
+  int* cj2 = reinterpret_cast<int*>(cq2 + cand_cap);
   const int cell = blockIdx.x;
   const int hbeg = cell_start[cell], hend = cell_start[cell + 1];
   if (hbeg == hend) return;
@@ -469,19 +526,18 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   const int base = B.nsys ? B.cell_base[sys] : 0;
   const CellStage cs =
       stage_cell(cell, base, g, n, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, s_sh, cand_cap, flags);
+  merge_stage(cq, cj, cs.ncand, s_off, cq2, cj2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // per warp: the row's entries and its sort keys (j << 1 | bond), 16-byte aligned
-  const int stride = (max_row + 3) & ~3;
-  uint32_t* rows = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(cj + cand_cap) + 15) & ~uintptr_t(15));
-  uint32_t* buf = rows + (size_t)warp * stride;
-  uint32_t* kw = rows + (size_t)(nwarps + warp) * stride;
   const float rl2f = (float)rl2, rb2f = (float)rb2;
+  const unsigned below = (1u << lane) - 1u;
   for (int h = hbeg + warp; h < hend; h += nwarps) {
     const int64_t i = cell_sites[h];
     const double qi[3] = {q[i], q[n + i], q[2 * n + i]};
     const float4 qfi = cs.fast ? qf[n + i] : qf[i];
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
+    const int64_t off = DIRECT ? i * (int64_t)max_row : (int64_t)nb_off[i];
+    const int64_t boff = DIRECT ? i * (int64_t)max_row : (int64_t)bd_off[i];
     int m = 0, nbond = 0;
     for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
       const int t = t0 + lane;
@@ -489,10 +545,10 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
       uint32_t ent = 0;
       int j = 0;
       if (t < cs.ncand) {
-        ent = (uint32_t)cj[t];
+        ent = (uint32_t)cj2[t];
         j = (int)(ent & kIdxMask);
-        r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
-                    : test_cand(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
+        r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq2[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
+                    : test_cand(i, qi, qfi, j, cq2[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
       }
       if (r.in && !cs.fast) {
         int code = 0;
@@ -505,41 +561,23 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
         ent = (uint32_t)j | ((uint32_t)code << kCodeShift);
       }
       const unsigned msk = __ballot_sync(0xffffffffu, r.in);
+      const unsigned bmsk = __ballot_sync(0xffffffffu, r.bond);
       if (r.in) {
-        const int pos = m + __popc(msk & ((1u << lane) - 1u));
-        if (pos < max_row) {
-          buf[pos] = ent;
-          kw[pos] = ((uint32_t)j << 1) | (r.bond ? 1u : 0u);
-        }
+        const int pos = m + __popc(msk & below);
+        if (pos < max_row) nb_ent[off + pos] = ent;
+      }
+      if (r.bond) {
+        const int bpos = nbond + __popc(bmsk & below);
+        if (bpos < max_row) bd_idx[boff + bpos] = j;
       }
       m += __popc(msk);
-      if (DIRECT) nbond += __popc(__ballot_sync(0xffffffffu, r.bond));
+      nbond += __popc(bmsk);
     }
     if (DIRECT && lane == 0) {
       nb_cnt[i] = m;
       bd_cnt[i] = nbond;
       atomicMax(row_max, m);
     }
-    if (m > max_row) m = max_row;  // count + fill: cannot happen (max_row is the counted maximum)
-    const int m4 = (m + 3) >> 2;
-    for (int e = m + lane; e < 4 * m4; e += 32) kw[e] = 0xFFFFFFFFu;  // pads rank after every key
-    __syncwarp();
-    const int64_t off = DIRECT ? i * (int64_t)max_row : (int64_t)nb_off[i];
-    const int64_t boff = DIRECT ? i * (int64_t)max_row : (int64_t)bd_off[i];
-    const uint4* k4 = reinterpret_cast<const uint4*>(kw);
-    for (int e = lane; e < m; e += 32) {
-      const uint32_t ke = kw[e] & ~1u;  // j << 1: keys of smaller j are below it
-      int rank = 0, brank = 0;
-      for (int f = 0; f < m4; ++f) {
-        const uint4 v = k4[f];
-        const uint32_t l0 = v.x < ke, l1 = v.y < ke, l2 = v.z < ke, l3 = v.w < ke;
-        rank += (int)(l0 + l1 + l2 + l3);
-        brank += (int)((l0 & v.x) + (l1 & v.y) + (l2 & v.z) + (l3 & v.w));
-      }
-      nb_ent[off + rank] = buf[e];
-      if (kw[e] & 1u) bd_idx[boff + brank] = (int)(ke >> 1);
-    }
-    __syncwarp();
   }
 }
 
@@ -686,10 +724,12 @@ __global__ void k_pair_count(const int* __restrict__ nb_off, const uint32_t* __r
   cnt[i] = end - fg;
 }
 
+// Pair records rec[p] = (i, entry of j in row i with its image code, that
+// entry's index, the index of the reverse entry i in row j): the owner branch
+// writes the first three words, the row of the other end the fourth.
 __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __restrict__ nb_ent, int64_t n,
                             const int* __restrict__ first_gt, const int* __restrict__ pair_off, int64_t npair,
-                            int* __restrict__ pair_i, int* __restrict__ pair_t, int* __restrict__ pair_rev,
-                            int* __restrict__ pid, int* __restrict__ flags) {
+                            int* __restrict__ rec, int* __restrict__ pid, int* __restrict__ flags) {
   // one warp per row, lanes over its entries
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -698,12 +738,14 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
   const int64_t i = w;
   const int beg = nb_off[i], end = nb_off[i + 1], fg = first_gt[i];
   for (int t = beg + lane; t < end; t += 32) {
-    const int64_t j = nb_ent[t] & kIdxMask;
+    const uint32_t e = nb_ent[t];
+    const int64_t j = e & kIdxMask;
     if (t >= fg) {
       const int p = pair_off[i] + (t - fg);
       if (p < npair) {
-        pair_i[p] = (int)i;
-        pair_t[p] = t;
+        rec[4 * (int64_t)p] = (int)i;
+        rec[4 * (int64_t)p + 1] = (int)e;
+        rec[4 * (int64_t)p + 2] = t;
         pid[t] = p;
       } else {
         pid[t] = 0;
@@ -715,7 +757,7 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
       const int t2 = first_above(nb_ent, jb, je, (uint32_t)i) - 1;
       if (t2 >= jb && (nb_ent[t2] & kIdxMask) == (uint32_t)i && pair_off[j] + (t2 - jb) < npair) {
         pid[t] = pair_off[j] + (t2 - jb);
-        pair_rev[pair_off[j] + (t2 - jb)] = t;
+        rec[4 * (int64_t)(pair_off[j] + (t2 - jb)) + 3] = t;
       } else {
         pid[t] = 0;
         atomicOr(flags, kFlagOverflow);
@@ -723,7 +765,6 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
     }
   }
 }
-
 
 // rows written at a fixed stride -> CSR (one warp per row)
 __global__ void k_row_compact(const uint32_t* __restrict__ rows, const int* __restrict__ brows, int stride, int64_t n,
@@ -751,6 +792,12 @@ cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slo
                               int* cell_sites, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_cell_place<<<grid_for(n, 256), 256, 0, s>>>(n, cell_of, cell_slot, cell_start, cell_sites);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_sort(int64_t ncell, const int* cell_start, int* cell_sites, cudaStream_t s) {
+  if (ncell == 0) return cudaSuccess;
+  k_cell_sort<<<grid_for(ncell, 128), 128, 0, s>>>(ncell, cell_start, cell_sites);
   return cudaGetLastError();
 }
 
@@ -792,8 +839,9 @@ cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const Batch& B, con
 }
 
 size_t cell_stage_bytes(int cand_cap, int max_row, bool fill) {
+  (void)max_row;  // rows are written straight to global memory
   size_t b = (size_t)cand_cap * (sizeof(float4) + sizeof(int));
-  if (fill) b += 16 + (size_t)(kCellThreads / 32) * 2 * (size_t)((max_row + 3) & ~3) * sizeof(uint32_t);
+  if (fill) b += 16 + (size_t)cand_cap * (sizeof(float4) + sizeof(int));  // the candidates in j order
   return b + 16;
 }
 
@@ -893,11 +941,11 @@ cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t
 }
 
 cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
-                             const int* pair_off, int64_t npair, int* pair_i, int* pair_t, int* pair_rev, int* pid,
-                             int* flags, cudaStream_t s) {
+                             const int* pair_off, int64_t npair, int4* pair_rec, int* pid, int* flags,
+                             cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_pair_fill<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, first_gt, pair_off, npair,
-                                                               pair_i, pair_t, pair_rev, pid, flags);
+                                                               (int*)pair_rec, pid, flags);
   return cudaGetLastError();
 }
 

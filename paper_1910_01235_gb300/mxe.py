@@ -68,7 +68,9 @@ EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy",
            "mxe_sync_status", "mxe_relax", "mxe_relax_info", "mxe_diffuse_step", "mxe_diffuse_step_async",
            "mxe_diffuse_step_noalloc", "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs",
            "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape",
-           "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad", "mxe_transport_step"]
+           "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad", "mxe_transport_step",
+           "mxe_set_embedding", "mxe_element_param_grad"]
+EMBED_TAYLOR, EMBED_EXACT = 0, 1
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
 
@@ -101,6 +103,8 @@ def lib():
             L.mxe_run_staggered.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.POINTER(C.c_int32)]
             L.mxe_autotune.argtypes = [p, p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
             L.mxe_set_pass_shape.argtypes = [p, C.c_int32, C.c_int32]
+            L.mxe_set_embedding.argtypes = [p, C.c_int32]
+            L.mxe_element_param_grad.argtypes = [p, p, p]
             i32p = C.POINTER(C.c_int32)
             L.mxe_potential_terms.argtypes = [p, i32p, i32p, p, p, p]
             L.mxe_tangent.argtypes = [p, p] + [p] * 10
@@ -187,6 +191,10 @@ def mxe_autotune(ctx, state):
 
 def mxe_set_pass_shape(ctx, lanes, threads):
     return lib().mxe_set_pass_shape(ctx, int(lanes), int(threads))
+
+
+def mxe_set_embedding(ctx, mode):
+    return lib().mxe_set_embedding(ctx, int(mode))
 
 
 def mxe_potential_terms(ctx):
@@ -477,6 +485,12 @@ class MxeSystem:
     def set_pass_shape(self, lanes, threads):
         self._check(mxe_set_pass_shape(self.ctx, lanes, threads), "mxe_set_pass_shape")
 
+    def set_embedding(self, mode):
+        """"taylor" (Eq. F_taylor_mxe, default) or "exact" (App. A's rule over
+        each site and its neighbours inside r_cut)."""
+        m = {"taylor": EMBED_TAYLOR, "exact": EMBED_EXACT}[mode] if isinstance(mode, str) else int(mode)
+        self._check(mxe_set_embedding(self.ctx, m), "mxe_set_embedding")
+
     # ---------------------------------------------------------- second order
     def potential_terms(self):
         st, nphi, nf, terms, phi_of, f_of = mxe_potential_terms(self.ctx)
@@ -528,51 +542,16 @@ class MxeSystem:
         return self.relax(ftol, max_iter, fire)
 
 
-def term_parameters(pot, phi_of, f_of, n_phi, n_f):
-    """(c, lambda) of each of the library's radial terms computed from the
-    potential tables: c = ln A + exponent, lambda = exponent / length scale;
-    a geometric-mean cross pair averages the two like-pair terms (the form in
-    which the library evaluates it)."""
-    T = n_phi + n_f
-    c = np.zeros(T)
-    lam = np.zeros(T)
-    seen = np.zeros(T, bool)
-    S = pot.n_species
-    for k in range(S):
-        for l in range(S):
-            u = phi_of[k, l]
-            if u >= 0 and not seen[u]:
-                if pot.cross_geomean and k != l:
-                    c[u] = 0.5 * (np.log(pot.phi_A[k, k]) + pot.phi_p[k, k] + np.log(pot.phi_A[l, l]) + pot.phi_p[l, l])
-                    lam[u] = 0.5 * (pot.phi_p[k, k] / pot.phi_r0[k, k] + pot.phi_p[l, l] / pot.phi_r0[l, l])
-                else:
-                    c[u] = np.log(pot.phi_A[k, l]) + pot.phi_p[k, l]
-                    lam[u] = pot.phi_p[k, l] / pot.phi_r0[k, l]
-                seen[u] = True
-            v = f_of[k, l]
-            if v >= 0 and not seen[v]:
-                c[v] = np.log(pot.f_xi[k, l]) + pot.f_q[k, l]
-                lam[v] = pot.f_q[k, l] / pot.f_r0[k, l]
-                seen[v] = True
-    return c, lam
-
-
-def chain_to_parameters(dterm, make_pot, theta, phi_of, f_of, n_phi, n_f, rel_step=1e-6):
-    """dL/dtheta from the per-term sensitivities dterm = [dL/dc (T), dL/dlambda
-    (T)]: the chain rule through the host map theta -> potential -> (c,
-    lambda), whose Jacobian is taken by central differences of that map
-    (a few logarithms and ratios; error ~1e-12 relative)."""
-    T = n_phi + n_f
-    theta = np.asarray(theta, float)
-    out = np.zeros(theta.size)
-    for m in range(theta.size):
-        h = rel_step * max(abs(theta[m]), 1.0)
-        tp, tm = theta.copy(), theta.copy()
-        tp[m] += h
-        tm[m] -= h
-        cp, lp = term_parameters(make_pot(tp), phi_of, f_of, n_phi, n_f)
-        cm, lm = term_parameters(make_pot(tm), phi_of, f_of, n_phi, n_f)
-        out[m] = dterm[:T] @ ((cp - cm) / (2 * h)) + dterm[T:2 * T] @ ((lp - lm) / (2 * h))
+def element_param_grad(pot, dterm):
+    """dL/d(A_e, p_e, q_e, r0_e) for each element e ([S, 4]) from the term
+    sensitivities dterm = [dL/dc (T), dL/dlambda (T)] (mxe_element_param_grad:
+    the closed-form chain rule, computed by the library)."""
+    P = make_potential(pot)
+    d = np.ascontiguousarray(dterm, dtype=np.float64)
+    out = np.zeros((pot.n_species, 4))
+    st = lib().mxe_element_param_grad(C.byref(P), d.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p))
+    if st != OK:
+        raise MxeError(st, "mxe_element_param_grad")
     return out
 
 

@@ -94,8 +94,7 @@ def test_parameter_gradient_against_oracle_differences():
     dterm = g.tangent()["dterm"].cpu().numpy()
     theta = W.theta_of(s.pot)
     base = s.pot
-    grad = M.chain_to_parameters(dterm[:2 * T], lambda th: W.binary_from_theta(th, base), theta, phi_of, f_of,
-                                 nphi, nf)
+    grad = M.element_param_grad(base, dterm[:2 * T]).reshape(-1)
     fd = np.zeros_like(theta)
     for m in range(theta.size):
         h = 1e-5 * abs(theta[m])
@@ -144,7 +143,7 @@ def test_mixed_parameter_state_derivatives_against_oracle_differences():
     dt_term = out["dterm"].cpu().numpy()[2 * T:]
     theta = W.theta_of(s.pot)
     base = s.pot
-    got = M.chain_to_parameters(dt_term, lambda th: W.binary_from_theta(th, base), theta, phi_of, f_of, nphi, nf)
+    got = M.element_param_grad(base, dt_term).reshape(-1)
     fd = np.zeros_like(theta)
     for m in range(theta.size):
         h = 1e-5 * abs(theta[m])
@@ -231,7 +230,7 @@ def test_unrolled_gradient_against_oracle_differences():
     np.testing.assert_allclose(g.x.cpu().numpy(), so.x, rtol=0, atol=1e-10)   # forward run
     theta = W.theta_of(s.pot)
     base = s.pot
-    grad = M.chain_to_parameters(dterm, lambda th: W.binary_from_theta(th, base), theta, phi_of, f_of, nphi, nf)
+    grad = M.element_param_grad(base, dterm).reshape(-1)
     for m in (W.THETA_NAMES.index("q_B"), W.THETA_NAMES.index("r0_A")):
         h = 3e-4 * abs(theta[m])
         vals = []
