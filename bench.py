@@ -184,23 +184,6 @@ def peak_fp64_ops(clock_mhz=2070.0):
     return 152 * 2 * clock_mhz * 1e6
 
 
-def ncu_counter(kernel, name, record="counters_binary_alloy_256k.json"):
-    """A per-launch counter of `kernel` from a committed ncu capture of this
-    workload, or None when the kernel sources changed since the capture."""
-    import hashlib
-    p = os.path.join(ROOT, "profiles", record)
-    if not os.path.exists(p):
-        return None
-    d = json.load(open(p))
-    h = hashlib.sha256()
-    for f in d["source_files"]:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    k = d["kernels"].get(kernel)
-    if k is None or h.hexdigest()[:16] != d["source_digest"] or name not in k:
-        return None
-    return k[name]
-
-
 def kernel_shares(kern):
     """Per kernel class: launches, total and mean device time, share of the step."""
     shares = {}
@@ -224,13 +207,15 @@ def roofline_of(shares, npairs, S, n_phi, n_f, with_traffic):
     fp64 = "64" in dom or dom.endswith("fp64") or dom.startswith("gradient_fp64") or dom.startswith("density_fp64")
     out = {"bound": "alu", "kernel": dom, "kernel_avg_ms": shares[dom]["avg_ms"], "share": shares[dom]["share"]}
     if fp64:
-        inst = ncu_counter(dom, "inst_fp64")
+        ops = ncu_counter(dom, "fp64_lane_ops")
         peak = peak_fp64_ops()
-        ach = inst / avg_s / 1e12 if inst else None
-        out.update({"achieved": ach, "peak": peak / 1e12, "unit": "T instructions/s (FP64 pipe)",
-                    "frac": ach / (peak / 1e12) if ach else None, "ops_per_launch": inst,
-                    "ops_basis": "FP64-pipe instructions of one launch (sm__inst_executed_pipe_fp64.sum, ncu)",
-                    "peak_note": "152 SMs x 2 FP64 instructions/cycle x 2070 MHz (nominal 1.25 TFLOP/s)"})
+        ach = ops / avg_s / 1e12 if ops else None
+        out.update({"achieved": ach, "peak": peak / 1e12, "unit": "T lane-ops/s (FP64 pipe)",
+                    "frac": ach / (peak / 1e12) if ach else None, "ops_per_launch": ops,
+                    "ops_basis": ("FP64-pipe operations of one launch: 32 x smsp__inst_executed_pipe_fp64.sum "
+                                  "from the committed ncu capture (the pipe's own count, FP64 exp, sqrt and "
+                                  "division included)"),
+                    "peak_note": "152 SMs x 2 FP64 lanes x 2070 MHz (nominal 1.25 TFLOP/s)"})
     else:
         opp = ops_per_pair(dom, n_phi, n_f, S)
         peak = peak_fp32_ops()
@@ -248,21 +233,42 @@ def roofline_of(shares, npairs, S, n_phi, n_f, with_traffic):
     return out
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture of this
-    workload, or None when the kernel sources changed since the capture."""
+COUNTERS = os.path.join(ROOT, "profiles", "counters_binary_alloy_256k.json")
+
+
+def kernel_source_digest(src):
+    """sha256 (first 16 hex digits) of one kernel's source text: the text of
+    src["file"] from the marker src["from"] to the marker src["to"]."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "traffic_binary_alloy_256k.json")
-    if not os.path.exists(p):
+    text = open(os.path.join(ROOT, src["file"])).read()
+    a = text.find(src["from"])
+    b = text.find(src["to"], a + 1) if a >= 0 else -1
+    if a < 0 or b < 0:
         return None
-    d = json.load(open(p))
-    h = hashlib.sha256()
-    for f in d["source_files"]:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    k = d["kernels"].get(kernel)
-    if k is None or h.hexdigest()[:16] != d["source_digest"]:
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+
+
+def ncu_record(kernel):
+    """Per-launch counters of `kernel` (timing class name) from the committed
+    ncu capture of the 256,000-site alloy, or None when the kernel's source
+    text changed since the capture."""
+    if not os.path.exists(COUNTERS):
         return None
-    return k["dram_read"] + k["dram_write"]
+    rec = json.load(open(COUNTERS))["kernels"].get(kernel)
+    if rec is None or kernel_source_digest(rec["source"]) != rec["source_digest"]:
+        return None
+    return rec
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    rec = ncu_record(kernel)
+    return None if rec is None else rec["dram_read"] + rec["dram_write"]
+
+
+def ncu_counter(kernel, name):
+    rec = ncu_record(kernel)
+    return None if rec is None else rec.get(name)
 
 
 def measured_peaks():
@@ -292,12 +298,14 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def set_shape(g):
-        """Pass shape: the autotuner's choice, or --pass-shape (lanes,threads)."""
+        """Pass shape: the autotuner's choice, or --pass-shape
+        (lanes,threads[,pair_threads]); returns (lanes, threads, pair_threads)."""
         if args.pass_shape:
-            lanes, threads = (int(v) for v in args.pass_shape.split(","))
-            g.set_pass_shape(lanes, threads)
-            return lanes, threads
-        return g.autotune()
+            v = [int(t) for t in args.pass_shape.split(",")]
+            g.set_pass_shape(v[0], v[1], v[2] if len(v) > 2 else None)
+        else:
+            g.autotune()
+        return g.pass_shape()
 
     def timed_arm(prec, steps, warmup, launches_out=None, kernel_events=False):
         stream = torch.cuda.Stream(dev)
@@ -449,6 +457,7 @@ def run_ours(args):
                    "evals_per_step": K + 2, "neighbor_pairs": npairs, "parallelism": f"replicas{world}",
                    "l2": "flushed between steps (256 MB write)", "precision": main_prec,
                    "pass_shape": {"lanes_per_site": shape[0], "threads_per_block": shape[1],
+                                  "pairs_per_block": shape[2],
                                   "chosen_by": "--pass-shape" if args.pass_shape else "autotuner"}},
         "diffusion_steps_per_s": world * 1e3 / ms,
         "kernels": shares,
@@ -512,10 +521,11 @@ def run_ensemble(args):
     g.build_neighbors()
     g.set_dt_scale(list(dts))
     if args.pass_shape:
-        lanes, threads = (int(v) for v in args.pass_shape.split(","))
-        g.set_pass_shape(lanes, threads)
+        v = [int(t) for t in args.pass_shape.split(",")]
+        g.set_pass_shape(v[0], v[1], v[2] if len(v) > 2 else None)
     else:
-        lanes, threads = g.autotune()
+        g.autotune()
+    lanes, threads, pair_threads = g.pass_shape()
     q0, s0, x0 = g.q.clone(), g.sigma.clone(), g.x.clone()
 
     def restore():
@@ -543,6 +553,7 @@ def run_ensemble(args):
         stream.synchronize()
         assert st == M.OK and done == steps_per_run, (st, done)
         times.append(e0.elapsed_time(e1))
+        launches, kernels_per_step = g.run_stats()
     clocks = sampler.stop()
     ms_run = float(np.median(times))
     ms_step = ms_run / steps_per_run
@@ -557,11 +568,14 @@ def run_ensemble(args):
         "data": "synthetic (seeded ensemble of FCC single-species lattices with vacancies)",
         "config": {"workload": "ensemble_512_systems", "systems": len(systems), "sites": n,
                    "fire_iters_per_step": K, "evals_per_step": K + 2, "steps_per_graph_run": steps_per_run,
-                   "pass_shape": {"lanes_per_site": lanes, "threads_per_block": threads},
+                   "pass_shape": {"lanes_per_site": lanes, "threads_per_block": threads,
+                                  "pairs_per_block": pair_threads},
                    "potential": "single species, variant with pair exponent 5 and density exponent 3",
                    "precision": prec,
                    "l2": "working set ~1 GB > L2, not flushed", "parallelism": f"replicas{world}"},
         "diffusion_steps_per_s": world * 1e3 / ms_step,
+        "graph_launches_per_run": launches, "kernels_per_step": kernels_per_step,
+        "gpu_launches": kernels_per_step * steps_per_run * len(times),
         "max_abs_dx": moved,
         "clocks": clocks,
     }
@@ -799,7 +813,8 @@ def main():
     ap.add_argument("--workload", default="binary",
                     choices=["binary", "ensemble", "unrolled_grad", "slab4m", "embedding"])
     ap.add_argument("--ensemble-steps", type=int, default=ENSEMBLE_STEPS)
-    ap.add_argument("--pass-shape", default="", help="lanes,threads of the passes (default: autotuned)")
+    ap.add_argument("--pass-shape", default="",
+                    help="lanes,threads[,pair_threads] of the passes (default: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

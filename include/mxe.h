@@ -288,12 +288,14 @@ MXE_API mxe_status mxe_diffuse_step_async(mxe_ctx *ctx, mxe_state *state, const 
  *      fire): exactly max_iter + 1 force evaluations are enqueued; a system
  *      that converges earlier stops moving.  Not converging within max_iter
  *      is not an error here (the next step starts from the last iterate).
- * The whole step is captured once in a CUDA graph on a private stream and
- * replayed on the context's stream, so a step costs one graph launch and no
- * host round trip; the graph is rebuilt when the state pointers, the step
- * parameters, the pass shape or the lists change.  When the skin criterion
- * fails, the graph stops itself; the host rebuilds the lists, finishes the
- * interrupted step and resumes.  *steps_done (host, optional) receives the
+ * The step is captured once in a CUDA graph (on a private stream) as the body
+ * of a while node, so one graph launch runs all the steps on the device, with
+ * no host round trip between them: after each step a one-thread kernel lets
+ * the loop go on while steps remain, no stop is pending and the body has run
+ * fewer than (steps left + 2) times.  The graph is rebuilt when the state
+ * pointers, the step parameters, the pass shape or the lists change.  When
+ * the skin criterion fails, the loop stops itself; the host rebuilds the
+ * lists, finishes the interrupted step and launches the loop again.  *steps_done (host, optional) receives the
  * completed steps.  On MXE_ERR_GEOMETRY / NONFINITE / X_RANGE the run stops
  * inside the failing step: steps before it are complete, and x is not
  * advanced by a step whose range check failed.  mxe_relax_info then
@@ -303,15 +305,24 @@ MXE_API mxe_status mxe_run_staggered(mxe_ctx *ctx, mxe_state *state, int32_t n_s
                                      double Qm, double ftol, int32_t max_iter, const mxe_fire_params *fire,
                                      int32_t *steps_done);
 
-/* Autotuner of the density and gradient passes: times every pass shape
- * (lanes per site 4, 8, 16 -- the neighbour chunk one site's row is split
- * into -- times 128 or 256 threads per block) on the given state over one
- * staggered step's worth of passes and keeps the fastest for this context.
- * Results do not depend on the shape beyond rounding order.  Requires a
- * neighbour list.  lanes_out / threads_out (host, optional) receive the
- * choice.  Syncs.  mxe_set_pass_shape sets a shape directly.                 */
+/* The last mxe_run_staggered: graph launches it made (one, plus one after
+ * each list rebuild) and the kernels of one captured step (the loop-control
+ * kernel included); host values, either pointer may be NULL.                */
+MXE_API mxe_status mxe_run_stats(mxe_ctx *ctx, int32_t *graph_launches, int32_t *kernels_per_step);
+
+/* Autotuner of the passes: times every pass shape -- lanes per site 4, 8, 16
+ * (the chunk of a site's neighbour row each lane takes) times 128 or 256
+ * threads per block of the per-site passes and gathers, times 64, 128 or 256
+ * unordered pairs per block of the pair kernels (contexts with a pair index)
+ * -- on the given state over one staggered step's worth of passes and keeps
+ * the fastest for this context.  Results do not depend on the shape beyond
+ * rounding order.  Requires a neighbour list.  lanes_out / threads_out (host,
+ * optional) receive the choice; mxe_get_pass_shape reads all three.  Syncs.
+ * mxe_set_pass_shape and mxe_set_pair_block set a shape directly.           */
 MXE_API mxe_status mxe_autotune(mxe_ctx *ctx, const mxe_state *state, int32_t *lanes_out, int32_t *threads_out);
 MXE_API mxe_status mxe_set_pass_shape(mxe_ctx *ctx, int32_t lanes, int32_t threads);
+MXE_API mxe_status mxe_set_pair_block(mxe_ctx *ctx, int32_t pair_threads);
+MXE_API mxe_status mxe_get_pass_shape(mxe_ctx *ctx, int32_t *lanes, int32_t *threads, int32_t *pair_threads);
 
 /* Phase average of the embedding term (App. B.2).
  *  MXE_EMBED_TAYLOR (default): the Taylor form Eq. F_taylor_mxe,
@@ -418,6 +429,19 @@ MXE_API mxe_status mxe_unrolled_grad(mxe_ctx *ctx, mxe_state *state, int32_t n_s
                                      double Qm, double ftol, int32_t max_iter, const mxe_fire_params *fire,
                                      int32_t checkpoint_every, const double *w_dev, double cg_tol, int32_t cg_max,
                                      double *dterm_host, double *dx0_dev, mxe_grad_info *info);
+
+/* As mxe_unrolled_grad for n_obj objectives L_o = sum_ik w_o,ik x_ik(n_steps)
+ * at once (w_dev: device [n_obj][S][n], e.g. the bins of a z-profile): one
+ * forward sweep, and one recomputation of each checkpoint segment's relaxed
+ * states, serve every objective; the reverse steps (Euler-step VJP, the CG
+ * solve on H_yy, the tangent pass) run per objective.  dterm_host: host
+ * [n_obj][2 T]; dx0_dev: device [n_obj][S][n] or NULL.  1 <= n_obj <= 4096.
+ * Same requirements and statuses as mxe_unrolled_grad.                       */
+MXE_API mxe_status mxe_unrolled_grad_multi(mxe_ctx *ctx, mxe_state *state, int32_t n_steps, double dt, double nu0,
+                                           double Qm, double ftol, int32_t max_iter, const mxe_fire_params *fire,
+                                           int32_t checkpoint_every, int32_t n_obj, const double *w_dev,
+                                           double cg_tol, int32_t cg_max, double *dterm_host, double *dx0_dev,
+                                           mxe_grad_info *info);
 
 /* Variants of the transport step (Sec. 3: Eq. Transport, Eq. MassTransport).
  *  host_species = -1: vacancy-mediated exchange, as mxe_diffuse_step.

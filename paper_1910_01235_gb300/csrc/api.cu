@@ -25,14 +25,14 @@ struct StepKey {
   int32_t max_iter;
   double dt0, alpha0;
   int64_t list_gen;
-  int32_t nl, tpb;
+  int32_t nl, tpb, pair_tpb;
 };
 
 inline bool same_key(const StepKey& a, const StepKey& b) {
   return a.q == b.q && a.sigma == b.sigma && a.x == b.x && a.T == b.T && a.sub == b.sub &&
          a.mobile_mask == b.mobile_mask && a.dt == b.dt && a.nu0 == b.nu0 && a.Qm == b.Qm &&
          a.max_iter == b.max_iter && a.dt0 == b.dt0 && a.alpha0 == b.alpha0 && a.list_gen == b.list_gen &&
-         a.nl == b.nl && a.tpb == b.tpb;
+         a.nl == b.nl && a.tpb == b.tpb && a.pair_tpb == b.pair_tpb;
 }
 
 struct mxe_ctx {
@@ -85,7 +85,7 @@ struct mxe_ctx {
   int *first_gt = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
   int4* pair_rec = nullptr;  // [pairs] (i, entry of j with its image code, entry index, reverse entry index)
   int* pid = nullptr;        // [entries] pair of every entry
-  double* pair_buf = nullptr;  // [pairs][pair_record_len] 8-byte values (float pairs or doubles)
+  double* pair_buf = nullptr;  // [entries][pair_record_len] 8-byte values (float pairs or doubles)
   void *ent_dens = nullptr, *ent_frc = nullptr;  // [entries] relaxation records (relax_record_bytes each)
   bool relax_records = false;  // allocate them (first relaxation of the context, then with every list growth)
   int64_t pair_cap = 0, n_upairs = 0;
@@ -130,13 +130,19 @@ struct mxe_ctx {
   SysFire* sf_h = nullptr;      // pinned copy after a relaxation
   double* dt_sys = nullptr;     // [nsys] Euler step multipliers
   Batch B{};
-  // pass shape: lanes per site and threads per block of the density/gradient passes
+  // pass shape: lanes per site and threads per block of the density/gradient
+  // passes and gathers, threads (pairs) per block of the pair kernels
   int tpb = 256;
+  int pair_tpb = 128;
   // captured staggered step
   int64_t list_gen = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t step_exec = nullptr;
+  cudaGraphExec_t step_exec = nullptr;  // the run's loop: a while node around one captured step
   StepKey step_key{};
+  int* loop_dev = nullptr;  // [3] device loop control (bodies run, step count to reach, cap)
+  int* loop_h = nullptr;    // pinned staging of loop_dev
+  int step_kernels = 0;     // kernel nodes of the captured step
+  int run_launches = 0;     // graph launches of the last staggered run
   // second-order passes (allocated on first use)
   double* tan_buf = nullptr;   // a, b, e values and tangents: 6 [S][n]
   double* th_buf = nullptr;    // per-site term sensitivities, values and tangents: 2 x [2 T][n]
@@ -337,6 +343,7 @@ mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
            d.f_of[0][1] == 1 && d.f_of[1][1] == 1)
               ? 1
               : 0;
+  d.cross_geo = (S == 2 && p.cross_geomean && !p.lj) ? 1 : 0;
   d.rs = p.r_switch;
   d.rc = p.r_cut;
   d.inv_w = 1.0 / (p.r_cut - p.r_switch);
@@ -389,6 +396,7 @@ void fill_pass(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
   A.check_skin = 0;
   A.batch = c->B;
   A.tpb = c->tpb;
+  A.pair_tpb = c->pair_tpb;
 }
 
 mxe_status ensure_cells(mxe_ctx* c, int64_t ncell) {
@@ -506,7 +514,6 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, B, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
   CK(TIMED("build_misc", launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st)));
   CK(TIMED("build_misc", launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st)));
-  CK(TIMED("build_misc", launch_cell_sort(ncell, c->cell_start, c->cell_sites, st)));
   // largest stencil candidate set: the cell-staged kernels need it in shared memory
   CK(cudaMemsetAsync(c->max_row, 0, 2 * sizeof(int), st));
   CK(TIMED("build_misc", launch_cand_max(ncell, g, B, c->cell_start, c->max_row + 1, st)));
@@ -576,7 +583,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     const int64_t cap = std::max<int64_t>(c->nb_cap, npairs);
     CK(dalloc(&c->pid, cap));
     CK(dalloc(&c->pair_rec, cap / 2 + 64));
-    CK(dalloc(&c->pair_buf, (cap / 2 + 64) * (int64_t)pair_record_len(c->dp)));
+    CK(dalloc(&c->pair_buf, cap * (int64_t)pair_record_len(c->dp)));  // one record per entry
     dfree(c->ent_dens);
     dfree(c->ent_frc);
     if (c->relax_records) {
@@ -723,9 +730,9 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
     CK(TIMED(prec == MXE_FP64 ? "pair_geo64" : "pair_ff",
              launch_pair_geo(prec, PP, c->grid, G, c->pair_rec, c->n_upairs, c->pair_buf, st)));
     CK(TIMED(accurate_gather_name(false, prec),
-             launch_pair_gather(prec, false, c->nl, PP, G, c->pid, c->pair_buf, c->n_upairs, st)));
+             launch_pair_gather(prec, false, c->nl, PP, G, c->pair_buf, st)));
     CK(TIMED(accurate_gather_name(true, prec),
-             launch_pair_gather(prec, true, c->nl, PP, G, c->pid, c->pair_buf, c->n_upairs, st)));
+             launch_pair_gather(prec, true, c->nl, PP, G, c->pair_buf, st)));
   }
   if (A.gq != nullptr || A.gs != nullptr) {
     PassArgs F = A;
@@ -977,10 +984,14 @@ mxe_status enqueue_staggered_step(mxe_ctx* c, mxe_state* s, const StepKey& k) {
   return MXE_OK;
 }
 
-// Capture one staggered step on a private stream (the caller's stream may be
-// the legacy default stream, which cannot be captured) and instantiate it;
-// kept while the key (state pointers, step parameters, list generation, pass
-// shape) is unchanged.
+// The staggered run as one graph: a while node whose body is one captured
+// staggered step followed by the loop-control kernel, so a launch runs the
+// steps on the device until the requested count is reached, a step stops for
+// a list rebuild or an error, or the body count hits its cap.  The step is
+// captured on a private stream (the caller's stream may be the legacy
+// default stream, which cannot be captured); the graph is kept while the key
+// (state pointers, step parameters, list generation, pass shape) is
+// unchanged.
 mxe_status ensure_step_graph(mxe_ctx* c, mxe_state* s, StepKey key) {
   key.list_gen = c->list_gen;
   if (c->step_exec && same_key(key, c->step_key)) return MXE_OK;
@@ -989,21 +1000,55 @@ mxe_status ensure_step_graph(mxe_ctx* c, mxe_state* s, StepKey key) {
     c->step_exec = nullptr;
   }
   if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  cudaStream_t user = c->stream;
-  const bool timing = c->timing;
-  c->stream = c->cap_stream;
-  c->timing = false;
-  mxe_status ms = MXE_OK;
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    ms = enqueue_staggered_step(c, s, key);
-    e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (!c->loop_dev) {
+    CK(dalloc(&c->loop_dev, 3));
+    CK(cudaMallocHost((void**)&c->loop_h, 3 * sizeof(int)));
   }
-  c->stream = user;
-  c->timing = timing;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  }
+  mxe_status ms = MXE_OK;
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t user = c->stream;
+    const bool timing = c->timing;
+    c->stream = c->cap_stream;
+    c->timing = false;
+    e = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      ms = enqueue_staggered_step(c, s, key);
+      if (ms == MXE_OK) e = launch_loop_cond(h, c->ctrl, c->loop_dev, c->cap_stream);
+      cudaGraph_t out = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &out);
+      if (e == cudaSuccess) e = e2;
+      // kernel nodes of one step (the loop-control kernel included)
+      size_t nn = 0;
+      if (e == cudaSuccess && cudaGraphGetNodes(body, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        int k = 0;
+        if (cudaGraphGetNodes(body, nodes.data(), &nn) == cudaSuccess)
+          for (size_t u = 0; u < nn; ++u) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[u], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+          }
+        c->step_kernels = k;
+      }
+    }
+    c->stream = user;
+    c->timing = timing;
+  }
   if (e == cudaSuccess && ms == MXE_OK) e = cudaGraphInstantiate(&c->step_exec, g, 0);
-  if (g) cudaGraphDestroy(g);
+  cudaGraphDestroy(g);
   if (ms != MXE_OK) return ms;
   if (e != cudaSuccess) {
     c->step_exec = nullptr;
@@ -1326,6 +1371,8 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  dfree(c->loop_dev);
+  if (c->loop_h) cudaFreeHost(c->loop_h);
   dfree(c->tan_buf);
   dfree(c->emb_buf);
   dfree(c->emb_nrule);
@@ -1587,11 +1634,15 @@ mxe_status mxe_flux_vjp(mxe_ctx* c, const mxe_state* s, const double* mu_ex_dev,
   return mxe_sync_status(c);
 }
 
-mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double dt, double nu0, double Qm,
-                             double ftol, int32_t max_iter, const mxe_fire_params* fire, int32_t every,
-                             const double* w_dev, double cg_tol, int32_t cg_max, double* dterm_host,
-                             double* dx0_dev, mxe_grad_info* info) {
+// The forward sweep and each checkpoint segment's recomputed relaxations are
+// shared by the n_obj objectives; the reverse steps (Euler-step VJP, CG on
+// H_yy, tangent pass) run per objective.
+mxe_status unrolled_grad_impl(mxe_ctx* c, mxe_state* s, int32_t n_steps, double dt, double nu0, double Qm,
+                              double ftol, int32_t max_iter, const mxe_fire_params* fire, int32_t every, int32_t n_obj,
+                              const double* w_dev, double cg_tol, int32_t cg_max, double* dterm_host,
+                              double* dx0_dev, mxe_grad_info* info) {
   if (info) std::memset(info, 0, sizeof(*info));
+  if (n_obj < 1 || n_obj > 4096) return MXE_ERR_ARG;
   if (!c || !state_ok(c, s) || n_steps < 0 || every < 1 || !w_dev || !dterm_host || !(cg_tol > 0.0) ||
       cg_max < 1 || !(dt >= 0.0) || !(nu0 >= 0.0) || !std::isfinite(Qm) || !(ftol >= 0.0) || max_iter < 0)
     return MXE_ERR_ARG;
@@ -1622,7 +1673,7 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
   double* seg = alloc((int64_t)every * ny);          // (q, sigma) recomputed inside a segment
   double* yT = alloc(ny);                            // final state
   double* mu = alloc(nx);
-  double* xbar = alloc(nx);
+  double* xbar = alloc((int64_t)n_obj * nx);  // one cotangent of x per objective
   double* xdir = alloc(nx);
   double* mubar = alloc(nx);
   double* rhs = alloc(ny);
@@ -1680,8 +1731,8 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
   }
   RUN(save_y(yT));
   // ---- reverse sweep
-  std::vector<double> acc(2 * T, 0.0), hth(4 * T, 0.0);
-  CK(copy_d2d(xbar, w_dev, sizeof(double) * nx, st));
+  std::vector<double> acc((size_t)n_obj * 2 * T, 0.0), hth(4 * T, 0.0);
+  CK(copy_d2d(xbar, w_dev, sizeof(double) * nx * n_obj, st));
   for (int c0 = ((n_steps - 1) / every) * every; n_steps > 0 && c0 >= 0; c0 -= every) {
     const int c1 = std::min(c0 + every, n_steps);
     // recompute the relaxed states of the segment from its checkpoint
@@ -1699,34 +1750,37 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
       CK(copy_d2d(s->x, X + (int64_t)t * nx, sizeof(double) * nx, st));
       RUN(build_lists(c, s, c->skin, c->r_bond));
       RUN(mu_pass());
-      // Euler step: xbar_t (direct part) and mubar from xbar_{t+1}
-      CK(launch_flux_vjp(s->x, s->T, mu, c->bd_off, c->bd_idx, n, (int)S, dt, nu0, Qm,
-                         c->nsys ? c->dt_sys : nullptr, c->nsys ? c->sys_of : nullptr, xbar, xdir, mubar, st));
-      // relaxed state as an implicit function of x: H lam = H_yx mubar
-      RUN(enqueue_tangent(c, s, nullptr, nullptr, mubar, nullptr, nullptr, nullptr, rhs, rhs + 3 * n, nullptr,
-                          nullptr));
-      int iters = 0;
-      double rel = 0.0;
-      RUN(cg_solve(c, s, rhs, lam, r, p, Hp, cg_tol, cg_max, iters, rel));
-      if (info) {
-        info->cg_iters_total += iters;
-        info->cg_iters_max = std::max(info->cg_iters_max, iters);
-        info->cg_resid_max = std::max(info->cg_resid_max, rel);
+      for (int o = 0; o < n_obj; ++o) {
+        double* xb = xbar + (int64_t)o * nx;
+        // Euler step: xbar_t (direct part) and mubar from xbar_{t+1}
+        CK(launch_flux_vjp(s->x, s->T, mu, c->bd_off, c->bd_idx, n, (int)S, dt, nu0, Qm,
+                           c->nsys ? c->dt_sys : nullptr, c->nsys ? c->sys_of : nullptr, xb, xdir, mubar, st));
+        // relaxed state as an implicit function of x: H lam = H_yx mubar
+        RUN(enqueue_tangent(c, s, nullptr, nullptr, mubar, nullptr, nullptr, nullptr, rhs, rhs + 3 * n, nullptr,
+                            nullptr));
+        int iters = 0;
+        double rel = 0.0;
+        RUN(cg_solve(c, s, rhs, lam, r, p, Hp, cg_tol, cg_max, iters, rel));
+        if (info) {
+          info->cg_iters_total += iters;
+          info->cg_iters_max = std::max(info->cg_iters_max, iters);
+          info->cg_resid_max = std::max(info->cg_resid_max, rel);
+        }
+        if (rel > cg_tol && iters >= cg_max) return MXE_ERR_NO_CONVERGE;
+        // xbar_t = xdir + H_xx mubar - H_xy lam; thetabar += H_tx mubar - H_ty lam
+        CK(launch_axpby(lam, lam, 0.0, -1.0, ny, st));
+        RUN(enqueue_tangent(c, s, lam, lam + 3 * n, mubar, nullptr, nullptr, nullptr, nullptr, nullptr, mut, th));
+        CK(launch_axpby(xdir, mut, 1.0, 1.0, nx, st));
+        CK(copy_d2d(xb, xdir, sizeof(double) * nx, st));
+        CK(cudaMemcpyAsync(hth.data(), th, sizeof(double) * 4 * T, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int u = 0; u < 2 * T; ++u) acc[(size_t)o * 2 * T + u] += hth[2 * T + u];
       }
-      if (rel > cg_tol && iters >= cg_max) return MXE_ERR_NO_CONVERGE;
-      // xbar_t = xdir + H_xx mubar - H_xy lam; thetabar += H_tx mubar - H_ty lam
-      CK(launch_axpby(lam, lam, 0.0, -1.0, ny, st));
-      RUN(enqueue_tangent(c, s, lam, lam + 3 * n, mubar, nullptr, nullptr, nullptr, nullptr, nullptr, mut, th));
-      CK(launch_axpby(xdir, mut, 1.0, 1.0, nx, st));
-      CK(copy_d2d(xbar, xdir, sizeof(double) * nx, st));
-      CK(cudaMemcpyAsync(hth.data(), th, sizeof(double) * 4 * T, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int u = 0; u < 2 * T; ++u) acc[u] += hth[2 * T + u];
       RUN(mxe_sync_status(c));
     }
   }
-  for (int u = 0; u < 2 * T; ++u) dterm_host[u] = acc[u];
-  if (dx0_dev) CK(copy_d2d(dx0_dev, xbar, sizeof(double) * nx, st));
+  for (size_t u = 0; u < (size_t)n_obj * 2 * T; ++u) dterm_host[u] = acc[u];
+  if (dx0_dev) CK(copy_d2d(dx0_dev, xbar, sizeof(double) * nx * n_obj, st));
   // leave the state at the end of the run
   RUN(load_y(yT));
   CK(copy_d2d(s->x, X + (int64_t)n_steps * nx, sizeof(double) * nx, st));
@@ -1734,6 +1788,22 @@ mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
 #undef RUN
   CK(cudaStreamSynchronize(st));
   return MXE_OK;
+}
+
+mxe_status mxe_unrolled_grad(mxe_ctx* c, mxe_state* s, int32_t n_steps, double dt, double nu0, double Qm,
+                             double ftol, int32_t max_iter, const mxe_fire_params* fire, int32_t every,
+                             const double* w_dev, double cg_tol, int32_t cg_max, double* dterm_host,
+                             double* dx0_dev, mxe_grad_info* info) {
+  return unrolled_grad_impl(c, s, n_steps, dt, nu0, Qm, ftol, max_iter, fire, every, 1, w_dev, cg_tol, cg_max,
+                            dterm_host, dx0_dev, info);
+}
+
+mxe_status mxe_unrolled_grad_multi(mxe_ctx* c, mxe_state* s, int32_t n_steps, double dt, double nu0, double Qm,
+                                   double ftol, int32_t max_iter, const mxe_fire_params* fire, int32_t every,
+                                   int32_t n_obj, const double* w_dev, double cg_tol, int32_t cg_max,
+                                   double* dterm_host, double* dx0_dev, mxe_grad_info* info) {
+  return unrolled_grad_impl(c, s, n_steps, dt, nu0, Qm, ftol, max_iter, fire, every, n_obj, w_dev, cg_tol, cg_max,
+                            dterm_host, dx0_dev, info);
 }
 
 mxe_status mxe_transport_step(mxe_ctx* c, mxe_state* s, const mxe_transport* opt, const double* mu_ex_dev,
@@ -1909,13 +1979,20 @@ mxe_status mxe_run_staggered(mxe_ctx* c, mxe_state* s, int32_t n_steps, double d
   init_ctrl(c, H, fp, ftol, max_iter);
   CK(cudaMemcpyAsync(c->ctrl, &H, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   const StepKey key{s->q, s->sigma, s->x, s->T, s->sublattice, s->mobile_mask, dt, nu0, Qm, max_iter,
-                    fp.dt0, fp.alpha0, 0, c->nl, c->tpb};
+                    fp.dt0, fp.alpha0, 0, c->nl, c->tpb, c->pair_tpb};
   mxe_status result = MXE_OK;
   int done = 0, stops = 0;
+  c->run_launches = 0;
   while (done < n_steps) {
     mxe_status ms = ensure_step_graph(c, s, key);
     if (ms != MXE_OK) return ms;
-    for (int k = done; k < n_steps; ++k) CK(cudaGraphLaunch(c->step_exec, st));
+    // one launch runs every remaining step on the device
+    c->loop_h[0] = 0;
+    c->loop_h[1] = n_steps;
+    c->loop_h[2] = n_steps - done + 2;
+    CK(cudaMemcpyAsync(c->loop_dev, c->loop_h, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(c->step_exec, st));
+    c->run_launches += 1;
     CK(cudaMemcpyAsync(&H, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     done = H.steps;
@@ -1981,31 +2058,35 @@ mxe_status mxe_autotune(mxe_ctx* c, const mxe_state* s, int32_t* lanes_out, int3
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   mxe_status result = MXE_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) result = MXE_ERR_CUDA;
-  const int lanes[3] = {4, 8, 16}, threads[2] = {128, 256};
-  int best_nl = c->nl, best_tpb = c->tpb;
+  const int lanes[3] = {4, 8, 16}, threads[2] = {128, 256}, pthreads[3] = {64, 128, 256};
+  int best_nl = c->nl, best_tpb = c->tpb, best_ptpb = c->pair_tpb;
   float best = INFINITY;
   for (int a = 0; a < 3 && result == MXE_OK; ++a)
-    for (int b = 0; b < 2 && result == MXE_OK; ++b) {
-      c->nl = lanes[a];
-      c->tpb = threads[b];
-      float total = 0.f;
-      for (int rep = 0; rep < 3 && result == MXE_OK; ++rep) {  // rep 0 warms up
-        if (cudaEventRecord(e0, st) != cudaSuccess) result = MXE_ERR_CUDA;
-        if (result == MXE_OK) result = enqueue_tune_work(c, s);
-        if (result == MXE_OK && cudaEventRecord(e1, st) != cudaSuccess) result = MXE_ERR_CUDA;
-        float ms = 0.f;
-        if (result == MXE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-          result = MXE_ERR_CUDA;
-        if (rep > 0) total += ms;
+    for (int b = 0; b < 2 && result == MXE_OK; ++b)
+      for (int pb = 0; pb < (has_pair_index(c) ? 3 : 1) && result == MXE_OK; ++pb) {
+        c->nl = lanes[a];
+        c->tpb = threads[b];
+        c->pair_tpb = has_pair_index(c) ? pthreads[pb] : 128;
+        float total = 0.f;
+        for (int rep = 0; rep < 3 && result == MXE_OK; ++rep) {  // rep 0 warms up
+          if (cudaEventRecord(e0, st) != cudaSuccess) result = MXE_ERR_CUDA;
+          if (result == MXE_OK) result = enqueue_tune_work(c, s);
+          if (result == MXE_OK && cudaEventRecord(e1, st) != cudaSuccess) result = MXE_ERR_CUDA;
+          float ms = 0.f;
+          if (result == MXE_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            result = MXE_ERR_CUDA;
+          if (rep > 0) total += ms;
+        }
+        if (result == MXE_OK && total < best) {
+          best = total;
+          best_nl = c->nl;
+          best_tpb = c->tpb;
+          best_ptpb = c->pair_tpb;
+        }
       }
-      if (result == MXE_OK && total < best) {
-        best = total;
-        best_nl = lanes[a];
-        best_tpb = threads[b];
-      }
-    }
   c->nl = best_nl;
   c->tpb = best_tpb;
+  c->pair_tpb = best_ptpb;
   c->timing = timing;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -2036,6 +2117,27 @@ mxe_status mxe_set_pass_shape(mxe_ctx* c, int32_t lanes, int32_t threads) {
   if (!c || (lanes != 4 && lanes != 8 && lanes != 16) || (threads != 128 && threads != 256)) return MXE_ERR_ARG;
   c->nl = lanes;
   c->tpb = threads;
+  return MXE_OK;
+}
+
+mxe_status mxe_run_stats(mxe_ctx* c, int32_t* graph_launches, int32_t* kernels_per_step) {
+  if (!c) return MXE_ERR_ARG;
+  if (graph_launches) *graph_launches = c->run_launches;
+  if (kernels_per_step) *kernels_per_step = c->step_kernels;
+  return MXE_OK;
+}
+
+mxe_status mxe_set_pair_block(mxe_ctx* c, int32_t pair_threads) {
+  if (!c || (pair_threads != 64 && pair_threads != 128 && pair_threads != 256)) return MXE_ERR_ARG;
+  c->pair_tpb = pair_threads;
+  return MXE_OK;
+}
+
+mxe_status mxe_get_pass_shape(mxe_ctx* c, int32_t* lanes, int32_t* threads, int32_t* pair_threads) {
+  if (!c) return MXE_ERR_ARG;
+  if (lanes) *lanes = c->nl;
+  if (threads) *threads = c->tpb;
+  if (pair_threads) *pair_threads = c->pair_tpb;
   return MXE_OK;
 }
 

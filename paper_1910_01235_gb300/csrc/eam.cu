@@ -920,8 +920,12 @@ __device__ __forceinline__ double pair_term(const RadialFn& F, double r, const f
   return e;
 }
 
+// sqrt(a b) of two positive values (the cross term of a geometric-mean pair)
+__device__ __forceinline__ ff cross_mean(ff a, ff b) { return ff_sqrt(a * b); }
+__device__ __forceinline__ double cross_mean(double a, double b) { return sqrt(a * b); }
+
 template <int S, typename R>
-__global__ void __launch_bounds__(128) k_pair_geo(DevPot P, DevGrid g0, PassArgs A,
+__global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs A,
                                                   const int4* __restrict__ pair_rec, int64_t npair,
                                                   typename GeoRec<R>::T* __restrict__ buf, int C) {
   constexpr int PR = GeoPrec<R>::P;
@@ -965,23 +969,44 @@ __global__ void __launch_bounds__(128) k_pair_geo(DevPot P, DevGrid g0, PassArgs
     sw(P, pr[k], pw[k], dS);
   }
   // one term at a time over the points (rolled: one copy of the float-float
-  // exponential in the loop body)
-  typename GeoRec<R>::T* o = buf + p * (int64_t)C;
+  // exponential in the loop body); the record goes to both entries of the
+  // pair (every value is symmetric in i and j), so the gathers read rows in
+  // order
+  typename GeoRec<R>::T* o = buf + pr_.tp * (int64_t)C;
+  typename GeoRec<R>::T* o2 = buf + pr_.tr * (int64_t)C;
 #pragma unroll 1
   for (int v = 0; v < P.n_f; ++v) {
     R acc = (R)0;
 #pragma unroll 1
     for (int k = 0; k < 12; ++k) acc += geo_term(P.f[v], pr[k], s_exp) * pw[k];
     const R st = geo_term(P.f[v], pr[12], s_exp) * pw[12];
-    o[v] = GeoRec<R>::put(st);
-    o[P.n_f + v] = GeoRec<R>::put(acc);
+    o[v] = o2[v] = GeoRec<R>::put(st);
+    o[P.n_f + v] = o2[P.n_f + v] = GeoRec<R>::put(acc);
   }
+  if (P.tab == 1 && P.cross_geo) {
+    // binary pattern with a geometric-mean cross pair: terms 0 and 2 are the
+    // like pairs and term 1's exponential is exactly the square root of their
+    // product (its c and lambda are their means), so a node costs two
+    // exponentials and a square root instead of three exponentials
+    R a0 = (R)0, a1 = (R)0, a2 = (R)0;
 #pragma unroll 1
-  for (int u = 0; u < P.n_phi; ++u) {
-    R acc = (R)0;
+    for (int k = 0; k < 12; ++k) {
+      const R e0 = pair_term(P.phi[0], pr[k], s_exp), e2 = pair_term(P.phi[2], pr[k], s_exp);
+      a0 += e0 * pw[k];
+      a2 += e2 * pw[k];
+      a1 += cross_mean(e0, e2) * pw[k];
+    }
+    o[2 * P.n_f + 0] = o2[2 * P.n_f + 0] = GeoRec<R>::put(a0);
+    o[2 * P.n_f + 1] = o2[2 * P.n_f + 1] = GeoRec<R>::put(a1);
+    o[2 * P.n_f + 2] = o2[2 * P.n_f + 2] = GeoRec<R>::put(a2);
+  } else {
 #pragma unroll 1
-    for (int k = 0; k < 12; ++k) acc += pair_term(P.phi[u], pr[k], s_exp) * pw[k];
-    o[2 * P.n_f + u] = GeoRec<R>::put(acc);
+    for (int u = 0; u < P.n_phi; ++u) {
+      R acc = (R)0;
+#pragma unroll 1
+      for (int k = 0; k < 12; ++k) acc += pair_term(P.phi[u], pr[k], s_exp) * pw[k];
+      o[2 * P.n_f + u] = o2[2 * P.n_f + u] = GeoRec<R>::put(acc);
+    }
   }
   if (bad) atomicOr(A.flags, kFlagGeometry);
 }
@@ -1017,9 +1042,8 @@ __device__ __forceinline__ void load_x(const PassArgs& A, int64_t j, double x[S]
 }
 
 template <int S, int NL, typename R, typename Acc>
-__global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, const int* __restrict__ pid,
-                                                      const typename GeoRec<R>::T* __restrict__ buf, int C,
-                                                      int64_t npair) {
+__global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A,
+                                                      const typename GeoRec<R>::T* __restrict__ buf, int C) {
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
@@ -1036,12 +1060,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
 #pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
       const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
-      const int pp = __ldg(&pid[t]);
-      if (pp < 0 || pp >= npair) {
-        atomicOr(A.flags, kFlagOverflow);
-        continue;
-      }
-      const typename GeoRec<R>::T* rec = buf + (int64_t)pp * C;
+      const typename GeoRec<R>::T* rec = buf + (int64_t)t * C;
       R xj[S];
       load_x<S>(A, j, xj);
 #pragma unroll
@@ -1129,9 +1148,8 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A, cons
 }
 
 template <int S, int NL, typename R, typename Acc>
-__global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int* __restrict__ pid,
-                                                 const typename GeoRec<R>::T* __restrict__ buf, int C,
-                                                 int64_t npair) {
+__global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A,
+                                                 const typename GeoRec<R>::T* __restrict__ buf, int C) {
   constexpr int PR = GeoPrec<R>::P;
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1150,12 +1168,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A, const int
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
     for (int t = beg + lane; t < end; t += NL) {
       const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
-      const int pp = __ldg(&pid[t]);
-      if (pp < 0 || pp >= npair) {
-        atomicOr(A.flags, kFlagOverflow);
-        continue;
-      }
-      const typename GeoRec<R>::T* rec = buf + (int64_t)pp * C;
+      const typename GeoRec<R>::T* rec = buf + (int64_t)t * C;
       R xj[S];
       load_x<S>(A, j, xj);
       R aj[S], bj[S];
@@ -1315,7 +1328,7 @@ struct RelaxAcc<2> {
 };
 
 template <int PREC, int S, int TAB>
-__global__ void __launch_bounds__(128) k_pair_rdensity(DevPot P, DevGrid g0, PassArgs A,
+__global__ void __launch_bounds__(256) k_pair_rdensity(DevPot P, DevGrid g0, PassArgs A,
                                                        const int4* __restrict__ pair_rec, int64_t npair,
                                                        typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens) {
   using R = typename Traits<PREC>::R;
@@ -1491,7 +1504,7 @@ __global__ void __launch_bounds__(256) k_gather_rdensity(DevPot P, PassArgs A,
 }
 
 template <int PREC, int S, int TAB>
-__global__ void __launch_bounds__(128) k_pair_rforce(DevPot P, DevGrid g0, PassArgs A,
+__global__ void __launch_bounds__(256) k_pair_rforce(DevPot P, DevGrid g0, PassArgs A,
                                                      const int4* __restrict__ pair_rec, int64_t npair,
                                                      typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc) {
   using R = typename Traits<PREC>::R;
@@ -2453,16 +2466,20 @@ cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, d
 
 int pair_record_len(const DevPot& P) { return (2 * P.n_f + P.n_phi + 3) & ~3; }
 
+// threads per block of the pair kernels: the unordered pairs one block takes
+int pair_threads(const PassArgs& A) { return A.pair_tpb == 64 || A.pair_tpb == 256 ? A.pair_tpb : 128; }
+
 namespace {
 template <typename R>
 cudaError_t pair_geo_t(const DevPot& P, const DevGrid& g, const PassArgs& A, const int4* pair_rec, int64_t npair,
                        void* buf, cudaStream_t s) {
   const int C = pair_record_len(P);
-  const unsigned blocks = (unsigned)((npair + 127) / 128);
+  const int pt = pair_threads(A);
+  const unsigned blocks = (unsigned)((npair + pt - 1) / pt);
   using T = typename GeoRec<R>::T;
   switch (P.S) {
-    case 1: k_pair_geo<1, R><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
-    case 2: k_pair_geo<2, R><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
+    case 1: k_pair_geo<1, R><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
+    case 2: k_pair_geo<2, R><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -2479,44 +2496,43 @@ cudaError_t launch_pair_geo(int precision, const DevPot& P, const DevGrid& g, co
 
 namespace {
 template <int S, int NL, typename R, typename Acc>
-cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const int* pid, const void* buf, int C,
-                          int64_t npair, cudaStream_t s) {
+cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const void* buf, int C, cudaStream_t s) {
   const int threads = A.tpb > 0 ? A.tpb : 256;
   const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
   using T = typename GeoRec<R>::T;
-  if (mu) k_pair_mu<S, NL, R, Acc><<<blocks, threads, 0, s>>>(P, A, pid, (const T*)buf, C, npair);
-  else k_pair_density<S, NL, R, Acc><<<blocks, threads, 0, s>>>(P, A, pid, (const T*)buf, C, npair);
+  if (mu) k_pair_mu<S, NL, R, Acc><<<blocks, threads, 0, s>>>(P, A, (const T*)buf, C);
+  else k_pair_density<S, NL, R, Acc><<<blocks, threads, 0, s>>>(P, A, (const T*)buf, C);
   return cudaGetLastError();
 }
 template <int S, int NL>
-cudaError_t pair_gather_p(int precision, bool mu, const DevPot& P, const PassArgs& A, const int* pid, const void* buf,
-                          int C, int64_t npair, cudaStream_t s) {
+cudaError_t pair_gather_p(int precision, bool mu, const DevPot& P, const PassArgs& A, const void* buf, int C,
+                          cudaStream_t s) {
   switch (precision) {
-    case 0: return pair_gather_t<S, NL, double, AccD>(mu, P, A, pid, buf, C, npair, s);
-    case 1: return pair_gather_t<S, NL, ff, AccD>(mu, P, A, pid, buf, C, npair, s);
-    case 2: return pair_gather_t<S, NL, ff, AccF2>(mu, P, A, pid, buf, C, npair, s);
+    case 0: return pair_gather_t<S, NL, double, AccD>(mu, P, A, buf, C, s);
+    case 1: return pair_gather_t<S, NL, ff, AccD>(mu, P, A, buf, C, s);
+    case 2: return pair_gather_t<S, NL, ff, AccF2>(mu, P, A, buf, C, s);
     default: return cudaErrorInvalidValue;
   }
 }
 template <int S>
-cudaError_t pair_gather_s(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid,
-                          const void* buf, int C, int64_t npair, cudaStream_t s) {
+cudaError_t pair_gather_s(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf, int C,
+                          cudaStream_t s) {
   switch (nl) {
-    case 4: return pair_gather_p<S, 4>(precision, mu, P, A, pid, buf, C, npair, s);
-    case 8: return pair_gather_p<S, 8>(precision, mu, P, A, pid, buf, C, npair, s);
-    case 16: return pair_gather_p<S, 16>(precision, mu, P, A, pid, buf, C, npair, s);
+    case 4: return pair_gather_p<S, 4>(precision, mu, P, A, buf, C, s);
+    case 8: return pair_gather_p<S, 8>(precision, mu, P, A, buf, C, s);
+    case 16: return pair_gather_p<S, 16>(precision, mu, P, A, buf, C, s);
     default: return cudaErrorInvalidValue;
   }
 }
 }  // namespace
 
-cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid,
-                               const void* buf, int64_t npair, cudaStream_t s) {
+cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf,
+                               cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   const int C = pair_record_len(P);
   switch (P.S) {
-    case 1: return pair_gather_s<1>(precision, mu, nl, P, A, pid, buf, C, npair, s);
-    case 2: return pair_gather_s<2>(precision, mu, nl, P, A, pid, buf, C, npair, s);
+    case 1: return pair_gather_s<1>(precision, mu, nl, P, A, buf, C, s);
+    case 2: return pair_gather_s<2>(precision, mu, nl, P, A, buf, C, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -2552,15 +2568,16 @@ template <int PREC>
 cudaError_t relax_pair_p(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int4* pair_rec,
                          int64_t npair, void* dens, void* frc, cudaStream_t s) {
   using T = typename Rec4<typename Traits<PREC>::R>::T;
-  const unsigned blocks = (unsigned)((npair + 127) / 128);
+  const int pt = pair_threads(A);
+  const unsigned blocks = (unsigned)((npair + pt - 1) / pt);
   if (force) {
-    if (P.S == 1) k_pair_rforce<PREC, 1, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
-    else if (P.tab == 1) k_pair_rforce<PREC, 2, 1><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
-    else k_pair_rforce<PREC, 2, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
+    if (P.S == 1) k_pair_rforce<PREC, 1, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
+    else if (P.tab == 1) k_pair_rforce<PREC, 2, 1><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
+    else k_pair_rforce<PREC, 2, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)frc);
   } else {
-    if (P.S == 1) k_pair_rdensity<PREC, 1, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
-    else if (P.tab == 1) k_pair_rdensity<PREC, 2, 1><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
-    else k_pair_rdensity<PREC, 2, 0><<<blocks, 128, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
+    if (P.S == 1) k_pair_rdensity<PREC, 1, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
+    else if (P.tab == 1) k_pair_rdensity<PREC, 2, 1><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
+    else k_pair_rdensity<PREC, 2, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)dens);
   }
   return cudaGetLastError();
 }

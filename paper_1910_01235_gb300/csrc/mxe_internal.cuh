@@ -56,6 +56,7 @@ struct DevPot {
   int8_t f_of[kMaxS][kMaxS];     // species pair -> distinct f term (-1: zero)
   double E[kMaxS];
   int tab;                       // 1: the binary alloy pattern below, 0: general tables
+  int cross_geo;                 // the cross pair term is the geometric mean of the like pairs
   double rs, rc, inv_w;          // switch start, cutoff, 1/(rc - rs)
   float rs_f, rc_f, inv_w_f, dS_scale_f;
   ff rs_ff, inv_w_ff, dS_scale_ff;
@@ -151,8 +152,6 @@ cudaError_t launch_cell_assign(const double* q, int64_t n, const DevGrid& g, con
                                int* cell_slot, int* cell_count, int* abs_cell, float4* qf, cudaStream_t s);
 cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slot, const int* cell_start,
                               int* cell_sites, cudaStream_t s);
-// each cell's sites in increasing index
-cudaError_t launch_cell_sort(int64_t ncell, const int* cell_start, int* cell_sites, cudaStream_t s);
 cudaError_t launch_nbr_count(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask, int64_t n,
                              const DevGrid& g, const Batch& B, const int* cell_of, const int* cell_start, const int* cell_sites,
                              double rl2, double rb2, float band, int* nb_cnt, int* bd_cnt, int* max_row,
@@ -244,22 +243,25 @@ struct PassArgs {
   int lean;         // FP32 density pass of the relaxation: write only the packed (a, b)
   Batch batch;      // several systems (nsys > 0): per-site box and cell grid
   int tpb;  // threads per block of the density and gradient passes (0: 256)
+  int pair_tpb;  // threads per block of the pair kernels: pairs per block (64, 128, 256; else 128)
 };
 cudaError_t launch_density(int precision, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                            cudaStream_t s);
 enum { kGradAll = 0, kGradForce = 1, kGradMu = 2, kGradForceNoE = 3 };
 cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, const DevGrid& g, const PassArgs& a,
                             cudaStream_t s);
-// half-list accurate passes: records of pair_record_len(P) values per
-// unordered pair (float pairs: float-float node arithmetic of the FP32 modes;
-// doubles: FP64 contexts), then the density (mu = false) or
-// chemical-potential gather (per-site sums in float-float for MXE_FP32_FF,
+// half-list accurate passes: each unordered pair's record of
+// pair_record_len(P) values (float pairs: float-float node arithmetic of the
+// FP32 modes; doubles: FP64 contexts) written to both of its entries
+// ([entries][C]), then the density (mu = false) or chemical-potential gather
+// over each site's own row (per-site sums in float-float for MXE_FP32_FF,
 // FP64 otherwise)
 int pair_record_len(const DevPot& P);
+int pair_threads(const PassArgs& A);
 cudaError_t launch_pair_geo(int precision, const DevPot& P, const DevGrid& g, const PassArgs& A,
                             const int4* pair_rec, int64_t npair, void* buf, cudaStream_t s);
-cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const int* pid,
-                               const void* buf, int64_t npair, cudaStream_t s);
+cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf,
+                               cudaStream_t s);
 // half-list relaxation passes (FP32 node math in the FP32 modes, FP64 in FP64
 // contexts): the pair kernel writes each pair's record to both of its entries
 // (pair_t[p], pair_rev[p]); the gather then reads its own row: density (force
@@ -312,6 +314,9 @@ cudaError_t launch_fire_seg_init(SysFire* sf, int nsys, double dt0, double alpha
 // rebuild or an error is kept until the host clears it)
 cudaError_t launch_step_begin(Ctrl* ctrl, double dt0, double alpha0, cudaStream_t s);
 cudaError_t launch_step_end(Ctrl* ctrl, cudaStream_t s);
+// end of the body of a device-side loop of steps (graph while node): sets
+// the loop's condition; loop [3] = bodies run, step count to reach, cap
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const Ctrl* ctrl, int* loop, cudaStream_t s);
 cudaError_t launch_fire_zero_v(double* vq, double* vs, int64_t n, const Ctrl* gate, cudaStream_t s);
 
 // deriv.cu: forward-mode (dual-number) density and gradient passes

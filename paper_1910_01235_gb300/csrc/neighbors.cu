@@ -10,10 +10,8 @@
 // (the band bounds the position rounding, the image choice and the rounding
 // of |d|^2; outside it the FP32 and FP64 decisions agree).
 // One warp handles one site: lanes sweep the candidates of the distinct
-// neighbouring cells and accepted entries are compacted with ballots.  The
-// cell-staged kernels visit a block's candidates in increasing j (sorted once
-// per block), so the compaction is the row in j order; the warp-per-site
-// fallback places entries in j order by rank counting.  Each entry stores j in the
+// neighbouring cells, accepted entries are compacted into shared memory with
+// ballots and placed in j order by rank counting.  Each entry stores j in the
 // low 27 bits and the periodic image code (cell offset in {-1,0,1}^3) above it,
 // which the FP32 kernels use to rebuild d from cell-relative positions.
 #include <cuda_runtime.h>
@@ -55,24 +53,6 @@ __global__ void k_cell_place(int64_t n, const int* __restrict__ cell_of, const i
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   cell_sites[cell_start[cell_of[i]] + cell_slot[i]] = (int)i;
-}
-
-// Each cell's sites in increasing index (the slots above come from atomics):
-// one thread per cell, insertion sort of its ~15 sites.  The cell-staged fill
-// then stages every stencil cell as a sorted run.
-__global__ void k_cell_sort(int64_t ncell, const int* __restrict__ cell_start, int* __restrict__ cell_sites) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int b = cell_start[c], e = cell_start[c + 1];
-  for (int u = b + 1; u < e; ++u) {
-    const int v = cell_sites[u];
-    int w = u - 1;
-    while (w >= b && cell_sites[w] > v) {
-      cell_sites[w + 1] = cell_sites[w];
-      --w;
-    }
-    cell_sites[w + 1] = v;
-  }
 }
 
 // The distinct cells of the 3x3x3 stencil around `cell` (duplicates removed
@@ -434,6 +414,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
   const int sys = B.nsys ? B.cell_sys[cell] : 0;
   const DevGrid g = B.nsys ? B.grids[sys] : g0;
   const int base = B.nsys ? B.cell_base[sys] : 0;
+  __shared__ int s_rowmax;  // the block's longest row: one global atomic per block
+  if (threadIdx.x == 0) s_rowmax = 0;
   const CellStage cs =
       stage_cell(cell, base, g, n, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, s_sh, cand_cap, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -459,46 +441,13 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
     if (lane == 0) {
       nb_cnt[i] = cnt;
       bd_cnt[i] = bcnt;
-      atomicMax(max_row, cnt);
+      atomicMax(&s_rowmax, cnt);
     }
-  }
-}
-
-// The staged candidates in increasing j: the 27 stencil cells are staged as
-// runs that are each sorted (k_cell_sort), and every candidate j is distinct
-// (each site sits in one cell, the stencil's cells are distinct), so a
-// candidate's place in the merged order is the sum over the runs of the
-// number of keys below it (a binary search per run).  Each candidate is
-// copied to its place in (cq2, cj2).
-__device__ __forceinline__ int run_lower_bound(const int* cj, int beg, int end, uint32_t key) {
-  while (beg < end) {
-    const int mid = (beg + end) >> 1;
-    if (((uint32_t)cj[mid] & kIdxMask) < key) beg = mid + 1;
-    else end = mid;
-  }
-  return beg;
-}
-
-__device__ __forceinline__ void merge_stage(const float4* cq, const int* cj, int ncand, const int* s_off,
-                                            float4* cq2, int* cj2) {
-  for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
-    const uint32_t key = (uint32_t)cj[t] & kIdxMask;
-    int rank = 0;
-#pragma unroll 1
-    for (int r = 0; r < 27; ++r) {
-      const int b = s_off[r], e = min(s_off[r + 1], ncand);
-      if (b >= e) continue;
-      rank += run_lower_bound(cj, b, e, key) - b;
-    }
-    cq2[rank] = cq[t];
-    cj2[rank] = cj[t];
   }
   __syncthreads();
+  if (threadIdx.x == 0) atomicMax(max_row, s_rowmax);
 }
 
-// The candidates are visited in increasing j (merge_stage), so the ballot
-// compaction of the accepted ones is the row in j order: entries go straight
-// to nb_ent (bonds to bd_idx), each ballot round a coalesced run.
 // DIRECT: no count pass before: row i goes to nb_ent[i * max_row ...] (max_row
 // = the stride, from the previous build) with its counts in nb_cnt / bd_cnt
 // and the longest row in *row_max; a row longer than the stride is cut and
@@ -516,28 +465,31 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   __shared__ float s_sh[27 * 3];
   float4* cq = reinterpret_cast<float4*>(smem);
   int* cj = reinterpret_cast<int*>(cq + cand_cap);
-  float4* cq2 = reinterpret_cast<float4*>(cj + cand_cap + ((4 - (cand_cap & 3)) & 3));  // 16-byte aligned
-  int* cj2 = reinterpret_cast<int*>(cq2 + cand_cap);
   const int cell = blockIdx.x;
   const int hbeg = cell_start[cell], hend = cell_start[cell + 1];
   if (hbeg == hend) return;
   const int sys = B.nsys ? B.cell_sys[cell] : 0;
   const DevGrid g = B.nsys ? B.grids[sys] : g0;
   const int base = B.nsys ? B.cell_base[sys] : 0;
+  // the longest row of the block, then one global maximum per block (a global
+  // atomic per site serialises 256,000 updates of one word)
+  __shared__ int s_rowmax;
+  if (threadIdx.x == 0) s_rowmax = 0;
   const CellStage cs =
       stage_cell(cell, base, g, n, cell_start, cell_sites, qf, cq, cj, s_off, s_beg, s_sh, cand_cap, flags);
-  merge_stage(cq, cj, cs.ncand, s_off, cq2, cj2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // per warp: the row's entries and its sort keys (j << 1 | bond), 16-byte aligned
+  const int stride = (max_row + 3) & ~3;
+  uint32_t* rows = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(cj + cand_cap) + 15) & ~uintptr_t(15));
+  uint32_t* buf = rows + (size_t)warp * stride;
+  uint32_t* kw = rows + (size_t)(nwarps + warp) * stride;
   const float rl2f = (float)rl2, rb2f = (float)rb2;
-  const unsigned below = (1u << lane) - 1u;
   for (int h = hbeg + warp; h < hend; h += nwarps) {
     const int64_t i = cell_sites[h];
     const double qi[3] = {q[i], q[n + i], q[2 * n + i]};
     const float4 qfi = cs.fast ? qf[n + i] : qf[i];
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
-    const int64_t off = DIRECT ? i * (int64_t)max_row : (int64_t)nb_off[i];
-    const int64_t boff = DIRECT ? i * (int64_t)max_row : (int64_t)bd_off[i];
     int m = 0, nbond = 0;
     for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
       const int t = t0 + lane;
@@ -545,10 +497,10 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
       uint32_t ent = 0;
       int j = 0;
       if (t < cs.ncand) {
-        ent = (uint32_t)cj2[t];
+        ent = (uint32_t)cj[t];
         j = (int)(ent & kIdxMask);
-        r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq2[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
-                    : test_cand(i, qi, qfi, j, cq2[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
+        r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
+                    : test_cand(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub, true);
       }
       if (r.in && !cs.fast) {
         int code = 0;
@@ -561,23 +513,45 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
         ent = (uint32_t)j | ((uint32_t)code << kCodeShift);
       }
       const unsigned msk = __ballot_sync(0xffffffffu, r.in);
-      const unsigned bmsk = __ballot_sync(0xffffffffu, r.bond);
       if (r.in) {
-        const int pos = m + __popc(msk & below);
-        if (pos < max_row) nb_ent[off + pos] = ent;
-      }
-      if (r.bond) {
-        const int bpos = nbond + __popc(bmsk & below);
-        if (bpos < max_row) bd_idx[boff + bpos] = j;
+        const int pos = m + __popc(msk & ((1u << lane) - 1u));
+        if (pos < max_row) {
+          buf[pos] = ent;
+          kw[pos] = ((uint32_t)j << 1) | (r.bond ? 1u : 0u);
+        }
       }
       m += __popc(msk);
-      nbond += __popc(bmsk);
+      if (DIRECT) nbond += __popc(__ballot_sync(0xffffffffu, r.bond));
     }
     if (DIRECT && lane == 0) {
       nb_cnt[i] = m;
       bd_cnt[i] = nbond;
-      atomicMax(row_max, m);
+      atomicMax(&s_rowmax, m);
     }
+    if (m > max_row) m = max_row;  // count + fill: cannot happen (max_row is the counted maximum)
+    const int m4 = (m + 3) >> 2;
+    for (int e = m + lane; e < 4 * m4; e += 32) kw[e] = 0xFFFFFFFFu;  // pads rank after every key
+    __syncwarp();
+    const int64_t off = DIRECT ? i * (int64_t)max_row : (int64_t)nb_off[i];
+    const int64_t boff = DIRECT ? i * (int64_t)max_row : (int64_t)bd_off[i];
+    const uint4* k4 = reinterpret_cast<const uint4*>(kw);
+    for (int e = lane; e < m; e += 32) {
+      const uint32_t ke = kw[e] & ~1u;  // j << 1: keys of smaller j are below it
+      int rank = 0, brank = 0;
+      for (int f = 0; f < m4; ++f) {
+        const uint4 v = k4[f];
+        const uint32_t l0 = v.x < ke, l1 = v.y < ke, l2 = v.z < ke, l3 = v.w < ke;
+        rank += (int)(l0 + l1 + l2 + l3);
+        brank += (int)((l0 & v.x) + (l1 & v.y) + (l2 & v.z) + (l3 & v.w));
+      }
+      nb_ent[off + rank] = buf[e];
+      if (kw[e] & 1u) bd_idx[boff + brank] = (int)(ke >> 1);
+    }
+    __syncwarp();
+  }
+  if (DIRECT) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(row_max, s_rowmax);
   }
 }
 
@@ -766,6 +740,7 @@ __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __re
   }
 }
 
+
 // rows written at a fixed stride -> CSR (one warp per row)
 __global__ void k_row_compact(const uint32_t* __restrict__ rows, const int* __restrict__ brows, int stride, int64_t n,
                               const int* __restrict__ nb_off, const int* __restrict__ bd_off,
@@ -792,12 +767,6 @@ cudaError_t launch_cell_place(int64_t n, const int* cell_of, const int* cell_slo
                               int* cell_sites, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_cell_place<<<grid_for(n, 256), 256, 0, s>>>(n, cell_of, cell_slot, cell_start, cell_sites);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cell_sort(int64_t ncell, const int* cell_start, int* cell_sites, cudaStream_t s) {
-  if (ncell == 0) return cudaSuccess;
-  k_cell_sort<<<grid_for(ncell, 128), 128, 0, s>>>(ncell, cell_start, cell_sites);
   return cudaGetLastError();
 }
 
@@ -839,9 +808,8 @@ cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const Batch& B, con
 }
 
 size_t cell_stage_bytes(int cand_cap, int max_row, bool fill) {
-  (void)max_row;  // rows are written straight to global memory
   size_t b = (size_t)cand_cap * (sizeof(float4) + sizeof(int));
-  if (fill) b += 16 + (size_t)cand_cap * (sizeof(float4) + sizeof(int));  // the candidates in j order
+  if (fill) b += 16 + (size_t)(kCellThreads / 32) * 2 * (size_t)((max_row + 3) & ~3) * sizeof(uint32_t);
   return b + 16;
 }
 

@@ -391,6 +391,18 @@ __global__ void k_step_end(Ctrl* __restrict__ ctrl) {
   C.phase = 0;
 }
 
+// The staggered run replayed on the device: after each step the condition of
+// the graph's while node is set to repeat the step while steps remain, no
+// stop (rebuild or error) is pending and the body has run fewer than `cap`
+// times, so the loop always ends.  loop[0]: bodies run, loop[1]: the step
+// count to reach, loop[2]: the cap (set by the host before each launch).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const Ctrl* __restrict__ ctrl, int* __restrict__ loop) {
+  const int runs = loop[0] + 1;
+  loop[0] = runs;
+  const bool more = ctrl->steps < loop[1] && !run_stopped(*ctrl) && runs < loop[2];
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 __global__ void __launch_bounds__(256) k_fire_zero_v(double* __restrict__ vq, double* __restrict__ vs, int64_t n,
                                                      const Ctrl* __restrict__ gate) {
   if (gate->halted) return;
@@ -411,6 +423,11 @@ cudaError_t launch_step_begin(Ctrl* ctrl, double dt0, double alpha0, cudaStream_
 
 cudaError_t launch_step_end(Ctrl* ctrl, cudaStream_t s) {
   k_step_end<<<1, 1, 0, s>>>(ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const Ctrl* ctrl, int* loop, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(h, ctrl, loop);
   return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy",
            "mxe_diffuse_step_noalloc", "mxe_timing_enable", "mxe_timing_read", "mxe_set_reservoirs",
            "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape",
            "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad", "mxe_transport_step",
-           "mxe_set_embedding", "mxe_element_param_grad"]
+           "mxe_set_embedding", "mxe_element_param_grad", "mxe_unrolled_grad_multi", "mxe_set_pair_block",
+           "mxe_get_pass_shape", "mxe_run_stats"]
 EMBED_TAYLOR, EMBED_EXACT = 0, 1
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
@@ -104,7 +105,12 @@ def lib():
             L.mxe_autotune.argtypes = [p, p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
             L.mxe_set_pass_shape.argtypes = [p, C.c_int32, C.c_int32]
             L.mxe_set_embedding.argtypes = [p, C.c_int32]
+            L.mxe_set_pair_block.argtypes = [p, C.c_int32]
+            L.mxe_get_pass_shape.argtypes = [p, p, p, p]
+            L.mxe_run_stats.argtypes = [p, p, p]
             L.mxe_element_param_grad.argtypes = [p, p, p]
+            L.mxe_unrolled_grad_multi.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.c_int32, C.c_int32,
+                                                  p, d, C.c_int32, p, p, p]
             i32p = C.POINTER(C.c_int32)
             L.mxe_potential_terms.argtypes = [p, i32p, i32p, p, p, p]
             L.mxe_tangent.argtypes = [p, p] + [p] * 10
@@ -235,6 +241,18 @@ def mxe_unrolled_grad(ctx, state, n_steps, dt, nu0, Qm, ftol, max_iter, fire, ev
                                  C.c_void_p(w_ptr), float(cg_tol), int(cg_max), dterm, C.c_void_p(dx0_ptr or 0),
                                  C.byref(info))
     return st, np.array(dterm[:2 * n_terms]), {nm: getattr(info, nm) for nm, _ in mxe_grad_info._fields_}
+
+
+def mxe_unrolled_grad_multi(ctx, state, n_steps, dt, nu0, Qm, ftol, max_iter, fire, every, n_obj, w_ptr, cg_tol,
+                            cg_max, n_terms, dx0_ptr=0):
+    dterm = (C.c_double * max(2 * n_terms * n_obj, 1))()
+    info = mxe_grad_info()
+    st = lib().mxe_unrolled_grad_multi(ctx, C.byref(state), int(n_steps), float(dt), float(nu0), float(Qm),
+                                       float(ftol), int(max_iter), C.byref(fire) if fire is not None else None,
+                                       int(every), int(n_obj), C.c_void_p(w_ptr), float(cg_tol), int(cg_max), dterm,
+                                       C.c_void_p(dx0_ptr or 0), C.byref(info))
+    return (st, np.array(dterm[:2 * n_terms * n_obj]).reshape(n_obj, 2 * n_terms),
+            {nm: getattr(info, nm) for nm, _ in mxe_grad_info._fields_})
 
 
 def mxe_build_neighbors(ctx, state: mxe_state, skin: float, r_bond: float):
@@ -477,13 +495,28 @@ class MxeSystem:
         self._check(st, "mxe_run_staggered", allow)
         return st, done
 
+    def run_stats(self):
+        """(graph launches, kernels per step) of the last run_staggered."""
+        v = (C.c_int32 * 2)()
+        self._check(lib().mxe_run_stats(self.ctx, C.byref(v, 0), C.byref(v, 4)), "mxe_run_stats")
+        return tuple(v)
+
     def autotune(self):
         st, lanes, threads = mxe_autotune(self.ctx, self.state)
         self._check(st, "mxe_autotune")
         return lanes, threads
 
-    def set_pass_shape(self, lanes, threads):
+    def set_pass_shape(self, lanes, threads, pair_threads=None):
         self._check(mxe_set_pass_shape(self.ctx, lanes, threads), "mxe_set_pass_shape")
+        if pair_threads is not None:
+            self._check(lib().mxe_set_pair_block(self.ctx, int(pair_threads)), "mxe_set_pair_block")
+
+    def pass_shape(self):
+        """(lanes per site, threads per block, pairs per block of the pair kernels)."""
+        v = (C.c_int32 * 3)()
+        self._check(lib().mxe_get_pass_shape(self.ctx, C.byref(v, 0), C.byref(v, 4), C.byref(v, 8)),
+                    "mxe_get_pass_shape")
+        return tuple(v)
 
     def set_embedding(self, mode):
         """"taylor" (Eq. F_taylor_mxe, default) or "exact" (App. A's rule over
@@ -532,6 +565,20 @@ class MxeSystem:
                                             self.sys.Qm if Qm is None else Qm, ftol, max_iter, fire, every,
                                             _ptr(w), cg_tol, cg_max, nphi + nf, _ptr(dx0))
         self._check(st, "mxe_unrolled_grad")
+        return dterm, dx0, info
+
+    def unrolled_grad_multi(self, n_steps, dt, w, ftol=1e-10, max_iter=50000, every=5, cg_tol=1e-10, cg_max=5000,
+                            fire=None, nu0=None, Qm=None):
+        """As unrolled_grad for the objectives w [n_obj, S, n] at once
+        (mxe_unrolled_grad_multi).  Returns (dterm [n_obj, 2 T], dx0, info)."""
+        nphi, nf, _, _, _ = self.potential_terms()
+        w = self.torch.as_tensor(w, dtype=self.torch.float64, device=self.device).contiguous()
+        dx0 = self.torch.zeros_like(w)
+        st, dterm, info = mxe_unrolled_grad_multi(self.ctx, self.state, n_steps, dt,
+                                                  self.sys.nu0 if nu0 is None else nu0,
+                                                  self.sys.Qm if Qm is None else Qm, ftol, max_iter, fire, every,
+                                                  w.shape[0], _ptr(w), cg_tol, cg_max, nphi + nf, _ptr(dx0))
+        self._check(st, "mxe_unrolled_grad_multi")
         return dterm, dx0, info
 
     def staggered_step(self, dt, ftol, max_iter, fire=None):

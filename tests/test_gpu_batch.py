@@ -284,6 +284,9 @@ def test_graph_run_matches_step_by_step_calls(prec):
     b.build_neighbors()
     st, done = b.run_staggered(steps, dt, 0.0, K)
     assert st == M.OK and done == steps
+    # every step of the run from one graph launch (a device-side loop)
+    launches, kernels = b.run_stats()
+    assert launches == 1 and kernels >= 7 * (K + 1)
     dx = (a.x - b.x).abs().max().item()
     dq = (a.q - b.q).abs().max().item()
     ds = (a.sigma - b.sigma).abs().max().item()
@@ -306,6 +309,11 @@ def test_graph_run_fp64_oracle_parity(skin):
     g.build_neighbors()
     st, done = g.run_staggered(steps, dt, 0.0, K)
     assert st == M.OK and done == steps
+    launches, _ = g.run_stats()
+    if skin == 0.2:
+        assert launches == 1
+    else:
+        assert launches > 1       # the loop stopped for rebuilds and was launched again
     sto, so, iters = O.staggered(s, steps, dt, 0.0, K, g.r_bond, initial_relax=False)
     assert sto == O.OK
     assert np.abs(so.x - s.x).max() > 1e-3
@@ -378,10 +386,14 @@ def test_autotune_picks_a_valid_shape_and_keeps_results():
     scale = max(ref[0].abs().max().item(), 1.0)
     assert (g.gq - ref[0]).abs().max().item() <= 1e-6 * scale
     assert (g.mu_ex - ref[1]).abs().max().item() <= 1e-10
-    for lanes, threads in ((4, 128), (16, 256)):
-        g.set_pass_shape(lanes, threads)
+    assert g.pass_shape()[2] in (64, 128, 256)     # pairs per block of the pair kernels
+    for lanes, threads, pairs in ((4, 128, 64), (16, 256, 256)):
+        g.set_pass_shape(lanes, threads, pairs)
+        assert g.pass_shape() == (lanes, threads, pairs)
         g.free_energy_grad()
         assert (g.gq - ref[0]).abs().max().item() <= 1e-6 * scale
+        assert (g.mu_ex - ref[1]).abs().max().item() <= 1e-10
     assert M.mxe_set_pass_shape(g.ctx, 5, 256) == M.ERR_ARG
     assert M.mxe_set_pass_shape(g.ctx, 8, 96) == M.ERR_ARG
+    assert M.lib().mxe_set_pair_block(g.ctx, 96) == M.ERR_ARG
     g.close()

@@ -276,3 +276,47 @@ def test_unrolled_gradient_rejects_fp32_contexts_and_reservoirs():
                                           M._ptr(dev(w)), 1e-10, 100, 5)
     assert st == M.ERR_ARG
     g.close()
+
+
+def z_profile_weights(s, nbins):
+    """Mean x_B of the sites in each of nbins slabs along z (the B-fraction
+    z-profile): w[b] = indicator(bin b) / (sites in bin b) on species B."""
+    z = s.q[2] % s.L[2]
+    b = np.minimum((z / s.L[2] * nbins).astype(int), nbins - 1)
+    w = np.zeros((nbins,) + s.x.shape)
+    for k in range(nbins):
+        m = b == k
+        w[k, 1, m] = 1.0 / m.sum()
+    return w
+
+
+def test_z_profile_jacobian_shares_one_forward_sweep():
+    """The whole B-fraction z-profile (4 bins) x 8 parameters from one call:
+    every row equals the single-objective gradient of that bin, and two
+    entries match central differences of the oracle's staggered run."""
+    s, rb, dt, _ = unrolled_case()
+    W4 = z_profile_weights(s, 4)
+    g = ctx_for(s)
+    dterm, dx0, info = g.unrolled_grad_multi(N_STEPS, dt, W4, ftol=1e-10, every=1)
+    g.close()
+    assert dterm.shape[0] == 4
+    jac = np.array([M.element_param_grad(s.pot, dterm[b]).reshape(-1) for b in range(4)])
+    for b in (0, 3):
+        g = ctx_for(s)
+        d1, x1, _ = g.unrolled_grad(N_STEPS, dt, W4[b], ftol=1e-10, every=1)
+        g.close()
+        np.testing.assert_allclose(dterm[b], d1, rtol=1e-9, atol=1e-12 * np.abs(d1).max())
+        np.testing.assert_allclose(dx0[b].cpu().numpy(), x1.cpu().numpy(), rtol=0,
+                                   atol=1e-9 * np.abs(x1.cpu().numpy()).max())
+    theta = W.theta_of(s.pot)
+    m = W.THETA_NAMES.index("p_B")
+    h = 3e-4 * abs(theta[m])
+    for b in (1, 2):
+        vals = []
+        for sgn in (1, -1):
+            th = theta.copy()
+            th[m] += sgn * h
+            vals.append(oracle_L(s, W.binary_from_theta(th, s.pot), dt, W4[b], rb)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        print("bin", b, jac[b, m], fd)
+        assert abs(jac[b, m] - fd) <= 1e-4 * abs(fd) + 1e-12
