@@ -514,7 +514,10 @@ MXE_API mxe_status mxe_timing_read(mxe_ctx *ctx, int32_t max_entries, char *name
  * the process exits; it bounds n to MXE_NOALLOC_MAX_SITES(S), and a larger n
  * (or S outside 1..2) returns MXE_ERR_ARG before any GPU work.  The first
  * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  The address is
+ * current.  Every call ends by reading the step's status back and
+ * synchronising its stream, so no call may be issued on a stream that is
+ * being captured (the capture would be invalidated and the call returns
+ * MXE_ERR_CUDA).  The address is
  * kept for the life of the process: a process that resets a device
  * (cudaDeviceReset) must not call this entry point on it again.  Every call shares
  * the array and it keeps the last call's contents: the flag words are cleared

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmxe.so")
 SOURCES = ["api.cu", "neighbors.cu", "eam.cu", "relax.cu", "flux.cu", "noalloc.cu", "deriv.cu"]
-HEADERS = [os.path.join(CSRC, "mxe_internal.cuh"), os.path.join(ROOT, "include", "mxe.h")]
+HEADERS = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")) + [os.path.join(ROOT, "include", "mxe.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

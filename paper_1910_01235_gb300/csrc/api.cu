@@ -72,8 +72,9 @@ struct mxe_ctx {
   int64_t nb_cap = 0, bd_cap = 0;
   long long* scan_tmp = nullptr;
   int64_t scan_len = 0;
-  long long* totals = nullptr;  // [4]: cells, neighbours, bonds, spare
+  long long* totals = nullptr;  // [4]: cells, neighbours, bonds, owned pairs
   int* max_row = nullptr;
+  int cand_cap_prev = 0;  // largest stencil candidate set of the last build
   unsigned long long* smax_bits = nullptr;
   int64_t n_pairs = 0, n_bonds = 0;
   int max_row_h = 0;
@@ -82,9 +83,9 @@ struct mxe_ctx {
   double* q_build = nullptr;
   // unordered-pair index and records of the half-list passes (contexts whose
   // potential the pair kernels support)
-  int *first_gt = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
+  // per row: entries below its site (head), pairs it owns (tail), their scan
+  int *n_below = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
   int4* pair_rec = nullptr;  // [pairs] (i, entry of j with its image code, entry index, reverse entry index)
-  int* pid = nullptr;        // [entries] pair of every entry
   double* pair_buf = nullptr;  // [entries][pair_record_len] 8-byte values (float pairs or doubles)
   void *ent_dens = nullptr, *ent_frc = nullptr;  // [entries] relaxation records (relax_record_bytes each)
   bool relax_records = false;  // allocate them (first relaxation of the context, then with every list growth)
@@ -514,21 +515,34 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   CK(TIMED("build_misc", launch_cell_assign(s->q, n, g, B, c->cell_of, c->cell_slot, c->cell_count, c->abs_cell, c->qf, st)));
   CK(TIMED("build_misc", launch_scan(c->cell_count, c->cell_start, ncell, c->totals + 0, (int*)c->scan_tmp, c->scan_len, st)));
   CK(TIMED("build_misc", launch_cell_place(n, c->cell_of, c->cell_slot, c->cell_start, c->cell_sites, st)));
-  // largest stencil candidate set: the cell-staged kernels need it in shared memory
-  CK(cudaMemsetAsync(c->max_row, 0, 2 * sizeof(int), st));
+  // largest stencil candidate set: the cell-staged kernels hold it in shared
+  // memory.  A rebuild that can skip the count pass (the previous build's
+  // longest row bounds this one's) sizes it from the previous build's largest
+  // stencil plus a margin and checks the true size, computed on the device
+  // meanwhile, together with the totals: a larger stencil discards that fill
+  // (count + fill instead).  Otherwise the host waits for the size here.
+  CK(cudaMemsetAsync(c->max_row, 0, 3 * sizeof(int), st));
   CK(TIMED("build_misc", launch_cand_max(ncell, g, B, c->cell_start, c->max_row + 1, st)));
-  CK(cudaMemcpyAsync(c->ints_h + 2, c->max_row + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  const int cand_cap = std::max(c->ints_h[2], 1);
   // MXE_NEIGHBOR_PER_SITE forces the warp-per-site kernels (they are the
   // fallback for stencils too dense for shared memory; tests compare both)
-  const bool staged = cell_stage_bytes(cand_cap, 256, true) <= 64 * 1024 && !std::getenv("MXE_NEIGHBOR_PER_SITE");
+  const bool per_site = std::getenv("MXE_NEIGHBOR_PER_SITE") != nullptr;
+  const bool try_direct = c->max_row_h > 0 && c->max_row_h + 16 <= 256 && c->cand_cap_prev > 0 && !per_site &&
+                          !std::getenv("MXE_NEIGHBOR_COUNT");
+  int cand_cap;
+  if (try_direct) {
+    cand_cap = c->cand_cap_prev + c->cand_cap_prev / 8 + 8;
+  } else {
+    CK(cudaMemcpyAsync(c->ints_h + 2, c->max_row + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cand_cap = std::max(c->ints_h[2], 1);
+  }
+  bool staged = cell_stage_bytes(cand_cap, 256, true) <= 64 * 1024 && !per_site;
   // counts: from a fill at a fixed stride when the previous build's longest row
   // bounds it (no count pass), else a count pass before the fill
   const double rl2 = r_list * r_list, rb2 = r_bond * r_bond;
   bool direct = false;
   int stride = 0;
-  if (staged && c->max_row_h > 0 && c->max_row_h + 16 <= 256 && !std::getenv("MXE_NEIGHBOR_COUNT")) {
+  if (staged && try_direct) {
     stride = (c->max_row_h + 16 + 3) & ~3;
     if ((int64_t)n * stride > c->rows_cap) {
       dfree(c->rows_tmp);
@@ -537,17 +551,38 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
       CK(dalloc(&c->brows_tmp, (int64_t)n * stride));
       c->rows_cap = (int64_t)n * stride;
     }
+    const bool pi = has_pair_index(c);
+    // a stencil above cand_cap is cut and reported in max_row[2] (not in the
+    // context's flags): the check below then discards this fill
     CK(TIMED("build_fill", launch_cell_fill_direct(s->q, c->qf, s->sublattice, s->mobile_mask, n, ncell, g, B,
                                                    c->cell_start, c->cell_sites, c->abs_cell, rl2, rb2, band, cand_cap,
                                                    stride, c->rows_tmp, c->brows_tmp, c->nb_cnt, c->bd_cnt,
-                                                   c->max_row, c->flags, st)));
+                                                   pi ? c->n_below : nullptr, pi ? c->pair_cnt : nullptr,
+                                                   c->max_row, c->max_row + 2, st)));
     CK(TIMED("build_misc", launch_scan(c->nb_cnt, c->nb_off, n, c->totals + 1, (int*)c->scan_tmp, c->scan_len, st)));
     CK(TIMED("build_misc", launch_scan(c->bd_cnt, c->bd_off, n, c->totals + 2, (int*)c->scan_tmp, c->scan_len, st)));
-    CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 3, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->ints_h, c->max_row, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (pi)
+      CK(TIMED("build_misc", launch_scan(c->pair_cnt, c->pair_off, n, c->totals + 3, (int*)c->scan_tmp, c->scan_len, st)));
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(long long) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->ints_h, c->max_row, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    direct = c->ints_h[0] <= stride;  // else a row did not fit: count + fill
+    const int cand_true = std::max(c->ints_h[1], 1);
+    // else a row did not fit, or the stencil did not: count + fill
+    direct = c->ints_h[0] <= stride && cand_true <= cand_cap;
+    if (cand_true > cand_cap) {
+      cand_cap = cand_true;
+      staged = cell_stage_bytes(cand_cap, 256, true) <= 64 * 1024;
+    }
+    c->cand_cap_prev = cand_true;  // the next guess starts from the true size, not from this guess
     if (!direct) CK(cudaMemsetAsync(c->max_row, 0, sizeof(int), st));
+  } else if (try_direct) {  // the guessed size did not fit shared memory: take the true one
+    CK(cudaMemcpyAsync(c->ints_h + 2, c->max_row + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cand_cap = std::max(c->ints_h[2], 1);
+    staged = cell_stage_bytes(cand_cap, 256, true) <= 64 * 1024;
+    c->cand_cap_prev = cand_cap;
+  } else {
+    c->cand_cap_prev = cand_cap;  // the true size (read above)
   }
   if (direct) {
     // counts, offsets and totals are in place
@@ -576,12 +611,10 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
     c->nb_cap = cap;
   }
   const bool pairs = has_pair_index(c);
-  if (pairs && (npairs > c->pair_cap || !c->pid)) {
-    dfree(c->pid);
+  if (pairs && (npairs > c->pair_cap || !c->pair_rec)) {
     dfree(c->pair_rec);
     dfree(c->pair_buf);
     const int64_t cap = std::max<int64_t>(c->nb_cap, npairs);
-    CK(dalloc(&c->pid, cap));
     CK(dalloc(&c->pair_rec, cap / 2 + 64));
     CK(dalloc(&c->pair_buf, cap * (int64_t)pair_record_len(c->dp)));  // one record per entry
     dfree(c->ent_dens);
@@ -614,15 +647,19 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
   }
   if (pairs) {
     if (npairs % 2) return MXE_ERR_NBR_OVERFLOW;  // a symmetric list has every pair twice
-    CK(TIMED("build_misc", launch_pair_count(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_cnt, st)));
-    CK(TIMED("build_misc", launch_scan(c->pair_cnt, c->pair_off, n, c->totals + 3, (int*)c->scan_tmp, c->scan_len, st)));
-    CK(TIMED("build_misc", launch_pair_fill(c->nb_off, c->nb_ent, n, c->first_gt, c->pair_off, npairs / 2,
-                                            c->pair_rec, c->pid, c->flags, st)));
-    // every pair record is written only if each row's tail owns exactly half
-    // of the entries (a symmetric list): check before any pair kernel runs
-    CK(cudaMemcpyAsync(c->totals_h + 3, c->totals + 3, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    // every pair record is written only if the rows' tails own exactly half
+    // of the entries (a symmetric list): checked before any pair kernel runs.
+    // The fill without a count pass counted heads and tails already (their
+    // total came with the list's); otherwise count them from the rows.
+    if (!direct) {
+      CK(TIMED("build_misc", launch_pair_count(c->nb_off, c->nb_ent, n, c->n_below, c->pair_cnt, st)));
+      CK(TIMED("build_misc", launch_scan(c->pair_cnt, c->pair_off, n, c->totals + 3, (int*)c->scan_tmp, c->scan_len, st)));
+      CK(cudaMemcpyAsync(c->totals_h + 3, c->totals + 3, sizeof(long long), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
     if (c->totals_h[3] != npairs / 2) return MXE_ERR_NBR_OVERFLOW;
+    CK(TIMED("build_misc", launch_pair_fill(c->nb_off, c->nb_ent, n, c->n_below, c->pair_off, npairs / 2,
+                                            c->pair_rec, c->flags, st)));
     c->n_upairs = npairs / 2;
   }
   CK(copy_d2d(c->q_build, s->q, sizeof(double) * 3 * n, st));
@@ -640,7 +677,7 @@ mxe_status build_lists(mxe_ctx* c, const mxe_state* s, double skin, double r_bon
 
 // The force passes run on the half list: pair index and relaxation records
 // present (the records are allocated by the first relaxation).
-bool half_list_forces(const mxe_ctx* c) { return has_pair_index(c) && c->pid && c->ent_dens && c->ent_frc; }
+bool half_list_forces(const mxe_ctx* c) { return has_pair_index(c) && c->pair_rec && c->ent_dens && c->ent_frc; }
 
 EmbArgs emb_args(mxe_ctx* c) {
   EmbArgs E;
@@ -694,7 +731,7 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
   cudaStream_t st = c->stream;
   const int prec = c->precision;
   const bool fp32 = prec != MXE_FP64;
-  const bool hl = has_pair_index(c) && c->pid;
+  const bool hl = has_pair_index(c) && c->pair_rec;
   // with the exact embedding average the pair passes run without embedding
   const DevPot& PP = c->embedding ? c->dp_pair : c->dp;
   if (fp32)
@@ -789,7 +826,7 @@ void relax_pass_args(mxe_ctx* c, const mxe_state* s, PassArgs& A) {
 // the first relaxation of a context with a pair index (outside any stream
 // capture) and kept, resized with the lists, from then on.
 mxe_status ensure_relax_records(mxe_ctx* c) {
-  if (!has_pair_index(c) || !c->pid) return MXE_OK;
+  if (!has_pair_index(c) || !c->pair_rec) return MXE_OK;
   c->relax_records = true;
   if (c->ent_dens && c->ent_frc) return MXE_OK;
   dfree(c->ent_dens);
@@ -846,7 +883,6 @@ mxe_status enqueue_fire_iter(mxe_ctx* c, mxe_state* s, const PassArgs& A) {
                                                    c->grid, c->B, c->sf, p32, c->ctrl, st)));
   } else {
     CK(TIMED("fire_reduce", launch_fire_reduce(c->gq, c->gs, s->sigma, c->vq, c->vs, n, c->partials, c->ctrl, c->flags, st)));
-    CK(TIMED("fire_logic", launch_fire_logic(c->partials, n, c->ctrl, c->flags, st)));
     CK(TIMED("fire_update", launch_fire_update(s->q, s->sigma, c->vq, c->vs, c->gq, c->gs, c->q_build, c->abs_cell, n,
                                                c->grid, c->B, p32, c->ctrl, st)));
   }
@@ -1274,7 +1310,7 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
   A(dalloc(&c->nb_off, n + 1));
   A(dalloc(&c->bd_off, n + 1));
   A(dalloc(&c->totals, 4));
-  A(dalloc(&c->max_row, 2));
+  A(dalloc(&c->max_row, 4));  // longest row, largest stencil, flags of a fill that may be discarded
   A(dalloc(&c->smax_bits, 2));
   A(dalloc(&c->qf, 2 * n));
   A(dalloc(&c->q_build, 3 * n));
@@ -1289,7 +1325,7 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
     A(dalloc(&c->ab32, 2 * n));
   }
   if (has_pair_index(c)) {
-    A(dalloc(&c->first_gt, n));
+    A(dalloc(&c->n_below, n));
     A(dalloc(&c->pair_cnt, n));
     A(dalloc(&c->pair_off, n + 1));
     if (precision != MXE_FP64) {
@@ -1303,7 +1339,7 @@ mxe_status mxe_create_batch(mxe_ctx** out, int32_t n_systems, const mxe_box* box
   A(dalloc(&c->gs, n));
   A(dalloc(&c->mu_ex, S * n));
   A(dalloc(&c->site_E, 3 * n));
-  A(dalloc(&c->partials, 3 * ((n + kReduceGroup - 1) / kReduceGroup + 1)));
+  A(dalloc(&c->partials, 3 * ((n + kFireGroup - 1) / kFireGroup + 1)));  // FIRE and energy partial sums (kFireGroup <= kReduceGroup)
   A(dalloc(&c->F4_tmp, 4));
   A(dalloc(&c->vq, 3 * n));
   A(dalloc(&c->vs, n));
@@ -1376,11 +1412,10 @@ mxe_status mxe_destroy(mxe_ctx* c) {
   dfree(c->tan_buf);
   dfree(c->emb_buf);
   dfree(c->emb_nrule);
-  dfree(c->first_gt);
+  dfree(c->n_below);
   dfree(c->pair_cnt);
   dfree(c->pair_off);
   dfree(c->pair_rec);
-  dfree(c->pid);
   dfree(c->pair_buf);
   dfree(c->rows_tmp);
   dfree(c->brows_tmp);

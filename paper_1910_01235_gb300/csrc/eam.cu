@@ -842,11 +842,12 @@ __global__ void __launch_bounds__(256, MXE_GRADIENT_MIN_BLOCKS) k_gradient(DevPo
 // The averages <phi_u>_ij, <f_v>_ij and the static f_v(r_ij) of a pair depend
 // only on its geometry and are the same from both ends (the node set of
 // App. A is symmetric in i and j).  k_pair_geo evaluates them once per
-// unordered pair (one thread per pair) into a record of C values:
+// unordered pair (one thread per pair) into a record of C values, written
+// to both entries of the pair:
 // [f_v static (n_f) | sum over the 12 nodes of f_v (n_f) | of phi_u (n_phi)];
 // k_pair_density / k_pair_mu gather the records over every site's full row
-// (entry t -> pair pid[t]) and finish exactly as the density and
-// chemical-potential passes do.  Node arithmetic R: float-float (records of
+// in row order and finish exactly as the density and chemical-potential
+// passes do.  Node arithmetic R: float-float (records of
 // float pairs; the FP32 modes) or FP64 (records of doubles).
 // The record of unordered pair p: owner site i, the entry of j in row i (j with
 // its image code), that entry's index tp and the index tr of the reverse

@@ -105,8 +105,10 @@ struct FFExpTable {
   float hi[32], lo[32];
 };
 
-// exp(x) for |x| <~ 80 (inputs of the radial terms are far smaller).
-// tab(j) returns 2^(j/32) as a float pair.
+// exp(x) for |x| < 87 (inputs of the radial terms are far smaller).
+// tab(j) returns 2^(j/32) as a float pair.  The absolute error of the reduced
+// argument r is the relative error of the result, so r is formed to about
+// 1e-16 and exp(r) to about 1e-14.
 template <typename Tab>
 __device__ __forceinline__ ff ff_exp_t(ff x, const Tab& tab) {
   // ln2/32 = c1 + c2 + c3: c1 has 12 significant bits, so n * c1 is exact for
@@ -119,24 +121,32 @@ __device__ __forceinline__ ff ff_exp_t(ff x, const Tab& tab) {
   const int ni = (int)n;
   const int j = ni & 31;
   const int m = (ni - j) / 32;
-  // r = x - n ln2/32 in float-float
-  ff r = ff_add_f(x, -n * c1);  // n * c1 exact
-  r = r + two_prod(-n, c2);
-  r = ff_add_f(r, -n * c3);
-  // exp(r) = 1 + r + r^2/2 + r^3 (1/6 + r/24 + r^2/120 + r^3/720), |r| <= ln2/64:
-  // the cubic tail is below 2.2e-7, so evaluating it in FP32 from r.hi costs
-  // under 1e-14 relative; the first three terms are kept as float pairs.
+  // r = x - n ln2/32.  x.hi - n c1 is exact: n c1 is, and for n != 0 the two
+  // lie within a factor of two of each other (Sterbenz).  n c2 is split
+  // exactly by TwoProduct; x.lo (up to 2e-6) and -n c2 enter by TwoSum, and
+  // the remaining pieces are below 1e-9.
+  const float s = fmaf(-n, c1, x.hi);
+  const ff p2 = two_prod(n, c2);
+  const ff t = two_sum(s, -p2.hi);
+  const ff u = two_sum(t.hi, x.lo);
+  const ff r = fast_two_sum(u.hi, (t.lo + u.lo) - (p2.lo + n * c3));
+  // exp(r) = 1 + r + r^2/2 + r^3 (1/6 + r/24 + r^2/120 + r^3/720), |r| <= ln2/64.
+  // The cubic tail (below 2.2e-7) in FP32 from r.hi; r^2/2 from TwoProduct
+  // plus the cross term; r + r^2/2 by Fast2Sum (|r| > r^2/2); every remaining
+  // piece is below 3e-7, so one float sums them to about 1e-14.
   const float q = r.hi;
-  const float tail = q * q * q * fmaf(fmaf(fmaf(q, 1.0f / 720.0f, 1.0f / 120.0f), q, 1.0f / 24.0f), q, 1.0f / 6.0f);
-  ff r2 = r * r;
-  r2.hi *= 0.5f;
-  r2.lo *= 0.5f;
-  ff p = ff_add_f(r2, tail) + r;
-  p = ff_add_f(p, 1.0f);
-  const ff t = tab(j);
-  p = p * t;
-  const float sc = ldexpf(1.0f, m);
-  return ff{p.hi * sc, p.lo * sc};
+  const float q2 = q * q;
+  const float tail = q2 * q * fmaf(fmaf(fmaf(q, 1.0f / 720.0f, 1.0f / 120.0f), q, 1.0f / 24.0f), q, 1.0f / 6.0f);
+  const float e2 = fmaf(q, q, -q2) + 2.0f * q * r.lo;  // r^2 = q2 + e2 (to 1e-19)
+  const ff s1 = fast_two_sum(q, 0.5f * q2);
+  const float small = ((s1.lo + r.lo) + 0.5f * e2) + tail;
+  ff pe = fast_two_sum(1.0f, s1.hi);
+  pe = fast_two_sum(pe.hi, pe.lo + small);
+  const ff pt = pe * tab(j);
+  // 2^m by its exponent bits (|m| <= 126 for |x| < 87; clamped to the normal
+  // range beyond)
+  const float sc = __int_as_float((min(max(m, -126), 127) + 127) << 23);
+  return ff{pt.hi * sc, pt.lo * sc};
 }
 
 // with the table in constant memory (uniform indices are broadcast, distinct

@@ -16,6 +16,7 @@ constexpr int kMaxFFn = MXE_MAXS * MXE_MAXS;              // distinct density te
 constexpr int kCodeShift = 27;                            // neighbour entry: j | image code << 27
 constexpr uint32_t kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kReduceGroup = 1024;                        // sites per fixed-order partial sum
+constexpr int kFireGroup = 256;                           // sites per partial sum of the FIRE reduction
 constexpr double kKB = 8.617333262e-5;                    // eV/K
 constexpr double kSqrt6 = 2.449489742783178098197284;     // node offset / sigma (App. A, r^2 = 3)
 constexpr double kRMin = 0.5;                             // smallest admissible node distance
@@ -132,7 +133,7 @@ struct Ctrl {
   // staggered runs captured in a graph
   int phase;          // 0: before the Euler step of the current step, 1: after it
   int steps;          // completed steps
-  int pad;
+  unsigned int red_ticket;  // blocks of the current FIRE reduction done (0 between launches)
 };
 
 enum { kReasonNone = 0, kReasonConverged = 1, kReasonMaxIter = 2, kReasonRebuild = 3, kReasonError = 4,
@@ -175,25 +176,26 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
                              const int* abs_cell, double rl2, double rb2, float band, int cand_cap,
                              const int* nb_off, uint32_t* nb_ent, const int* bd_off, int* bd_idx, int max_row,
                              int* flags, cudaStream_t s);
-// unordered-pair index of a symmetric list: first_gt[i] = first entry of row i
-// with j > i, cnt[i] = entries from there to the row's end; after a scan of
-// cnt into pair_off: pair p has the record pair_rec[p] = (i, entry of j in row
-// i with its image code, that entry's index, the index of the reverse entry),
-// and pid[t] = the pair of every entry t (kFlagOverflow if the list is not
-// symmetric)
-cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* first_gt, int* cnt,
+// unordered-pair index of a symmetric list (rows sorted by j): n_below[i] =
+// entries of row i with j < i (the head), cnt[i] = the rest (the tail, the
+// pairs row i owns); after a scan of cnt into pair_off, pair p has the record
+// pair_rec[p] = (i, entry of j in row i with its image code, that entry's
+// index, the index of the reverse entry i in row j) (kFlagOverflow if the
+// list is not symmetric)
+cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* n_below, int* cnt,
                               cudaStream_t s);
-cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
-                             const int* pair_off, int64_t npair, int4* pair_rec, int* pid, int* flags,
-                             cudaStream_t s);
+cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* n_below,
+                             const int* pair_off, int64_t npair, int4* pair_rec, int* flags, cudaStream_t s);
 // fill without a count pass: rows at a fixed stride (the previous build's
 // longest row plus a margin), counts and the longest row; then the scan of the
-// counts and the compaction into the CSR (a longer row: count + fill instead)
+// counts and the compaction into the CSR (a longer row: count + fill instead);
+// with n_below / pair_cnt (may be null) also the half-list index's head and
+// tail lengths of every row
 cudaError_t launch_cell_fill_direct(const double* q, const float4* qf, const uint8_t* sub, uint32_t mobile_mask,
                                     int64_t n, int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start,
                                     const int* cell_sites, const int* abs_cell, double rl2, double rb2, float band,
                                     int cand_cap, int stride, uint32_t* rows, int* brows, int* nb_cnt, int* bd_cnt,
-                                    int* row_max, int* flags, cudaStream_t s);
+                                    int* n_below, int* pair_cnt, int* row_max, int* flags, cudaStream_t s);
 cudaError_t launch_row_compact(const uint32_t* rows, const int* brows, int stride, int64_t n, const int* nb_off,
                                const int* bd_off, uint32_t* nb_ent, int* bd_idx, cudaStream_t s);
 // exclusive scan of n int32 counts into out[0..n] (out[n] = total, int64 total in *total64)
@@ -296,7 +298,6 @@ cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, d
 // relax.cu
 cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
                                const double* vs, int64_t n, double* partials, Ctrl* ctrl, int* flags, cudaStream_t s);
-cudaError_t launch_fire_logic(const double* partials, int64_t n, Ctrl* ctrl, int* flags, cudaStream_t s);
 cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
                                const double* gs, const double* q_build, const int* abs_cell, int64_t n,
                                const DevGrid& g, const Batch& B, float4* pos32, Ctrl* ctrl, cudaStream_t s);

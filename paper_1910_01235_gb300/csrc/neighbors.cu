@@ -11,7 +11,8 @@
 // of |d|^2; outside it the FP32 and FP64 decisions agree).
 // One warp handles one site: lanes sweep the candidates of the distinct
 // neighbouring cells, accepted entries are compacted into shared memory with
-// ballots and placed in j order by rank counting.  Each entry stores j in the
+// ballots and placed in j order (a bitonic sort in registers; rank counting
+// for rows longer than 128).  Each entry stores j in the
 // low 27 bits and the periodic image code (cell offset in {-1,0,1}^3) above it,
 // which the FP32 kernels use to rebuild d from cell-relative positions.
 #include <cuda_runtime.h>
@@ -398,6 +399,69 @@ __device__ __forceinline__ CandResult test_cand_rel(int64_t i, const double qi[3
   return r;
 }
 
+// Row order by a bitonic sort in registers: KPL keys per lane (32 KPL >= m),
+// element e = 32 h + lane in register h.  A key packs the entry's j, its image
+// code and its bond flag, (j << 6) | (code << 1) | bond, so the sort by key is
+// the sort by j (j is unique in a row); it needs j < 2^26.  Pads (e >= m) are
+// 0xFFFFFFFF and sort last.  The sorted entries go to ent_out[0, m) and the
+// bonds, in the same order, to bond_out (ballot-compacted).
+constexpr int64_t kSortKeySites = (int64_t)1 << 26;
+
+template <int KPL>
+__device__ __forceinline__ void warp_sort_row(const uint32_t* __restrict__ buf, const uint32_t* __restrict__ kw, int m,
+                                              int lane, uint32_t* __restrict__ ent_out,
+                                              int* __restrict__ bond_out) {
+  uint32_t v[KPL];
+#pragma unroll
+  for (int h = 0; h < KPL; ++h) {
+    const int e = 32 * h + lane;
+    v[h] = 0xFFFFFFFFu;
+    if (e < m) {
+      const uint32_t ent = buf[e];
+      v[h] = ((ent & kIdxMask) << 6) | ((ent >> kCodeShift) << 1) | (kw[e] & 1u);
+    }
+  }
+#pragma unroll
+  for (int k = 2; k <= 32 * KPL; k <<= 1) {
+#pragma unroll
+    for (int s = k >> 1; s > 0; s >>= 1) {
+      if (s >= 32) {
+        // partner in the same lane, register h ^ (s / 32)
+#pragma unroll
+        for (int h = 0; h < KPL; ++h) {
+          const int hp = h ^ (s / 32);
+          if (hp > h) {
+            const bool asc = ((32 * h + lane) & k) == 0;
+            const uint32_t lo = min(v[h], v[hp]), hi = max(v[h], v[hp]);
+            v[h] = asc ? lo : hi;
+            v[hp] = asc ? hi : lo;
+          }
+        }
+      } else {
+        const bool lower = (lane & s) == 0;
+#pragma unroll
+        for (int h = 0; h < KPL; ++h) {
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, v[h], s);
+          const bool asc = ((32 * h + lane) & k) == 0;
+          v[h] = (asc == lower) ? min(v[h], o) : max(v[h], o);
+        }
+      }
+    }
+  }
+  int nb = 0;
+#pragma unroll
+  for (int h = 0; h < KPL; ++h) {
+    const int e = 32 * h + lane;
+    const uint32_t key = v[h];
+    const uint32_t j = key >> 6;
+    if (e < m) ent_out[e] = j | (((key >> 1) & 31u) << kCodeShift);
+    const bool bond = e < m && (key & 1u);
+    const unsigned bm = __ballot_sync(0xffffffffu, bond);
+    if (bond) bond_out[nb + __popc(bm & ((1u << lane) - 1u))] = (int)j;
+    nb += __popc(bm);
+  }
+}
+
 __global__ void __launch_bounds__(kCellThreads) k_cell_count(
     const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
     int64_t n, DevGrid g0, Batch B, const int* __restrict__ cell_start, const int* __restrict__ cell_sites, double rl2,
@@ -459,7 +523,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     const int* __restrict__ abs_cell, double rl2, double rb2, float band, int cand_cap,
     const int* __restrict__ nb_off, uint32_t* __restrict__ nb_ent, const int* __restrict__ bd_off,
     int* __restrict__ bd_idx, int max_row, int* __restrict__ nb_cnt, int* __restrict__ bd_cnt,
-    int* __restrict__ row_max, int* __restrict__ flags) {
+    int* __restrict__ n_below, int* __restrict__ pair_cnt, int* __restrict__ row_max, int* __restrict__ flags) {
   extern __shared__ unsigned char smem[];
   __shared__ int s_off[28], s_beg[27];
   __shared__ float s_sh[27 * 3];
@@ -490,7 +554,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     const float4 qfi = cs.fast ? qf[n + i] : qf[i];
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
-    int m = 0, nbond = 0;
+    int m = 0, nbond = 0, nlow = 0;
     for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
       const int t = t0 + lane;
       CandResult r{false, false, {0.f, 0.f, 0.f}};
@@ -521,19 +585,38 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
         }
       }
       m += __popc(msk);
-      if (DIRECT) nbond += __popc(__ballot_sync(0xffffffffu, r.bond));
+      if (DIRECT) {
+        nbond += __popc(__ballot_sync(0xffffffffu, r.bond));
+        if (n_below) nlow += __popc(__ballot_sync(0xffffffffu, r.in && (int64_t)j < i));
+      }
     }
     if (DIRECT && lane == 0) {
       nb_cnt[i] = m;
       bd_cnt[i] = nbond;
+      if (n_below) {  // the half-list index: entries below i, pairs owned by i
+        n_below[i] = nlow;
+        pair_cnt[i] = m - nlow;
+      }
       atomicMax(&s_rowmax, m);
     }
     if (m > max_row) m = max_row;  // count + fill: cannot happen (max_row is the counted maximum)
-    const int m4 = (m + 3) >> 2;
-    for (int e = m + lane; e < 4 * m4; e += 32) kw[e] = 0xFFFFFFFFu;  // pads rank after every key
     __syncwarp();
     const int64_t off = DIRECT ? i * (int64_t)max_row : (int64_t)nb_off[i];
     const int64_t boff = DIRECT ? i * (int64_t)max_row : (int64_t)bd_off[i];
+    if (m <= 64 && n <= kSortKeySites) {
+      warp_sort_row<2>(buf, kw, m, lane, nb_ent + off, bd_idx + boff);
+      __syncwarp();
+      continue;
+    }
+    if (m <= 128 && n <= kSortKeySites) {
+      warp_sort_row<4>(buf, kw, m, lane, nb_ent + off, bd_idx + boff);
+      __syncwarp();
+      continue;
+    }
+    // longer rows: rank counting against the row
+    const int m4 = (m + 3) >> 2;
+    for (int e = m + lane; e < 4 * m4; e += 32) kw[e] = 0xFFFFFFFFu;  // pads rank after every key
+    __syncwarp();
     const uint4* k4 = reinterpret_cast<const uint4*>(kw);
     for (int e = lane; e < m; e += 32) {
       const uint32_t ke = kw[e] & ~1u;  // j << 1: keys of smaller j are below it
@@ -688,54 +771,51 @@ __device__ __forceinline__ int first_above(const uint32_t* __restrict__ ent, int
   return lo;
 }
 
+// n_below[i]: the length of row i's head (entries below i); cnt[i]: of its tail
 __global__ void k_pair_count(const int* __restrict__ nb_off, const uint32_t* __restrict__ nb_ent, int64_t n,
-                             int* __restrict__ first_gt, int* __restrict__ cnt) {
+                             int* __restrict__ n_below, int* __restrict__ cnt) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int beg = nb_off[i], end = nb_off[i + 1];
   const int fg = first_above(nb_ent, beg, end, (uint32_t)i);
-  first_gt[i] = fg;
+  n_below[i] = fg - beg;
   cnt[i] = end - fg;
 }
 
 // Pair records rec[p] = (i, entry of j in row i with its image code, that
-// entry's index, the index of the reverse entry i in row j): the owner branch
-// writes the first three words, the row of the other end the fourth.
+// entry's index, the index of the reverse entry i in row j): one warp per row
+// i, lanes over the row's tail (the pairs it owns); the reverse entry is
+// found by binary search in the head of row j (its entries below j, where i
+// lies since i < j), and the lane writes the whole record with one store.
+__device__ __forceinline__ int first_not_below(const uint32_t* __restrict__ ent, int beg, int end, uint32_t i) {
+  int lo = beg, hi = end;  // first t in [beg, end) with (ent[t] & mask) >= i
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((ent[mid] & kIdxMask) >= i) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 __global__ void k_pair_fill(const int* __restrict__ nb_off, const uint32_t* __restrict__ nb_ent, int64_t n,
-                            const int* __restrict__ first_gt, const int* __restrict__ pair_off, int64_t npair,
-                            int* __restrict__ rec, int* __restrict__ pid, int* __restrict__ flags) {
-  // one warp per row, lanes over its entries
+                            const int* __restrict__ n_below, const int* __restrict__ pair_off, int64_t npair,
+                            int4* __restrict__ rec, int* __restrict__ flags) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w == 0 && lane == 0 && pair_off[n] != npair) atomicOr(flags, kFlagOverflow);  // lists must be symmetric
   if (w >= n) return;
   const int64_t i = w;
-  const int beg = nb_off[i], end = nb_off[i + 1], fg = first_gt[i];
-  for (int t = beg + lane; t < end; t += 32) {
+  const int end = nb_off[i + 1], fg = nb_off[i] + n_below[i], p0 = pair_off[i];
+  for (int t = fg + lane; t < end; t += 32) {
     const uint32_t e = nb_ent[t];
     const int64_t j = e & kIdxMask;
-    if (t >= fg) {
-      const int p = pair_off[i] + (t - fg);
-      if (p < npair) {
-        rec[4 * (int64_t)p] = (int)i;
-        rec[4 * (int64_t)p + 1] = (int)e;
-        rec[4 * (int64_t)p + 2] = t;
-        pid[t] = p;
-      } else {
-        pid[t] = 0;
-        atomicOr(flags, kFlagOverflow);
-      }
+    const int p = p0 + (t - fg);
+    const int jb = nb_off[j], jh = jb + n_below[j];
+    const int tr = first_not_below(nb_ent, jb, jh, (uint32_t)i);
+    if (p < npair && tr < jh && (nb_ent[tr] & kIdxMask) == (uint32_t)i) {
+      rec[p] = make_int4((int)i, (int)e, t, tr);
     } else {
-      // the pair's owner entry: i in row j (j < i), in the tail of row j
-      const int jb = first_gt[j], je = nb_off[j + 1];
-      const int t2 = first_above(nb_ent, jb, je, (uint32_t)i) - 1;
-      if (t2 >= jb && (nb_ent[t2] & kIdxMask) == (uint32_t)i && pair_off[j] + (t2 - jb) < npair) {
-        pid[t] = pair_off[j] + (t2 - jb);
-        rec[4 * (int64_t)(pair_off[j] + (t2 - jb)) + 3] = t;
-      } else {
-        pid[t] = 0;
-        atomicOr(flags, kFlagOverflow);
-      }
+      atomicOr(flags, kFlagOverflow);
     }
   }
 }
@@ -839,7 +919,7 @@ cudaError_t launch_cell_fill(const double* q, const float4* qf, const uint8_t* s
   k_cell_fill<false><<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start,
                                                                 cell_sites, abs_cell, rl2, rb2, band, cand_cap, nb_off,
                                                                 nb_ent, bd_off, bd_idx, max_row, nullptr, nullptr,
-                                                                nullptr, flags);
+                                                                nullptr, nullptr, nullptr, flags);
   return cudaGetLastError();
 }
 
@@ -847,15 +927,15 @@ cudaError_t launch_cell_fill_direct(const double* q, const float4* qf, const uin
                                     int64_t n, int64_t ncell, const DevGrid& g, const Batch& B, const int* cell_start,
                                     const int* cell_sites, const int* abs_cell, double rl2, double rb2, float band,
                                     int cand_cap, int stride, uint32_t* rows, int* brows, int* nb_cnt, int* bd_cnt,
-                                    int* row_max, int* flags, cudaStream_t s) {
+                                    int* n_below, int* pair_cnt, int* row_max, int* flags, cudaStream_t s) {
   if (n == 0 || ncell == 0) return cudaSuccess;
   const size_t shm = cell_stage_bytes(cand_cap, stride, true);
   cudaError_t e = cudaFuncSetAttribute(k_cell_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
   k_cell_fill<true><<<(unsigned)ncell, kCellThreads, shm, s>>>(q, qf, sub, mobile_mask, n, g, B, cell_start,
                                                                cell_sites, abs_cell, rl2, rb2, band, cand_cap, nullptr,
-                                                               rows, nullptr, brows, stride, nb_cnt, bd_cnt, row_max,
-                                                               flags);
+                                                               rows, nullptr, brows, stride, nb_cnt, bd_cnt, n_below,
+                                                               pair_cnt, row_max, flags);
   return cudaGetLastError();
 }
 
@@ -901,19 +981,18 @@ cudaError_t launch_segment_ids(const int* base, int nseg, int64_t count, int* ou
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* first_gt, int* cnt,
+cudaError_t launch_pair_count(const int* nb_off, const uint32_t* nb_ent, int64_t n, int* n_below, int* cnt,
                               cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_pair_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, first_gt, cnt);
+  k_pair_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, n_below, cnt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* first_gt,
-                             const int* pair_off, int64_t npair, int4* pair_rec, int* pid, int* flags,
-                             cudaStream_t s) {
+cudaError_t launch_pair_fill(const int* nb_off, const uint32_t* nb_ent, int64_t n, const int* n_below,
+                             const int* pair_off, int64_t npair, int4* pair_rec, int* flags, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_pair_fill<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, first_gt, pair_off, npair,
-                                                               (int*)pair_rec, pid, flags);
+  k_pair_fill<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(nb_off, nb_ent, n, n_below, pair_off, npair,
+                                                               pair_rec, flags);
   return cudaGetLastError();
 }
 

@@ -5,9 +5,10 @@
 // One iteration is: density pass, gradient pass (eam.cu), then
 //   k_fire_reduce : per fixed group of sites, P = f.v, |v|^2, |f|^2 partial sums;
 //                   max_i max(|g_q,i|, |g_sigma,i|) by an atomic max on the bit
-//                   patterns of non-negative doubles (order independent);
-//   k_fire_logic  : one block sums the partials in a fixed order, tests
-//                   convergence / the iteration cap, and advances dt, alpha, n_pos;
+//                   patterns of non-negative doubles (order independent); the
+//                   launch's last block then sums the partials in a fixed
+//                   order, tests convergence / the iteration cap, and advances
+//                   dt, alpha, n_pos;
 //   k_fire_update : v = (1 - alpha)(keep v + dt f) + alpha |v'| f / |f|,
 //                   y += dt v, sigma kept in [sigma_lo, sigma_hi] (velocity
 //                   zeroed at a bound), and the maxima the skin test needs.
@@ -23,7 +24,9 @@
 namespace mxe {
 namespace {
 
-constexpr int kRedThreads = kReduceGroup / 4;
+// FIRE reduction: one site per thread, kFireGroup sites per partial sum
+// (many small blocks keep the SMs busy on a pass this short)
+constexpr int kRedThreads = kFireGroup;
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   unsigned long long b = __double_as_longlong(v);
@@ -35,6 +38,24 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
   if ((threadIdx.x & 31) == 0) atomicMax(addr, b);
 }
 
+// The block's maximum of non-negative doubles, then one atomic per block (a
+// global atomic per warp serialises thousands of updates of one word).
+// Every thread of the block must call it.
+__device__ __forceinline__ void block_max_nonneg(unsigned long long* addr, double v) {
+  __shared__ unsigned long long s_max;
+  if (threadIdx.x == 0) s_max = 0ull;
+  __syncthreads();
+  unsigned long long b = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+    b = y > b ? y : b;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_max, b);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_max) atomicMax(addr, s_max);
+}
+
 // force on sigma projected on the box [lo, hi]: zero where a bound blocks it
 __device__ __forceinline__ double proj_fsig(double gs, double sigma, double lo, double hi) {
   const double f = -gs;
@@ -43,61 +64,22 @@ __device__ __forceinline__ double proj_fsig(double gs, double sigma, double lo, 
   return f;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_fire_reduce(const double* __restrict__ gq,
-                                                             const double* __restrict__ gs,
-                                                             const double* __restrict__ sigma,
-                                                             const double* __restrict__ vq,
-                                                             const double* __restrict__ vs, int64_t n,
-                                                             int64_t ngroups, double* __restrict__ partials,
-                                                             Ctrl* __restrict__ ctrl, int* __restrict__ flags) {
-  if (ctrl->halted) return;
-  __shared__ double sh[3][kRedThreads];
-  const int tid = threadIdx.x;
-  const double lo = ctrl->sigma_lo, hi = ctrl->sigma_hi;
-  double P = 0.0, vv = 0.0, ff = 0.0, fm = 0.0;
-  bool finite = true;
-  for (int r = 0; r < 4; ++r) {
-    int64_t i = blockIdx.x * (int64_t)kReduceGroup + r * kRedThreads + tid;
-    if (i >= n) continue;
-    double g0 = gq[i], g1 = gq[n + i], g2 = gq[2 * n + i];
-    double f3 = proj_fsig(gs[i], sigma[i], lo, hi);
-    double v0 = vq[i], v1 = vq[n + i], v2 = vq[2 * n + i], v3 = vs[i];
-    P += -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
-    vv += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
-    ff += g0 * g0 + g1 * g1 + g2 * g2 + f3 * f3;
-    // the largest squared force component norm; its square root is taken
-    // once, by the logic kernel (sqrt is monotone and correctly rounded, so
-    // sqrt(max) == max(sqrt))
-    fm = fmax(fm, fmax(g0 * g0 + g1 * g1 + g2 * g2, f3 * f3));
-    finite = finite && isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs[i]);
-  }
-  sh[0][tid] = P;
-  sh[1][tid] = vv;
-  sh[2][tid] = ff;
-  if (!finite) atomicOr(flags, kFlagNonfinite);
-  atomic_max_nonneg(&ctrl->fmax_bits, finite ? fm : 0.0);
-  __syncthreads();
-  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-    if (tid < w)
-      for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
-    __syncthreads();
-  }
-  if (tid == 0)
-    for (int c = 0; c < 3; ++c) partials[c * ngroups + blockIdx.x] = sh[c][0];
-}
-
-__global__ void __launch_bounds__(256) k_fire_logic(const double* __restrict__ partials, int64_t ngroups,
-                                                    Ctrl* __restrict__ ctrl, const int* __restrict__ flags) {
-  if (ctrl->halted) return;
-  __shared__ double sh[3][256];
+// The FIRE logic of one iteration, run by the last block of k_fire_reduce
+// (blockDim = kRedThreads): the partial sums in a fixed order (the same
+// result whichever block runs it), the convergence and iteration-cap tests,
+// and the advance of dt, alpha, n_pos.  Partials, the force maximum and the
+// flags are written by other blocks of the same launch, so they are read past
+// L1 (__ldcg).
+__device__ void fire_logic_block(const double* __restrict__ partials, int64_t ngroups, Ctrl* __restrict__ ctrl,
+                                 const int* __restrict__ flags, double (*sh)[kRedThreads]) {
   const int tid = threadIdx.x;
   for (int c = 0; c < 3; ++c) {
     double v = 0.0;
-    for (int64_t gi = tid; gi < ngroups; gi += 256) v += partials[c * ngroups + gi];
+    for (int64_t gi = tid; gi < ngroups; gi += kRedThreads) v += __ldcg(&partials[c * ngroups + gi]);
     sh[c][tid] = v;
   }
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
     if (tid < w)
       for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
     __syncthreads();
@@ -105,9 +87,9 @@ __global__ void __launch_bounds__(256) k_fire_logic(const double* __restrict__ p
   if (tid != 0) return;
   Ctrl& C = *ctrl;
   const double P = sh[0][0], vv = sh[1][0], ff = sh[2][0];
-  const double fmx = sqrt(__longlong_as_double((long long)C.fmax_bits));
+  const double fmx = sqrt(__longlong_as_double((long long)__ldcg(&C.fmax_bits)));
   C.fmax = fmx;
-  if (*flags & (kFlagGeometry | kFlagNonfinite)) {
+  if (__ldcg(flags) & (kFlagGeometry | kFlagNonfinite)) {
     C.halted = 1;
     C.reason = kReasonError;
     return;
@@ -148,6 +130,62 @@ __global__ void __launch_bounds__(256) k_fire_logic(const double* __restrict__ p
   C.fmax_bits = 0ull;
   C.disp2_bits = 0ull;
   C.smax_bits = 0ull;
+}
+
+// Partial sums per group of kFireGroup sites; the last block to finish
+// (a ticket counted in the control block) then runs the logic, so an
+// iteration needs no separate single-block launch.
+__global__ void __launch_bounds__(kRedThreads) k_fire_reduce(const double* __restrict__ gq,
+                                                             const double* __restrict__ gs,
+                                                             const double* __restrict__ sigma,
+                                                             const double* __restrict__ vq,
+                                                             const double* __restrict__ vs, int64_t n,
+                                                             int64_t ngroups, double* __restrict__ partials,
+                                                             Ctrl* __restrict__ ctrl, int* __restrict__ flags) {
+  if (ctrl->halted) return;  // the same for every block: nothing in this launch changes it before the logic
+  __shared__ double sh[3][kRedThreads];
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+  const double lo = ctrl->sigma_lo, hi = ctrl->sigma_hi;
+  double P = 0.0, vv = 0.0, ff = 0.0, fm = 0.0;
+  bool finite = true;
+  {
+    const int64_t i = blockIdx.x * (int64_t)kFireGroup + tid;
+    if (i < n) {
+    double g0 = gq[i], g1 = gq[n + i], g2 = gq[2 * n + i];
+    double f3 = proj_fsig(gs[i], sigma[i], lo, hi);
+    double v0 = vq[i], v1 = vq[n + i], v2 = vq[2 * n + i], v3 = vs[i];
+    P += -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
+    vv += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
+    ff += g0 * g0 + g1 * g1 + g2 * g2 + f3 * f3;
+    // the largest squared force component norm; its square root is taken
+    // once, by the logic (sqrt is monotone and correctly rounded, so
+    // sqrt(max) == max(sqrt))
+    fm = fmax(fm, fmax(g0 * g0 + g1 * g1 + g2 * g2, f3 * f3));
+    finite = finite && isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs[i]);
+    }
+  }
+  sh[0][tid] = P;
+  sh[1][tid] = vv;
+  sh[2][tid] = ff;
+  if (!finite) atomicOr(flags, kFlagNonfinite);
+  block_max_nonneg(&ctrl->fmax_bits, finite ? fm : 0.0);
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int c = 0; c < 3; ++c) sh[c][tid] += sh[c][tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int c = 0; c < 3; ++c) partials[c * ngroups + blockIdx.x] = sh[c][0];
+    __threadfence();  // partials, flags and the maximum before the ticket
+    s_last = atomicAdd(&ctrl->red_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  fire_logic_block(partials, ngroups, ctrl, flags, sh);
+  if (tid == 0) ctrl->red_ticket = 0u;
 }
 
 // One FIRE update of site i with the given scalars; returns |q - q_build|^2 and sigma.
@@ -198,8 +236,8 @@ __global__ void __launch_bounds__(256) k_fire_update(double* __restrict__ q, dou
     fire_site(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, i, g, pos32, dt, keep, mix, oma, ctrl->sigma_lo,
               ctrl->sigma_hi, disp2, sg);
   }
-  atomic_max_nonneg(&ctrl->disp2_bits, disp2);
-  atomic_max_nonneg(&ctrl->smax_bits, sg);
+  block_max_nonneg(&ctrl->disp2_bits, disp2);
+  block_max_nonneg(&ctrl->smax_bits, sg);
 }
 
 // ---------------------------------------------------------------- batches
@@ -439,16 +477,9 @@ cudaError_t launch_fire_zero_v(double* vq, double* vs, int64_t n, const Ctrl* ga
 
 cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
                                const double* vs, int64_t n, double* partials, Ctrl* ctrl, int* flags, cudaStream_t s) {
-  int64_t ng = (n + kReduceGroup - 1) / kReduceGroup;
+  int64_t ng = (n + kFireGroup - 1) / kFireGroup;
   if (ng < 1) ng = 1;
   k_fire_reduce<<<(unsigned)ng, kRedThreads, 0, s>>>(gq, gs, sigma, vq, vs, n, ng, partials, ctrl, flags);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fire_logic(const double* partials, int64_t n, Ctrl* ctrl, int* flags, cudaStream_t s) {
-  int64_t ng = (n + kReduceGroup - 1) / kReduceGroup;
-  if (ng < 1) ng = 1;
-  k_fire_logic<<<1, 256, 0, s>>>(partials, ng, ctrl, flags);
   return cudaGetLastError();
 }
 

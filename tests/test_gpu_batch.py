@@ -284,9 +284,10 @@ def test_graph_run_matches_step_by_step_calls(prec):
     b.build_neighbors()
     st, done = b.run_staggered(steps, dt, 0.0, K)
     assert st == M.OK and done == steps
-    # every step of the run from one graph launch (a device-side loop)
+    # every step of the run from one graph launch (a device-side loop); per
+    # FIRE iteration at least the four force passes, the reduction and the update
     launches, kernels = b.run_stats()
-    assert launches == 1 and kernels >= 7 * (K + 1)
+    assert launches == 1 and kernels >= 6 * (K + 1)
     dx = (a.x - b.x).abs().max().item()
     dq = (a.q - b.q).abs().max().item()
     ds = (a.sigma - b.sigma).abs().max().item()
