@@ -149,9 +149,11 @@ def ops_per_pair(kernel, n_phi, n_f, S):
         static = 2 + 11 + 4 * n_f + 1
         pair = 20 + S * S + 4 * S * S + (n_phi + n_f) + 9 + 24
         return 12 * node + static + pair
-    # float-float passes (csrc/ff.cuh): add 11, mul 7, exp 95 FP32 operations; per
-    # radial term at a node: argument 18 + exp 95 + switch product 7 + sum 11
-    term = 18 + 95 + 7 + 11
+    # float-float passes (csrc/ff.cuh): add 11, mul 7, exp 64 FP32 operations; per
+    # radial term at a node: argument 18 + exp 64 + switch product 7 + sum 11
+    # (the implementation's own count: quoted for these kernels only, never as
+    # the step's roofline unless they are the largest share)
+    term = 18 + 64 + 7 + 11
     node = 11 + 10 + 3                      # node distance, square root, switch test
     if kernel.startswith("density_ff"):
         return 13 * (node + term * n_f) + 300

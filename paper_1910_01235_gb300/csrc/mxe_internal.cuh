@@ -133,7 +133,7 @@ struct Ctrl {
   // staggered runs captured in a graph
   int phase;          // 0: before the Euler step of the current step, 1: after it
   int steps;          // completed steps
-  unsigned int red_ticket;  // blocks of the current FIRE reduction done (0 between launches)
+  unsigned int red_ticket;  // blocks of the current FIRE reduction or update done (0 between launches)
 };
 
 enum { kReasonNone = 0, kReasonConverged = 1, kReasonMaxIter = 2, kReasonRebuild = 3, kReasonError = 4,
@@ -146,6 +146,37 @@ struct SysFire {
   double dt, alpha, keep, mix, one_minus_alpha, fmax;
   double P, vv, ff;
 };
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be
+// scheduled while the previous kernel of its stream is finishing; it calls
+// pdl_wait() before reading anything an earlier kernel wrote
+// (griddepcontrol.wait returns once the prerequisite grids have completed and
+// their memory is visible) and pdl_trigger() to let the next kernel be
+// scheduled early in the same way.  In a kernel launched normally both are
+// no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t shm, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Blocks of a grid-stride pass: the kernel's resident blocks on every SM (one
+// wave; a launch that returns at once then costs one wave, not one block per
+// work item), or fewer when the work is smaller.
+int64_t resident_grid(const void* kernel, int threads, int64_t work_items);
 
 // ---------------------------------------------------------------- launchers
 // neighbours.cu

@@ -41,11 +41,10 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
 // The block's maximum of non-negative doubles, then one atomic per block (a
 // global atomic per warp serialises thousands of updates of one word).
 // Every thread of the block must call it.
-__device__ __forceinline__ void block_max_nonneg(unsigned long long* addr, double v) {
+__device__ __forceinline__ void block_max_bits(unsigned long long* addr, unsigned long long b) {
   __shared__ unsigned long long s_max;
   if (threadIdx.x == 0) s_max = 0ull;
   __syncthreads();
-  unsigned long long b = __double_as_longlong(v);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
@@ -54,6 +53,23 @@ __device__ __forceinline__ void block_max_nonneg(unsigned long long* addr, doubl
   if ((threadIdx.x & 31) == 0) atomicMax(&s_max, b);
   __syncthreads();
   if (threadIdx.x == 0 && s_max) atomicMax(addr, s_max);
+}
+__device__ __forceinline__ void block_max_nonneg(unsigned long long* addr, double v) {
+  block_max_bits(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Tests on bit patterns (integer instructions; GB300's FP64 pipe is narrow):
+// finiteness, and the projection below for positive sigma, lo, hi, whose order
+// is that of their bits.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ double proj_fsig_bits(double gs, double sigma, long long lo_b, long long hi_b) {
+  const double f = -gs;
+  const long long fb = __double_as_longlong(f), sb = __double_as_longlong(sigma);
+  if (sb >= hi_b && fb > 0) return 0.0;                              // f > 0
+  if (sb <= lo_b && fb < 0 && fb != (long long)0x8000000000000000ull) return 0.0;  // f < 0 (not -0)
+  return f;
 }
 
 // force on sigma projected on the box [lo, hi]: zero where a bound blocks it
@@ -142,34 +158,38 @@ __global__ void __launch_bounds__(kRedThreads) k_fire_reduce(const double* __res
                                                              const double* __restrict__ vs, int64_t n,
                                                              int64_t ngroups, double* __restrict__ partials,
                                                              Ctrl* __restrict__ ctrl, int* __restrict__ flags) {
+  pdl_wait();
+  pdl_trigger();
   if (ctrl->halted) return;  // the same for every block: nothing in this launch changes it before the logic
   __shared__ double sh[3][kRedThreads];
   __shared__ int s_last;
   const int tid = threadIdx.x;
-  const double lo = ctrl->sigma_lo, hi = ctrl->sigma_hi;
-  double P = 0.0, vv = 0.0, ff = 0.0, fm = 0.0;
+  const long long lo_b = __double_as_longlong(ctrl->sigma_lo), hi_b = __double_as_longlong(ctrl->sigma_hi);
+  double P = 0.0, vv = 0.0, ff = 0.0;
+  unsigned long long fmb = 0ull;
   bool finite = true;
-  {
-    const int64_t i = blockIdx.x * (int64_t)kFireGroup + tid;
-    if (i < n) {
-    double g0 = gq[i], g1 = gq[n + i], g2 = gq[2 * n + i];
-    double f3 = proj_fsig(gs[i], sigma[i], lo, hi);
-    double v0 = vq[i], v1 = vq[n + i], v2 = vq[2 * n + i], v3 = vs[i];
-    P += -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
-    vv += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
-    ff += g0 * g0 + g1 * g1 + g2 * g2 + f3 * f3;
-    // the largest squared force component norm; its square root is taken
-    // once, by the logic (sqrt is monotone and correctly rounded, so
-    // sqrt(max) == max(sqrt))
-    fm = fmax(fm, fmax(g0 * g0 + g1 * g1 + g2 * g2, f3 * f3));
-    finite = finite && isfinite(g0) && isfinite(g1) && isfinite(g2) && isfinite(gs[i]);
-    }
+  const int64_t i = blockIdx.x * (int64_t)kFireGroup + tid;
+  if (i < n) {
+    const double g0 = gq[i], g1 = gq[n + i], g2 = gq[2 * n + i], gsi = gs[i];
+    const double f3 = proj_fsig_bits(gsi, sigma[i], lo_b, hi_b);
+    const double v0 = vq[i], v1 = vq[n + i], v2 = vq[2 * n + i], v3 = vs[i];
+    P = -(g0 * v0 + g1 * v1 + g2 * v2) + f3 * v3;
+    vv = v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
+    const double gg = g0 * g0 + g1 * g1 + g2 * g2, f33 = f3 * f3;
+    ff = gg + f33;
+    finite = finite_bits(g0) && finite_bits(g1) && finite_bits(g2) && finite_bits(gsi);
+    // the largest squared force component norm (maximum of non-negative
+    // doubles = maximum of their bits); its square root is taken once, by
+    // the logic (sqrt is monotone and correctly rounded, so sqrt(max) ==
+    // max(sqrt)); a site with a non-finite gradient enters as 0 (flagged)
+    const unsigned long long a = __double_as_longlong(gg), b = __double_as_longlong(f33);
+    fmb = finite ? (a > b ? a : b) : 0ull;
   }
   sh[0][tid] = P;
   sh[1][tid] = vv;
   sh[2][tid] = ff;
   if (!finite) atomicOr(flags, kFlagNonfinite);
-  block_max_nonneg(&ctrl->fmax_bits, finite ? fm : 0.0);
+  block_max_bits(&ctrl->fmax_bits, fmb);
   __syncthreads();
   for (int w = kRedThreads / 2; w > 0; w >>= 1) {
     if (tid < w)
@@ -208,7 +228,7 @@ __device__ __forceinline__ void fire_site(double* __restrict__ q, double* __rest
     disp2 += dq * dq;
     p[c] = (float)(qn - (double)abs_cell[c * n + i] * g.h[c]);
   }
-  const double f = proj_fsig(gs[i], sigma[i], lo, hi);
+  const double f = proj_fsig_bits(gs[i], sigma[i], __double_as_longlong(lo), __double_as_longlong(hi));
   double v = keep * vs[i] + dt * f;
   v = oma * v + mix * f;
   sg = sigma[i] + dt * v;
@@ -227,6 +247,8 @@ __global__ void __launch_bounds__(256) k_fire_update(double* __restrict__ q, dou
                                                      const double* __restrict__ q_build,
                                                      const int* __restrict__ abs_cell, int64_t n, DevGrid g0,
                                                      Batch B, float4* __restrict__ pos32, Ctrl* __restrict__ ctrl) {
+  pdl_wait();
+  pdl_trigger();
   if (ctrl->halted) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const double dt = ctrl->dt, keep = ctrl->keep, mix = ctrl->mix, oma = ctrl->one_minus_alpha;
@@ -238,6 +260,26 @@ __global__ void __launch_bounds__(256) k_fire_update(double* __restrict__ q, dou
   }
   block_max_nonneg(&ctrl->disp2_bits, disp2);
   block_max_nonneg(&ctrl->smax_bits, sg);
+  // The last block to finish (a ticket in the control block) tests the
+  // rebuild criterion on this update's maxima, so that every kernel of the
+  // next evaluation returns at once when the lists must be rebuilt (the same
+  // test as the first pass's, which then finds the flag already set).
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl->red_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    ctrl->red_ticket = 0u;
+    const double disp = sqrt(__longlong_as_double((long long)__ldcg(&ctrl->disp2_bits)));
+    const double smax = __longlong_as_double((long long)__ldcg(&ctrl->smax_bits));
+    if (2.0 * disp + kSqrt6 * (smax - ctrl->sigma_max_build) > ctrl->skin) {
+      ctrl->reason = kReasonRebuild;
+      ctrl->halted = 1;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- batches
@@ -479,8 +521,8 @@ cudaError_t launch_fire_reduce(const double* gq, const double* gs, const double*
                                const double* vs, int64_t n, double* partials, Ctrl* ctrl, int* flags, cudaStream_t s) {
   int64_t ng = (n + kFireGroup - 1) / kFireGroup;
   if (ng < 1) ng = 1;
-  k_fire_reduce<<<(unsigned)ng, kRedThreads, 0, s>>>(gq, gs, sigma, vq, vs, n, ng, partials, ctrl, flags);
-  return cudaGetLastError();
+  return launch_pdl(k_fire_reduce, dim3((unsigned)ng), dim3(kRedThreads), 0, s, gq, gs, sigma, vq, vs, n, ng, partials,
+                    ctrl, flags);
 }
 
 cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs, const double* gq,
@@ -488,8 +530,8 @@ cudaError_t launch_fire_update(double* q, double* sigma, double* vq, double* vs,
                                const DevGrid& g, const Batch& B, float4* pos32, Ctrl* ctrl, cudaStream_t s) {
   unsigned blocks = (unsigned)((n + 255) / 256);
   if (blocks == 0) blocks = 1;
-  k_fire_update<<<blocks, 256, 0, s>>>(q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, g, B, pos32, ctrl);
-  return cudaGetLastError();
+  return launch_pdl(k_fire_update, dim3(blocks), dim3(256), 0, s, q, sigma, vq, vs, gq, gs, q_build, abs_cell, n, g, B,
+                    pos32, ctrl);
 }
 
 cudaError_t launch_fire_seg_reduce(const double* gq, const double* gs, const double* sigma, const double* vq,
