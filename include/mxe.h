@@ -324,6 +324,18 @@ MXE_API mxe_status mxe_set_pass_shape(mxe_ctx *ctx, int32_t lanes, int32_t threa
 MXE_API mxe_status mxe_set_pair_block(mxe_ctx *ctx, int32_t pair_threads);
 MXE_API mxe_status mxe_get_pass_shape(mxe_ctx *ctx, int32_t *lanes, int32_t *threads, int32_t *pair_threads);
 
+/* Forms of the pair kernels this context's potential takes (host values,
+ * either pointer may be NULL):
+ *  table_pattern 1: two species, two like pair terms and a cross term, a
+ *    density that depends on the neighbour's species only (the species tables
+ *    are compile-time constants in the pair kernels); 0: general tables.
+ *  power_form 1: in addition the cross term is the geometric mean of the like
+ *    terms, and each species' pair and density terms are integer powers
+ *    (<= 16) of one exponential exp(-beta_s r), to 1e-15 in their rates: the
+ *    accurate pass evaluates two exponentials per node (App. A) and forms the
+ *    terms as products; 0: one exponential per term.                        */
+MXE_API mxe_status mxe_pair_form(mxe_ctx *ctx, int32_t *table_pattern, int32_t *power_form);
+
 /* Phase average of the embedding term (App. B.2).
  *  MXE_EMBED_TAYLOR (default): the Taylor form Eq. F_taylor_mxe,
  *    <F_k(rho_i)> ~ F_k(rho_bar_i) + F_k'(rho_bar_i)(<rho_i> - rho_bar_i).

@@ -288,6 +288,51 @@ int add_fn(RadialFn* tab, int& count, int cap, double A, double kappa, double la
   return count++;
 }
 
+// The power form of a binary pattern with a geometric-mean cross term: for
+// each species s, integers m, n <= 16 with lambda(phi_ss) = m beta and
+// lambda(f_s) = n beta (m even, so the cross term's exponent m/2 is whole),
+// to 1e-15 relative (the rounding of rates computed from p / r0).  exp(c - lambda r) = exp(c) exp(-beta r)^m exactly in
+// real arithmetic; the rounding of the power adds at most m ulps of the base.
+void set_power_form(DevPot& d) {
+  d.pw_on = 0;
+  if (!(d.tab == 1 && d.cross_geo && !d.lj)) return;
+  const int phi_of_s[2] = {0, 2};
+  for (int s = 0; s < 2; ++s) {
+    const double lp = d.phi[phi_of_s[s]].lambda, lf = d.f[s].lambda;
+    if (!(lp > 0.0) || !(lf > 0.0)) return;
+    int m = 0, n = 0;
+    for (int nn = 1; nn <= 16 && !m; ++nn) {
+      const double mm = std::nearbyint(lp / lf * nn);
+      if (mm >= 1.0 && mm <= 16.0 && std::fabs(mm * lf - nn * lp) <= 1e-15 * nn * lp) {
+        m = (int)mm;
+        n = nn;
+      }
+    }
+    if (!m) return;
+    if (m % 2) {
+      m *= 2;
+      n *= 2;
+    }
+    if (m > 16 || n > 16) return;
+    d.pw_m[s] = m;
+    d.pw_n[s] = n;
+    d.pw_beta[s] = lp / m;
+  }
+  // the cross term's rate must be the mean of the like rates (geometric mean)
+  const double lx = d.phi[1].lambda, lmean = 0.5 * (d.pw_m[0] * d.pw_beta[0] + d.pw_m[1] * d.pw_beta[1]);
+  if (std::fabs(lx - lmean) > 1e-15 * lx) return;
+  for (int u = 0; u < 3; ++u) {
+    d.pw_pref_phi[u] = d.phi[u].A * std::exp(d.phi[u].kappa);
+    d.pw_pref_phi_ff[u] = ff(d.pw_pref_phi[u]);
+  }
+  for (int v = 0; v < 2; ++v) {
+    d.pw_pref_f[v] = d.f[v].A * std::exp(d.f[v].kappa);
+    d.pw_pref_f_ff[v] = ff(d.pw_pref_f[v]);
+  }
+  for (int s = 0; s < 2; ++s) d.pw_beta_ff[s] = ff(d.pw_beta[s]);
+  d.pw_on = 1;
+}
+
 mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
   std::memset(&d, 0, sizeof(d));
   const int S = p.n_species;
@@ -345,6 +390,7 @@ mxe_status make_devpot(const mxe_potential& p, DevPot& d) {
               ? 1
               : 0;
   d.cross_geo = (S == 2 && p.cross_geomean && !p.lj) ? 1 : 0;
+  set_power_form(d);
   d.rs = p.r_switch;
   d.rc = p.r_cut;
   d.inv_w = 1.0 / (p.r_cut - p.r_switch);
@@ -2173,6 +2219,13 @@ mxe_status mxe_get_pass_shape(mxe_ctx* c, int32_t* lanes, int32_t* threads, int3
   if (lanes) *lanes = c->nl;
   if (threads) *threads = c->tpb;
   if (pair_threads) *pair_threads = c->pair_tpb;
+  return MXE_OK;
+}
+
+mxe_status mxe_pair_form(mxe_ctx* c, int32_t* table_pattern, int32_t* power_form) {
+  if (!c) return MXE_ERR_ARG;
+  if (table_pattern) *table_pattern = c->dp.tab;
+  if (power_form) *power_form = c->dp.pw_on;
   return MXE_OK;
 }
 

@@ -924,11 +924,40 @@ __device__ __forceinline__ double pair_term(const RadialFn& F, double r, const f
   return e;
 }
 
+// the power form's pieces in the node arithmetic R
+__device__ __forceinline__ ff geo_exp(ff x, const float2* T) { return ff_exp(x, T); }
+__device__ __forceinline__ double geo_exp(double x, const float2*) { return exp(x); }
+__device__ __forceinline__ ff pw_beta(const DevPot& P, int s, ff) { return P.pw_beta_ff[s]; }
+__device__ __forceinline__ double pw_beta(const DevPot& P, int s, double) { return P.pw_beta[s]; }
+__device__ __forceinline__ ff pw_pref_phi(const DevPot& P, int u, ff) { return P.pw_pref_phi_ff[u]; }
+__device__ __forceinline__ double pw_pref_phi(const DevPot& P, int u, double) { return P.pw_pref_phi[u]; }
+__device__ __forceinline__ ff pw_pref_f(const DevPot& P, int v, ff) { return P.pw_pref_f_ff[v]; }
+__device__ __forceinline__ double pw_pref_f(const DevPot& P, int v, double) { return P.pw_pref_f[v]; }
+
+// c^e for 1 <= e <= 31 from the squares sq[b] = c^(2^b) (the bits of e are
+// uniform over the warp: the exponents are the potential's)
+template <typename R>
+__device__ __forceinline__ R pow_from_squares(const R sq[5], int e) {
+  R r = (R)1;
+  bool first = true;
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    if ((e >> b) & 1) {
+      r = first ? sq[b] : r * sq[b];
+      first = false;
+    }
+  return r;
+}
+
 // sqrt(a b) of two positive values (the cross term of a geometric-mean pair)
 __device__ __forceinline__ ff cross_mean(ff a, ff b) { return ff_sqrt(a * b); }
 __device__ __forceinline__ double cross_mean(double a, double b) { return sqrt(a * b); }
 
-template <int S, typename R>
+// PW 1: the power form with the exponents fixed at compile time, m = 6 and
+// n = 10 for both species (pair rate 3/r0, density rate 5/r0: c_s =
+// exp(-r / (2 r0_s))); PW 0: the general form, or the power form with the
+// exponents read at run time.
+template <int S, typename R, int PW>
 __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs A,
                                                   const int4* __restrict__ pair_rec, int64_t npair,
                                                   typename GeoRec<R>::T* __restrict__ buf, int C) {
@@ -953,6 +982,73 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
   const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
   const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   int bad = D2 < (R)(kRMin * kRMin);
+  typename GeoRec<R>::T* o = buf + pr_.tp * (int64_t)C;
+  typename GeoRec<R>::T* o2 = buf + pr_.tr * (int64_t)C;
+  if (PW == 1 || P.pw_on) {
+    // power form: per point its distance and switch, the two bases c_s =
+    // exp(-beta_s r) and the terms as their integer powers (prefactors
+    // applied to the sums); no per-point arrays
+    R af[2] = {(R)0, (R)0}, aphi[3] = {(R)0, (R)0, (R)0}, st[2];
+    const int top0 = max(P.pw_m[0], P.pw_n[0]), top1 = max(P.pw_m[1], P.pw_n[1]);
+#pragma unroll 1
+    for (int k = 0; k < 13; ++k) {
+      R r2 = D2;  // point 12: the static point
+      if (k < 12) {
+        const int site = k / 6, a = (k / 2) % 3, pm = k & 1;
+        const R s = site == 0 ? s_i : s_j;
+        const R tw = (R)2 * s * d[a];
+        const R base = D2 + s * s;
+        r2 = pm == 0 ? base + tw : base - tw;
+        bad |= r2 < (R)(kRMin * kRMin);
+      }
+      R r, rinv, Sw, dS;
+      r_from_r2(r2, r, rinv);
+      sw(P, r, Sw, dS);
+      const R c0 = geo_exp(-(pw_beta(P, 0, R()) * r), s_exp);
+      const R c1 = geo_exp(-(pw_beta(P, 1, R()) * r), s_exp);
+      R f0, f1, h0, h1;  // c^n and c^(m/2) of each species
+      if constexpr (PW == 1) {
+        const R c0_2 = c0 * c0, c1_2 = c1 * c1;
+        h0 = c0_2 * c0;
+        h1 = c1_2 * c1;
+        const R c0_5 = h0 * c0_2, c1_5 = h1 * c1_2;
+        f0 = c0_5 * c0_5;
+        f1 = c1_5 * c1_5;
+      } else {
+        R sq0[5], sq1[5];
+        sq0[0] = c0;
+        sq1[0] = c1;
+#pragma unroll
+        for (int b = 1; b < 5; ++b) {
+          if ((top0 >> b) != 0) sq0[b] = sq0[b - 1] * sq0[b - 1];
+          if ((top1 >> b) != 0) sq1[b] = sq1[b - 1] * sq1[b - 1];
+        }
+        f0 = pow_from_squares(sq0, P.pw_n[0]);
+        f1 = pow_from_squares(sq1, P.pw_n[1]);
+        h0 = pow_from_squares(sq0, P.pw_m[0] / 2);
+        h1 = pow_from_squares(sq1, P.pw_m[1] / 2);
+      }
+      if (k == 12) {  // the static point: densities only
+        st[0] = f0 * Sw;
+        st[1] = f1 * Sw;
+        break;
+      }
+      af[0] += f0 * Sw;
+      af[1] += f1 * Sw;
+      aphi[0] += (h0 * h0) * Sw;
+      aphi[2] += (h1 * h1) * Sw;
+      aphi[1] += (h0 * h1) * Sw;
+    }
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      o[v] = o2[v] = GeoRec<R>::put(pw_pref_f(P, v, R()) * st[v]);
+      o[2 + v] = o2[2 + v] = GeoRec<R>::put(pw_pref_f(P, v, R()) * af[v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) o[4 + u] = o2[4 + u] = GeoRec<R>::put(pw_pref_phi(P, u, R()) * aphi[u]);
+    if (bad) atomicOr(A.flags, kFlagGeometry);
+    return;
+  }
   // the 13 points once: r and S(r) of the 12 nodes (0..11) and the static point (12)
   R pr[13], pw[13];
   {
@@ -972,12 +1068,10 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
     r_from_r2(r2, pr[k], rinv);
     sw(P, pr[k], pw[k], dS);
   }
-  // one term at a time over the points (rolled: one copy of the float-float
-  // exponential in the loop body); the record goes to both entries of the
-  // pair (every value is symmetric in i and j), so the gathers read rows in
-  // order
-  typename GeoRec<R>::T* o = buf + pr_.tp * (int64_t)C;
-  typename GeoRec<R>::T* o2 = buf + pr_.tr * (int64_t)C;
+  // general form: one term at a time over the points (rolled: one copy of
+  // the float-float exponential in the loop body).  The record goes to both
+  // entries of the pair (every value is symmetric in i and j), so the gathers
+  // read rows in order.
 #pragma unroll 1
   for (int v = 0; v < P.n_f; ++v) {
     R acc = (R)0;
@@ -2516,8 +2610,13 @@ cudaError_t pair_geo_t(const DevPot& P, const DevGrid& g, const PassArgs& A, con
   const unsigned blocks = (unsigned)((npair + pt - 1) / pt);
   using T = typename GeoRec<R>::T;
   switch (P.S) {
-    case 1: k_pair_geo<1, R><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
-    case 2: k_pair_geo<2, R><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
+    case 1: k_pair_geo<1, R, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C); break;
+    case 2:
+      if (P.pw_on && P.pw_m[0] == 6 && P.pw_n[0] == 10 && P.pw_m[1] == 6 && P.pw_n[1] == 10)
+        k_pair_geo<2, R, 1><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C);
+      else
+        k_pair_geo<2, R, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

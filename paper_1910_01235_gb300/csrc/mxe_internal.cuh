@@ -58,6 +58,14 @@ struct DevPot {
   double E[kMaxS];
   int tab;                       // 1: the binary alloy pattern below, 0: general tables
   int cross_geo;                 // the cross pair term is the geometric mean of the like pairs
+  // Power form (tab 1 with cross_geo): for each species s one base rate
+  // beta_s with phi_ss = pw_pref_phi[2s] c_s^pw_m[s], f_s = pw_pref_f[s]
+  // c_s^pw_n[s] and the cross term pw_pref_phi[1] c_0^(pw_m[0]/2)
+  // c_1^(pw_m[1]/2), c_s = exp(-beta_s r): two exponentials per node
+  int pw_on;
+  int pw_m[2], pw_n[2];
+  double pw_beta[2], pw_pref_phi[3], pw_pref_f[2];
+  ff pw_beta_ff[2], pw_pref_phi_ff[3], pw_pref_f_ff[2];
   double rs, rc, inv_w;          // switch start, cutoff, 1/(rc - rs)
   float rs_f, rc_f, inv_w_f, dS_scale_f;
   ff rs_ff, inv_w_ff, dS_scale_ff;

@@ -70,7 +70,7 @@ EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy",
            "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape",
            "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad", "mxe_transport_step",
            "mxe_set_embedding", "mxe_element_param_grad", "mxe_unrolled_grad_multi", "mxe_set_pair_block",
-           "mxe_get_pass_shape", "mxe_run_stats"]
+           "mxe_get_pass_shape", "mxe_run_stats", "mxe_pair_form"]
 EMBED_TAYLOR, EMBED_EXACT = 0, 1
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
@@ -107,6 +107,7 @@ def lib():
             L.mxe_set_embedding.argtypes = [p, C.c_int32]
             L.mxe_set_pair_block.argtypes = [p, C.c_int32]
             L.mxe_get_pass_shape.argtypes = [p, p, p, p]
+            L.mxe_pair_form.argtypes = [p, p, p]
             L.mxe_run_stats.argtypes = [p, p, p]
             L.mxe_element_param_grad.argtypes = [p, p, p]
             L.mxe_unrolled_grad_multi.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.c_int32, C.c_int32,
@@ -516,6 +517,12 @@ class MxeSystem:
         v = (C.c_int32 * 3)()
         self._check(lib().mxe_get_pass_shape(self.ctx, C.byref(v, 0), C.byref(v, 4), C.byref(v, 8)),
                     "mxe_get_pass_shape")
+        return tuple(v)
+
+    def pair_form(self):
+        """(table pattern, power form) of the pair kernels (see include/mxe.h)."""
+        v = (C.c_int32 * 2)()
+        self._check(lib().mxe_pair_form(self.ctx, C.byref(v, 0), C.byref(v, 4)), "mxe_pair_form")
         return tuple(v)
 
     def set_embedding(self, mode):

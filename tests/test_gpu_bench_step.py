@@ -176,3 +176,55 @@ def test_binary_alloy_tables_take_the_specialised_pattern():
     nphi, nf, terms, phi_of, f_of = g.potential_terms()
     assert phi_of[1, 1] == -1
     g.close()
+
+
+def _binary_with(p_a=None, q_b=None, cells=5, seed=21):
+    s = W.perturb(W.config_binary_alloy(cells=cells), 0.06, 0.02, seed=seed)
+    s = W.random_fractions(s, vac_min=0.01, seed=seed + 1)
+    if p_a is not None:
+        s.pot.phi_p[0, 0] = p_a
+    if q_b is not None:
+        s.pot.f_q[:, 1] = q_b
+    return s
+
+
+def test_power_form_taken_where_the_rates_allow_it():
+    """The alloy's pair and density rates are 3/r0 and 5/r0 per species
+    (integer powers 6 and 10 of exp(-r / (2 r0)), cross term powers 3 and 3):
+    the accurate pass takes the power form; a pair exponent of 3.1 (a ratio
+    31/50) or a density exponent of 4.9 for B leaves the general form, and so
+    does any potential outside the binary table pattern."""
+    for s, want in ((W.config_binary_alloy(cells=4), (1, 1)),
+                    (_binary_with(), (1, 1)),
+                    (_binary_with(p_a=3.1), (1, 0)),
+                    (_binary_with(q_b=4.9), (1, 0))):
+        g = M.MxeSystem(s, "ff")
+        assert g.pair_form() == want
+        g.close()
+    s = W.config_binary_alloy(cells=4)
+    s.pot = W.potential_binary_variant_s()
+    g = M.MxeSystem(s, "fp64")
+    assert g.pair_form() == (1, 1)   # rates 5/r0 and 3/r0: powers 10 and 6
+    g.close()
+    g = M.MxeSystem(W.config_vacancy_lattice(cells=4), "ff")
+    assert g.pair_form()[1] == 0
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ff"])
+@pytest.mark.parametrize("form", ["power", "general"])
+def test_accurate_pass_parity_in_both_forms(prec, form):
+    """Energies and chemical potentials (the accurate pass) against the oracle
+    with the power form taken and not taken (same tolerances as the other
+    parity tests: energies 1e-10 relative, mu^ex 1e-9 eV)."""
+    s = _binary_with() if form == "power" else _binary_with(p_a=3.1)
+    g = M.MxeSystem(s, prec)
+    assert g.pair_form()[1] == (1 if form == "power" else 0)
+    g.build_neighbors()
+    g.free_energy_grad()
+    torch.cuda.synchronize()
+    fe = O.free_energy(s, r_list=g.r_list)
+    assert fe["status"] == O.OK
+    np.testing.assert_allclose(g.F4.cpu().numpy(), fe["F4"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(g.mu_ex.cpu().numpy(), fe["mu_ex"], rtol=0, atol=1e-9)
+    g.close()
