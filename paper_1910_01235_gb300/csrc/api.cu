@@ -86,7 +86,7 @@ struct mxe_ctx {
   // per row: entries below its site (head), pairs it owns (tail), their scan
   int *n_below = nullptr, *pair_cnt = nullptr, *pair_off = nullptr;  // [n], [n], [n + 1]
   int4* pair_rec = nullptr;  // [pairs] (i, entry of j with its image code, entry index, reverse entry index)
-  double* pair_buf = nullptr;  // [entries][pair_record_len] 8-byte values (float pairs or doubles)
+  double* pair_buf = nullptr;  // pair_cap x pair_record_len 8-byte values (float pairs or doubles; see geo_layout)
   void *ent_dens = nullptr, *ent_frc = nullptr;  // [entries] relaxation records (relax_record_bytes each)
   bool relax_records = false;  // allocate them (first relaxation of the context, then with every list growth)
   int64_t pair_cap = 0, n_upairs = 0;
@@ -811,11 +811,11 @@ mxe_status enqueue_passes(mxe_ctx* c, const mxe_state* s, PassArgs& A, bool want
       G.ab32lo = nullptr;
     }
     CK(TIMED(prec == MXE_FP64 ? "pair_geo64" : "pair_ff",
-             launch_pair_geo(prec, PP, c->grid, G, c->pair_rec, c->n_upairs, c->pair_buf, st)));
+             launch_pair_geo(prec, PP, c->grid, G, c->pair_rec, c->n_upairs, c->pair_buf, c->pair_cap, st)));
     CK(TIMED(accurate_gather_name(false, prec),
-             launch_pair_gather(prec, false, c->nl, PP, G, c->pair_buf, st)));
+             launch_pair_gather(prec, false, c->nl, PP, G, c->pair_buf, c->pair_cap, st)));
     CK(TIMED(accurate_gather_name(true, prec),
-             launch_pair_gather(prec, true, c->nl, PP, G, c->pair_buf, st)));
+             launch_pair_gather(prec, true, c->nl, PP, G, c->pair_buf, c->pair_cap, st)));
   }
   if (A.gq != nullptr || A.gs != nullptr) {
     PassArgs F = A;

@@ -960,7 +960,7 @@ __device__ __forceinline__ double cross_mean(double a, double b) { return sqrt(a
 template <int S, typename R, int PW>
 __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs A,
                                                   const int4* __restrict__ pair_rec, int64_t npair,
-                                                  typename GeoRec<R>::T* __restrict__ buf, int C) {
+                                                  typename GeoRec<R>::T* __restrict__ buf, GeoLayout L) {
   constexpr int PR = GeoPrec<R>::P;
   // the float-float exponential's table, in shared memory (read by the
   // halt check's barrier below before any use)
@@ -982,8 +982,22 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
   const R s_i = sqrt6<R>() * si.sig, s_j = sqrt6<R>() * sj.sig;
   const R D2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   int bad = D2 < (R)(kRMin * kRMin);
-  typename GeoRec<R>::T* o = buf + pr_.tp * (int64_t)C;
-  typename GeoRec<R>::T* o2 = buf + pr_.tr * (int64_t)C;
+  // component c of the record, at both entries of the pair (plane A below
+  // L.ca, plane B above)
+  typename GeoRec<R>::T* oa = buf + pr_.tp * (int64_t)L.ca;
+  typename GeoRec<R>::T* oa2 = buf + pr_.tr * (int64_t)L.ca;
+  typename GeoRec<R>::T* ob = buf + L.b_off + pr_.tp * (int64_t)L.cb;
+  typename GeoRec<R>::T* ob2 = buf + L.b_off + pr_.tr * (int64_t)L.cb;
+  auto put = [&](int c, R v) {
+    const typename GeoRec<R>::T w = GeoRec<R>::put(v);
+    if (c < L.ca) {
+      oa[c] = w;
+      oa2[c] = w;
+    } else {
+      ob[c - L.ca] = w;
+      ob2[c - L.ca] = w;
+    }
+  };
   if (PW == 1 || P.pw_on) {
     // power form: per point its distance and switch, the two bases c_s =
     // exp(-beta_s r) and the terms as their integer powers (prefactors
@@ -1041,11 +1055,11 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
     }
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      o[v] = o2[v] = GeoRec<R>::put(pw_pref_f(P, v, R()) * st[v]);
-      o[2 + v] = o2[2 + v] = GeoRec<R>::put(pw_pref_f(P, v, R()) * af[v]);
+      put(v, pw_pref_f(P, v, R()) * st[v]);
+      put(2 + v, pw_pref_f(P, v, R()) * af[v]);
     }
 #pragma unroll
-    for (int u = 0; u < 3; ++u) o[4 + u] = o2[4 + u] = GeoRec<R>::put(pw_pref_phi(P, u, R()) * aphi[u]);
+    for (int u = 0; u < 3; ++u) put(4 + u, pw_pref_phi(P, u, R()) * aphi[u]);
     if (bad) atomicOr(A.flags, kFlagGeometry);
     return;
   }
@@ -1078,8 +1092,8 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
 #pragma unroll 1
     for (int k = 0; k < 12; ++k) acc += geo_term(P.f[v], pr[k], s_exp) * pw[k];
     const R st = geo_term(P.f[v], pr[12], s_exp) * pw[12];
-    o[v] = o2[v] = GeoRec<R>::put(st);
-    o[P.n_f + v] = o2[P.n_f + v] = GeoRec<R>::put(acc);
+    put(v, st);
+    put(P.n_f + v, acc);
   }
   if (P.tab == 1 && P.cross_geo) {
     // binary pattern with a geometric-mean cross pair: terms 0 and 2 are the
@@ -1094,16 +1108,16 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
       a2 += e2 * pw[k];
       a1 += cross_mean(e0, e2) * pw[k];
     }
-    o[2 * P.n_f + 0] = o2[2 * P.n_f + 0] = GeoRec<R>::put(a0);
-    o[2 * P.n_f + 1] = o2[2 * P.n_f + 1] = GeoRec<R>::put(a1);
-    o[2 * P.n_f + 2] = o2[2 * P.n_f + 2] = GeoRec<R>::put(a2);
+    put(2 * P.n_f + 0, a0);
+    put(2 * P.n_f + 1, a1);
+    put(2 * P.n_f + 2, a2);
   } else {
 #pragma unroll 1
     for (int u = 0; u < P.n_phi; ++u) {
       R acc = (R)0;
 #pragma unroll 1
       for (int k = 0; k < 12; ++k) acc += pair_term(P.phi[u], pr[k], s_exp) * pw[k];
-      o[2 * P.n_f + u] = o2[2 * P.n_f + u] = GeoRec<R>::put(acc);
+      put(2 * P.n_f + u, acc);
     }
   }
   if (bad) atomicOr(A.flags, kFlagGeometry);
@@ -1141,7 +1155,7 @@ __device__ __forceinline__ void load_x(const PassArgs& A, int64_t j, double x[S]
 
 template <int S, int NL, typename R, typename Acc>
 __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A,
-                                                      const typename GeoRec<R>::T* __restrict__ buf, int C) {
+                                                      const typename GeoRec<R>::T* __restrict__ buf, GeoLayout GL) {
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t i = tid / NL;
@@ -1158,7 +1172,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A,
 #pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
       const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
-      const typename GeoRec<R>::T* rec = buf + (int64_t)t * C;
+      const typename GeoRec<R>::T* rec = buf + (int64_t)t * GL.ca;  // densities: plane A
       R xj[S];
       load_x<S>(A, j, xj);
 #pragma unroll
@@ -1247,7 +1261,7 @@ __global__ void __launch_bounds__(256) k_pair_density(DevPot P, PassArgs A,
 
 template <int S, int NL, typename R, typename Acc>
 __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A,
-                                                 const typename GeoRec<R>::T* __restrict__ buf, int C) {
+                                                 const typename GeoRec<R>::T* __restrict__ buf, GeoLayout GL) {
   constexpr int PR = GeoPrec<R>::P;
   if (A.ctrl != nullptr && A.ctrl->halted) return;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1266,7 +1280,9 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A,
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
     for (int t = beg + lane; t < end; t += NL) {
       const int64_t j = __ldg(&A.nb_ent[t]) & kIdxMask;
-      const typename GeoRec<R>::T* rec = buf + (int64_t)t * C;
+      const typename GeoRec<R>::T* rec = buf + (int64_t)t * GL.ca;
+      // pair terms: plane B when the record is split, else after the densities
+      const typename GeoRec<R>::T* recp = GL.cb ? buf + GL.b_off + (int64_t)t * GL.cb : rec + 2 * P.n_f;
       R xj[S];
       load_x<S>(A, j, xj);
       R aj[S], bj[S];
@@ -1279,7 +1295,7 @@ __global__ void __launch_bounds__(256) k_pair_mu(DevPot P, PassArgs A,
         for (int l = 0; l < S; ++l) {
           const int u = P.phi_of[k][l];
           if (u >= 0) {
-            const R ph = GeoRec<R>::get(rec, 2 * P.n_f + u);
+            const R ph = GeoRec<R>::get(recp, u);
             m += xj[l] * ph * inv12;
             ep += xi[k] * xj[l] * ph;
           }
@@ -2596,7 +2612,18 @@ cudaError_t launch_energy_seg(const double* site_E, int64_t n, const Batch& B, d
   return cudaGetLastError();
 }
 
-int pair_record_len(const DevPot& P) { return (2 * P.n_f + P.n_phi + 3) & ~3; }
+namespace {
+bool geo_split(const DevPot& P) { return 2 * P.n_f + P.n_phi > 4; }
+}  // namespace
+int pair_record_len(const DevPot& P) {
+  if (geo_split(P)) return ((2 * P.n_f + 3) & ~3) + ((P.n_phi + 3) & ~3);
+  return (2 * P.n_f + P.n_phi + 3) & ~3;
+}
+GeoLayout geo_layout(const DevPot& P, int64_t cap) {
+  if (!geo_split(P)) return GeoLayout{pair_record_len(P), 0, 0};
+  const int ca = (2 * P.n_f + 3) & ~3;
+  return GeoLayout{ca, (P.n_phi + 3) & ~3, cap * ca};
+}
 
 // threads per block of the pair kernels: the unordered pairs one block takes
 int pair_threads(const PassArgs& A) { return A.pair_tpb == 64 || A.pair_tpb == 256 ? A.pair_tpb : 128; }
@@ -2604,8 +2631,8 @@ int pair_threads(const PassArgs& A) { return A.pair_tpb == 64 || A.pair_tpb == 2
 namespace {
 template <typename R>
 cudaError_t pair_geo_t(const DevPot& P, const DevGrid& g, const PassArgs& A, const int4* pair_rec, int64_t npair,
-                       void* buf, cudaStream_t s) {
-  const int C = pair_record_len(P);
+                       void* buf, int64_t cap, cudaStream_t s) {
+  const GeoLayout C = geo_layout(P, cap);
   const int pt = pair_threads(A);
   const unsigned blocks = (unsigned)((npair + pt - 1) / pt);
   using T = typename GeoRec<R>::T;
@@ -2624,16 +2651,16 @@ cudaError_t pair_geo_t(const DevPot& P, const DevGrid& g, const PassArgs& A, con
 }  // namespace
 
 cudaError_t launch_pair_geo(int precision, const DevPot& P, const DevGrid& g, const PassArgs& A,
-                            const int4* pair_rec, int64_t npair, void* buf, cudaStream_t s) {
+                            const int4* pair_rec, int64_t npair, void* buf, int64_t cap, cudaStream_t s) {
   if (npair == 0) return cudaSuccess;
-  if (precision == 0) return pair_geo_t<double>(P, g, A, pair_rec, npair, buf, s);
+  if (precision == 0) return pair_geo_t<double>(P, g, A, pair_rec, npair, buf, cap, s);
   if (P.lj) return cudaErrorInvalidValue;  // Lennard-Jones terms: FP64 passes only
-  return pair_geo_t<ff>(P, g, A, pair_rec, npair, buf, s);
+  return pair_geo_t<ff>(P, g, A, pair_rec, npair, buf, cap, s);
 }
 
 namespace {
 template <int S, int NL, typename R, typename Acc>
-cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const void* buf, int C, cudaStream_t s) {
+cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const void* buf, GeoLayout C, cudaStream_t s) {
   const int threads = A.tpb > 0 ? A.tpb : 256;
   const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
   using T = typename GeoRec<R>::T;
@@ -2642,7 +2669,7 @@ cudaError_t pair_gather_t(bool mu, const DevPot& P, const PassArgs& A, const voi
   return cudaGetLastError();
 }
 template <int S, int NL>
-cudaError_t pair_gather_p(int precision, bool mu, const DevPot& P, const PassArgs& A, const void* buf, int C,
+cudaError_t pair_gather_p(int precision, bool mu, const DevPot& P, const PassArgs& A, const void* buf, GeoLayout C,
                           cudaStream_t s) {
   switch (precision) {
     case 0: return pair_gather_t<S, NL, double, AccD>(mu, P, A, buf, C, s);
@@ -2652,7 +2679,7 @@ cudaError_t pair_gather_p(int precision, bool mu, const DevPot& P, const PassArg
   }
 }
 template <int S>
-cudaError_t pair_gather_s(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf, int C,
+cudaError_t pair_gather_s(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf, GeoLayout C,
                           cudaStream_t s) {
   switch (nl) {
     case 4: return pair_gather_p<S, 4>(precision, mu, P, A, buf, C, s);
@@ -2664,9 +2691,9 @@ cudaError_t pair_gather_s(int precision, bool mu, int nl, const DevPot& P, const
 }  // namespace
 
 cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf,
-                               cudaStream_t s) {
+                               int64_t cap, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
-  const int C = pair_record_len(P);
+  const GeoLayout C = geo_layout(P, cap);
   switch (P.S) {
     case 1: return pair_gather_s<1>(precision, mu, nl, P, A, buf, C, s);
     case 2: return pair_gather_s<2>(precision, mu, nl, P, A, buf, C, s);

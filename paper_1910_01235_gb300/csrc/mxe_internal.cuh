@@ -293,16 +293,24 @@ cudaError_t launch_gradient(int precision, int mode, int nl, const DevPot& P, co
                             cudaStream_t s);
 // half-list accurate passes: each unordered pair's record of
 // pair_record_len(P) values (float pairs: float-float node arithmetic of the
-// FP32 modes; doubles: FP64 contexts) written to both of its entries
-// ([entries][C]), then the density (mu = false) or chemical-potential gather
-// over each site's own row (per-site sums in float-float for MXE_FP32_FF,
-// FP64 otherwise)
+// FP32 modes; doubles: FP64 contexts) written to both of its entries, then
+// the density (mu = false) or chemical-potential gather over each site's own
+// row (per-site sums in float-float for MXE_FP32_FF, FP64 otherwise).  Record
+// components [0, 2 n_f) (the densities) and [2 n_f, 2 n_f + n_phi) (the pair
+// terms) lie in two planes when they do not fit one 32-byte group: plane A
+// [cap][ca] at buf, plane B [cap][cb] at buf + b_off (cap: entries allocated),
+// so that the density gather reads plane A only.
+struct GeoLayout {
+  int ca, cb;      // values per entry in plane A and plane B (cb 0: one plane)
+  int64_t b_off;   // plane B's first value
+};
 int pair_record_len(const DevPot& P);
+GeoLayout geo_layout(const DevPot& P, int64_t cap);
 int pair_threads(const PassArgs& A);
 cudaError_t launch_pair_geo(int precision, const DevPot& P, const DevGrid& g, const PassArgs& A,
-                            const int4* pair_rec, int64_t npair, void* buf, cudaStream_t s);
+                            const int4* pair_rec, int64_t npair, void* buf, int64_t cap, cudaStream_t s);
 cudaError_t launch_pair_gather(int precision, bool mu, int nl, const DevPot& P, const PassArgs& A, const void* buf,
-                               cudaStream_t s);
+                               int64_t cap, cudaStream_t s);
 // half-list relaxation passes (FP32 node math in the FP32 modes, FP64 in FP64
 // contexts): the pair kernel writes each pair's record to both of its entries
 // (pair_t[p], pair_rev[p]); the gather then reads its own row: density (force
