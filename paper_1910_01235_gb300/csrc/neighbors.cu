@@ -298,23 +298,32 @@ __device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGri
                                                 float4* cq, int* cj, int* s_off, int* s_beg, float* s_sh,
                                                 int cand_cap, int* __restrict__ flags) {
   const bool fast = g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // one stencil cell per lane (its first site and count; lanes past the
+    // stencil count nothing), then an exclusive scan of the counts: the
+    // cells' loads are in flight together
+    const int lane = threadIdx.x;
     const Stencil st = make_stencil(cell - base, g);
-    int k = 0, tot = 0;
-    for (int ax = 0; ax < st.cnt[0]; ++ax)
-      for (int ay = 0; ay < st.cnt[1]; ++ay)
-        for (int az = 0; az < st.cnt[2]; ++az) {
-          const int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
-          s_beg[k] = cell_start[c];
-          s_off[k] = tot;
-          // without duplicates index t of an axis is the offset t - 1, and k the image code
-          s_sh[3 * k + 0] = (float)(ax - 1) * g.h_f[0];
-          s_sh[3 * k + 1] = (float)(ay - 1) * g.h_f[1];
-          s_sh[3 * k + 2] = (float)(az - 1) * g.h_f[2];
-          tot += cell_start[c + 1] - cell_start[c];
-          ++k;
-        }
-    for (int r = k; r < 28; ++r) s_off[r] = tot;
+    const int n1 = st.cnt[1], n2 = st.cnt[2], nk = st.cnt[0] * n1 * n2;
+    int cntk = 0;
+    if (lane < nk) {
+      const int ax = lane / (n1 * n2), ay = (lane / n2) % n1, az = lane % n2;
+      const int c = base + (st.off[0][ax] * g.nc[1] + st.off[1][ay]) * g.nc[2] + st.off[2][az];
+      const int b0 = cell_start[c];
+      s_beg[lane] = b0;
+      cntk = cell_start[c + 1] - b0;
+      // without duplicates index t of an axis is the offset t - 1, and k the image code
+      s_sh[3 * lane + 0] = (float)(ax - 1) * g.h_f[0];
+      s_sh[3 * lane + 1] = (float)(ay - 1) * g.h_f[1];
+      s_sh[3 * lane + 2] = (float)(az - 1) * g.h_f[2];
+    }
+    int incl = cntk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane < 28) s_off[lane] = incl - cntk;  // lanes >= nk: the total
   }
   __syncthreads();
   int ncand = s_off[27];
@@ -322,16 +331,25 @@ __device__ __forceinline__ CellStage stage_cell(int cell, int base, const DevGri
     if (threadIdx.x == 0) atomicOr(flags, kFlagOverflow);
     ncand = cand_cap;
   }
+  // the candidates' indices, then their positions: the loads of each pass do
+  // not depend on one another, so a thread has all of its candidates' loads
+  // in flight (a thread reads back only what it wrote)
+#pragma unroll 4
   for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
     int k = 0;
     while (t >= s_off[k + 1]) ++k;
     const int j = cell_sites[s_beg[k] + (t - s_off[k])];
+    cj[t] = fast ? (int)((uint32_t)j | ((uint32_t)k << kCodeShift)) : j;
+  }
+#pragma unroll 4
+  for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
+    const uint32_t e = (uint32_t)cj[t];
+    const int j = (int)(e & kIdxMask);
     if (fast) {
+      const int k = (int)(e >> kCodeShift);
       const float4 r = qf[n + j];
-      cj[t] = (int)((uint32_t)j | ((uint32_t)k << kCodeShift));
       cq[t] = make_float4(r.x + s_sh[3 * k], r.y + s_sh[3 * k + 1], r.z + s_sh[3 * k + 2], 0.f);
     } else {
-      cj[t] = j;
       cq[t] = qf[j];
     }
   }
@@ -517,7 +535,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_count(
 // and the longest row in *row_max; a row longer than the stride is cut and
 // its true length reported, so the caller can fall back to count + fill.
 template <bool DIRECT>
-__global__ void __launch_bounds__(kCellThreads) k_cell_fill(
+__global__ void __launch_bounds__(kCellThreads, 8) k_cell_fill(
     const double* __restrict__ q, const float4* __restrict__ qf, const uint8_t* __restrict__ sub, uint32_t mobile_mask,
     int64_t n, DevGrid g0, Batch B, const int* __restrict__ cell_start, const int* __restrict__ cell_sites,
     const int* __restrict__ abs_cell, double rl2, double rb2, float band, int cand_cap,
@@ -547,6 +565,36 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
   uint32_t* rows = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(cj + cand_cap) + 15) & ~uintptr_t(15));
   uint32_t* buf = rows + (size_t)warp * stride;
   uint32_t* kw = rows + (size_t)(nwarps + warp) * stride;
+  // Octant lists (home-frame stencils): cells are at least r_list wide, so a
+  // home site in the lower half of its cell along an axis has no neighbour
+  // beyond 1.5 cell widths on that axis, and one in the upper half none below
+  // -0.5; list o holds the candidates the home sites of octant o can reach
+  // (about (5/6)^3 of the stencil).  The cut has a margin of 1e-4 h against
+  // the FP32 rounding of the home-frame positions (below 1e-6 h); the row
+  // order is set by the sort below, so the lists' order does not matter.
+  uint16_t* olist = reinterpret_cast<uint16_t*>(rows + (size_t)2 * nwarps * stride);
+  __shared__ int s_ocnt[8];
+  if (threadIdx.x < 8) s_ocnt[threadIdx.x] = 0;
+  __syncthreads();
+  if (cs.fast) {
+    float lo_cut[3], hi_cut[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo_cut[a] = 1.5f * g.h_f[a] + 1e-4f * g.h_f[a];
+      hi_cut[a] = -0.5f * g.h_f[a] - 1e-4f * g.h_f[a];
+    }
+    for (int t = threadIdx.x; t < cs.ncand; t += blockDim.x) {
+      const float4 u = cq[t];
+      const bool lo_x = u.x < lo_cut[0], lo_y = u.y < lo_cut[1], lo_z = u.z < lo_cut[2];
+      const bool hi_x = u.x >= hi_cut[0], hi_y = u.y >= hi_cut[1], hi_z = u.z >= hi_cut[2];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const bool need = ((o & 4) ? hi_x : lo_x) && ((o & 2) ? hi_y : lo_y) && ((o & 1) ? hi_z : lo_z);
+        if (need) olist[o * cand_cap + atomicAdd(&s_ocnt[o], 1)] = (uint16_t)t;
+      }
+    }
+    __syncthreads();
+  }
   const float rl2f = (float)rl2, rb2f = (float)rb2;
   for (int h = hbeg + warp; h < hend; h += nwarps) {
     const int64_t i = cell_sites[h];
@@ -555,12 +603,18 @@ __global__ void __launch_bounds__(kCellThreads) k_cell_fill(
     const int si = sub ? sub[i] : 0;
     const bool mob = (mobile_mask >> si) & 1u;
     int m = 0, nbond = 0, nlow = 0;
-    for (int t0 = 0; t0 < cs.ncand; t0 += 32) {
-      const int t = t0 + lane;
+    const int oct = cs.fast ? ((qfi.x >= 0.5f * g.h_f[0]) << 2) | ((qfi.y >= 0.5f * g.h_f[1]) << 1) |
+                                  (int)(qfi.z >= 0.5f * g.h_f[2])
+                            : 0;
+    const int nc = cs.fast ? s_ocnt[oct] : cs.ncand;
+    const uint16_t* ol = olist + oct * cand_cap;
+    for (int t0 = 0; t0 < nc; t0 += 32) {
+      const int tt = t0 + lane;
       CandResult r{false, false, {0.f, 0.f, 0.f}};
       uint32_t ent = 0;
       int j = 0;
-      if (t < cs.ncand) {
+      if (tt < nc) {
+        const int t = cs.fast ? (int)ol[tt] : tt;
         ent = (uint32_t)cj[t];
         j = (int)(ent & kIdxMask);
         r = cs.fast ? test_cand_rel(i, qi, qfi, j, cq[t], q, n, g, rl2f, rb2f, band, rl2, rb2, mob, si, sub)
@@ -889,7 +943,9 @@ cudaError_t launch_cand_max(int64_t ncell, const DevGrid& g, const Batch& B, con
 
 size_t cell_stage_bytes(int cand_cap, int max_row, bool fill) {
   size_t b = (size_t)cand_cap * (sizeof(float4) + sizeof(int));
-  if (fill) b += 16 + (size_t)(kCellThreads / 32) * 2 * (size_t)((max_row + 3) & ~3) * sizeof(uint32_t);
+  if (fill)
+    b += 16 + (size_t)(kCellThreads / 32) * 2 * (size_t)((max_row + 3) & ~3) * sizeof(uint32_t) +
+         (size_t)8 * cand_cap * sizeof(uint16_t);  // rows and sort keys per warp, octant lists
   return b + 16;
 }
 
