@@ -955,8 +955,8 @@ __device__ __forceinline__ double cross_mean(double a, double b) { return sqrt(a
 
 // PW 1: the power form with the exponents fixed at compile time, m = 6 and
 // n = 10 for both species (pair rate 3/r0, density rate 5/r0: c_s =
-// exp(-r / (2 r0_s))); PW 0: the general form, or the power form with the
-// exponents read at run time.
+// exp(-r / (2 r0_s))); PW 2: the power form with the exponents read at run
+// time; PW 0: the general form (no power-form code: fewer registers).
 template <int S, typename R, int PW>
 __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs A,
                                                   const int4* __restrict__ pair_rec, int64_t npair,
@@ -998,7 +998,7 @@ __global__ void __launch_bounds__(256) k_pair_geo(DevPot P, DevGrid g0, PassArgs
       ob2[c - L.ca] = w;
     }
   };
-  if (PW == 1 || P.pw_on) {
+  if constexpr (PW != 0) {
     // power form: per point its distance and switch, the two bases c_s =
     // exp(-beta_s r) and the terms as their integer powers (prefactors
     // applied to the sums); no per-point arrays
@@ -2641,6 +2641,8 @@ cudaError_t pair_geo_t(const DevPot& P, const DevGrid& g, const PassArgs& A, con
     case 2:
       if (P.pw_on && P.pw_m[0] == 6 && P.pw_n[0] == 10 && P.pw_m[1] == 6 && P.pw_n[1] == 10)
         k_pair_geo<2, R, 1><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C);
+      else if (P.pw_on)
+        k_pair_geo<2, R, 2><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C);
       else
         k_pair_geo<2, R, 0><<<blocks, pt, 0, s>>>(P, g, A, pair_rec, npair, (T*)buf, C);
       break;
@@ -2732,8 +2734,10 @@ cudaError_t relax_pair_p(bool force, const DevPot& P, const DevGrid& g, const Pa
                          int64_t npair, void* dens, void* frc, cudaStream_t s) {
   using T = typename Rec4<typename Traits<PREC>::R>::T;
   const int pt = pair_threads(A);
-  // the density pass strides over a resident grid; the force pass takes one
-  // thread per pair
+  // the density pass strides over a resident grid in a single system; the
+  // force pass, and every pass of a batch (a stride would take each thread
+  // across systems, reloading a system's grid per pair: 55 -> 62 ms per
+  // ensemble step), take one thread per pair
   auto run = [&](auto kernel, T* out, bool resident) {
     const int64_t blocks = resident ? resident_grid((const void*)kernel, pt, npair) : (npair + pt - 1) / pt;
     if (blocks < 0 || blocks > 0x7fffffff) return cudaErrorInvalidValue;
@@ -2744,9 +2748,9 @@ cudaError_t relax_pair_p(bool force, const DevPot& P, const DevGrid& g, const Pa
     if (P.tab == 1) return run(k_pair_rforce<PREC, 2, 1>, (T*)frc, false);
     return run(k_pair_rforce<PREC, 2, 0>, (T*)frc, false);
   }
-  if (P.S == 1) return run(k_pair_rdensity<PREC, 1, 0>, (T*)dens, true);
-  if (P.tab == 1) return run(k_pair_rdensity<PREC, 2, 1>, (T*)dens, true);
-  return run(k_pair_rdensity<PREC, 2, 0>, (T*)dens, true);
+  if (P.S == 1) return run(k_pair_rdensity<PREC, 1, 0>, (T*)dens, A.batch.nsys == 0);
+  if (P.tab == 1) return run(k_pair_rdensity<PREC, 2, 1>, (T*)dens, A.batch.nsys == 0);
+  return run(k_pair_rdensity<PREC, 2, 0>, (T*)dens, A.batch.nsys == 0);
 }
 }  // namespace
 
