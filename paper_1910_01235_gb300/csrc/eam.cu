@@ -1431,6 +1431,19 @@ struct Rec4<double> {
   }
 };
 
+// value type of the relaxation records: FP32 in PREC 2 (float-float sums);
+// doubles in PREC 0 and in PREC 1, whose FP32 node values are converted to
+// FP64 by the pair kernel (its FP64 pipe is idle) rather than by the gathers
+// (bound by the FP64 pipe: a conversion and an add per component)
+template <int PREC>
+struct RelaxRec {
+  using V = double;
+};
+template <>
+struct RelaxRec<2> {
+  using V = float;
+};
+
 // per-site sums of the relaxation gathers: float-float in PREC 2, FP64 otherwise
 template <int PREC>
 struct RelaxAcc {
@@ -1444,13 +1457,13 @@ struct RelaxAcc<2> {
 template <int PREC, int S, int TAB>
 __device__ __forceinline__ void pair_rdensity_one(const DevPot& P, const DevGrid& g0, const PassArgs& A,
                                                 const int4* __restrict__ pair_rec, int64_t p,
-                                                typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens);
+                                                typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ dens);
 
 // grid-stride over the unordered pairs (a resident grid: see resident_grid)
 template <int PREC, int S, int TAB>
 __global__ void __launch_bounds__(256) k_pair_rdensity(DevPot P, DevGrid g0, PassArgs A,
                                                        const int4* __restrict__ pair_rec, int64_t npair,
-                                                       typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens) {
+                                                       typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ dens) {
   pdl_wait();
   pdl_trigger();
   if (chunk_halted(A)) return;
@@ -1462,9 +1475,9 @@ __global__ void __launch_bounds__(256) k_pair_rdensity(DevPot P, DevGrid g0, Pas
 template <int PREC, int S, int TAB>
 __device__ __forceinline__ void pair_rdensity_one(const DevPot& P, const DevGrid& g0, const PassArgs& A,
                                                 const int4* __restrict__ pair_rec, int64_t p,
-                                                typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens) {
+                                                typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ dens) {
   using R = typename Traits<PREC>::R;
-  using RT = Rec4<R>;
+  using RT = Rec4<typename RelaxRec<PREC>::V>;
   using TB = Tables<TAB>;
   constexpr int NF = S * S;
   PairRef pr_;
@@ -1538,14 +1551,15 @@ __device__ __forceinline__ void pair_rdensity_one(const DevPot& P, const DevGrid
           cj[2 + k] += si.x[l] * fav[w];
         }
     }
-  dens[tp] = RT::make(ci[0], ci[1], ci[2], ci[3]);
-  dens[tr] = RT::make(cj[0], cj[1], cj[2], cj[3]);
+  using RV = typename RelaxRec<PREC>::V;
+  dens[tp] = RT::make((RV)ci[0], (RV)ci[1], (RV)ci[2], (RV)ci[3]);
+  dens[tr] = RT::make((RV)cj[0], (RV)cj[1], (RV)cj[2], (RV)cj[3]);
   if (bad) atomicOr(A.flags, kFlagGeometry);
 }
 
 template <int PREC, int S, int NL>
 __global__ void __launch_bounds__(256) k_gather_rdensity(DevPot P, PassArgs A,
-                                                         const typename Rec4<typename Traits<PREC>::R>::T* __restrict__ dens) {
+                                                         const typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ dens) {
   pdl_wait();
   pdl_trigger();
   using R = typename Traits<PREC>::R;
@@ -1565,8 +1579,8 @@ __global__ void __launch_bounds__(256) k_gather_rdensity(DevPot P, PassArgs A,
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
 #pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
-      R rec[4];
-      Rec4<R>::load(&dens[t], rec);
+      typename RelaxRec<PREC>::V rec[4];
+      Rec4<typename RelaxRec<PREC>::V>::load(&dens[t], rec);
       rb[0].add(rec[0]);
       ra[0].add(rec[2]);
       if (S > 1) {
@@ -1637,14 +1651,14 @@ __global__ void __launch_bounds__(256) k_gather_rdensity(DevPot P, PassArgs A,
 template <int PREC, int S, int TAB>
 __device__ __forceinline__ void pair_rforce_one(const DevPot& P, const DevGrid& g0, const PassArgs& A,
                                                 const int4* __restrict__ pair_rec, int64_t p,
-                                                typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc);
+                                                typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ frc);
 
 // one thread per unordered pair (a grid-stride loop here held 48 registers
 // against 40 and ran 9 % slower)
 template <int PREC, int S, int TAB>
 __global__ void __launch_bounds__(256) k_pair_rforce(DevPot P, DevGrid g0, PassArgs A,
                                                        const int4* __restrict__ pair_rec, int64_t npair,
-                                                       typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc) {
+                                                       typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ frc) {
   pdl_wait();
   pdl_trigger();
   if (A.ctrl != nullptr && A.ctrl->halted) return;
@@ -1655,9 +1669,9 @@ __global__ void __launch_bounds__(256) k_pair_rforce(DevPot P, DevGrid g0, PassA
 template <int PREC, int S, int TAB>
 __device__ __forceinline__ void pair_rforce_one(const DevPot& P, const DevGrid& g0, const PassArgs& A,
                                                 const int4* __restrict__ pair_rec, int64_t p,
-                                                typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc) {
+                                                typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ frc) {
   using R = typename Traits<PREC>::R;
-  using RT = Rec4<R>;
+  using RT = Rec4<typename RelaxRec<PREC>::V>;
   using TB = Tables<TAB>;
   constexpr int NF = S * S;
   constexpr int NP = S * (S + 1) / 2;
@@ -1766,13 +1780,15 @@ __device__ __forceinline__ void pair_rforce_one(const DevPot& P, const DevGrid& 
   // this entry: the force on i and its width derivative; the reverse entry:
   // the force on j (Newton's third law) and j's width derivative
   const R Fx = -(d[0] * Tt + U[0] * inv12), Fy = -(d[1] * Tt + U[1] * inv12), Fz = -(d[2] * Tt + U[2] * inv12);
-  frc[tp] = RT::make(Fx, Fy, Fz, Vs[0] * inv12);
-  frc[tr] = RT::make(-Fx, -Fy, -Fz, Vs[1] * inv12);
+  using RV = typename RelaxRec<PREC>::V;
+  const RV fx = (RV)Fx, fy = (RV)Fy, fz = (RV)Fz;
+  frc[tp] = RT::make(fx, fy, fz, (RV)(Vs[0] * inv12));
+  frc[tr] = RT::make(-fx, -fy, -fz, (RV)(Vs[1] * inv12));
 }
 
 template <int PREC, int S, int NL>
 __global__ void __launch_bounds__(256) k_gather_rforce(PassArgs A,
-                                                       const typename Rec4<typename Traits<PREC>::R>::T* __restrict__ frc) {
+                                                       const typename Rec4<typename RelaxRec<PREC>::V>::T* __restrict__ frc) {
   pdl_wait();
   pdl_trigger();
   using R = typename Traits<PREC>::R;
@@ -1790,8 +1806,8 @@ __global__ void __launch_bounds__(256) k_gather_rforce(PassArgs A,
     const int beg = A.nb_off[i], end = A.nb_off[i + 1];
 #pragma unroll 4
     for (int t = beg + lane; t < end; t += NL) {
-      R f[4];
-      Rec4<R>::load(&frc[t], f);
+      typename RelaxRec<PREC>::V f[4];
+      Rec4<typename RelaxRec<PREC>::V>::load(&frc[t], f);
       g[0].add(f[0]);
       g[1].add(f[1]);
       g[2].add(f[2]);
@@ -2707,7 +2723,7 @@ namespace {
 template <int PREC, int S, int NL>
 cudaError_t relax_gather_t(bool force, const DevPot& P, const PassArgs& A, const void* dens, const void* frc,
                            cudaStream_t s) {
-  using T = typename Rec4<typename Traits<PREC>::R>::T;
+  using T = typename Rec4<typename RelaxRec<PREC>::V>::T;
   const int threads = A.tpb > 0 ? A.tpb : 256;
   const unsigned blocks = (unsigned)((A.n * NL + threads - 1) / threads);
   if (force) return launch_pdl(k_gather_rforce<PREC, S, NL>, dim3(blocks), dim3(threads), 0, s, A, (const T*)frc);
@@ -2732,7 +2748,7 @@ cudaError_t relax_gather_p(bool force, int nl, const DevPot& P, const PassArgs& 
 template <int PREC>
 cudaError_t relax_pair_p(bool force, const DevPot& P, const DevGrid& g, const PassArgs& A, const int4* pair_rec,
                          int64_t npair, void* dens, void* frc, cudaStream_t s) {
-  using T = typename Rec4<typename Traits<PREC>::R>::T;
+  using T = typename Rec4<typename RelaxRec<PREC>::V>::T;
   const int pt = pair_threads(A);
   // the density pass strides over a resident grid in a single system; the
   // force pass, and every pass of a batch (a stride would take each thread
@@ -2813,7 +2829,7 @@ int64_t resident_grid(const void* kernel, int threads, int64_t work_items) {
   return std::max<int64_t>(1, std::min<int64_t>(need, wave));
 }
 
-size_t relax_record_bytes(int precision) { return precision == 0 ? sizeof(Dbl4) : sizeof(float4); }
+size_t relax_record_bytes(int precision) { return precision == 2 ? sizeof(float4) : sizeof(Dbl4); }
 
 cudaError_t launch_relax_pair(int precision, bool force, const DevPot& P, const DevGrid& g, const PassArgs& A,
                               const int4* pair_rec, int64_t npair, void* dens, void* frc, cudaStream_t s) {
