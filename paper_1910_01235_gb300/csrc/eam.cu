@@ -1747,6 +1747,27 @@ __device__ __forceinline__ void pair_rforce_one(const DevPot& P, const DevGrid& 
         r_from_r2(r2, r, rinv);
         sw(P, r, Sw, dS);
         R A1 = (R)0, A2 = (R)0;
+        if constexpr (TAB == 2) {
+          // power form (FP64): two exponentials, the five terms as products;
+          // minus a term's derivative is its rate times the term
+          const R c0 = exp(-P.pw_beta[0] * r), c1 = exp(-P.pw_beta[1] * r);
+          const R c0_2 = c0 * c0, c1_2 = c1 * c1;
+          const R h0 = c0_2 * c0, h1 = c1_2 * c1;
+          const R c0_5 = h0 * c0_2, c1_5 = h1 * c1_2;
+          const R ephi[3] = {P.pw_pref_phi[0] * (h0 * h0), P.pw_pref_phi[1] * (h0 * h1),
+                             P.pw_pref_phi[2] * (h1 * h1)};
+          const R ef[2] = {P.pw_pref_f[0] * (c0_5 * c0_5), P.pw_pref_f[1] * (c1_5 * c1_5)};
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            A1 += cphi[u] * ephi[u];
+            A2 += clphi[u] * ephi[u];
+          }
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            A1 += cfa[v] * ef[v];
+            A2 += clf[v] * ef[v];
+          }
+        } else {
 #pragma unroll
         for (int u = 0; u < NP; ++u)
           if (u < TB::n_phi(P)) {
@@ -1768,6 +1789,7 @@ __device__ __forceinline__ void pair_rforce_one(const DevPot& P, const DevGrid& 
             A1 += cfa[v] * e;
             A2 += clf[v] * e;
           }
+        }
         w2[pm] = (A1 * dS - A2 * Sw) * rinv;
       }
       T += w2[0] + w2[1];
@@ -2761,6 +2783,10 @@ cudaError_t relax_pair_p(bool force, const DevPot& P, const DevGrid& g, const Pa
   };
   if (force) {
     if (P.S == 1) return run(k_pair_rforce<PREC, 1, 0>, (T*)frc, false);
+    if constexpr (PREC == 0) {
+      if (P.tab == 1 && P.pw_on && P.pw_m[0] == 6 && P.pw_n[0] == 10 && P.pw_m[1] == 6 && P.pw_n[1] == 10)
+        return run(k_pair_rforce<PREC, 2, 2>, (T*)frc, false);
+    }
     if (P.tab == 1) return run(k_pair_rforce<PREC, 2, 1>, (T*)frc, false);
     return run(k_pair_rforce<PREC, 2, 0>, (T*)frc, false);
   }

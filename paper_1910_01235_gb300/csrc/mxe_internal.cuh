@@ -91,6 +91,10 @@ struct Tables<1> {
   static __device__ __forceinline__ constexpr int n_phi(const DevPot&) { return 3; }
   static __device__ __forceinline__ constexpr int n_f(const DevPot&) { return 2; }
 };
+// pattern 1 whose terms are also in the power form with m = 6, n = 10 (see
+// DevPot::pw_on): the FP64 force pass forms them as products
+template <>
+struct Tables<2> : Tables<1> {};
 
 // Box / cell grid for positions and image codes.
 struct DevGrid {

@@ -328,6 +328,30 @@ def test_relax_fixed_iterations_fp64_parity(pot):
     g.close()
 
 
+@pytest.mark.parametrize("pot", ["literal", "variant_s"])
+def test_relax_fixed_iterations_fp64_binary_parity(pot):
+    """FP64 FIRE on the binary alloy: with the literal tables the half-list
+    force pass takes the power form (rates 3/r0 and 5/r0: two exponentials
+    per node, the terms as products), with the swapped exponents the general
+    form; both against the oracle's trajectory at 1e-9 A."""
+    s = W.perturb(W.config_binary_alloy(cells=4), 0.05, 0.02, seed=13)
+    s = W.random_fractions(s, vac_min=0.01, seed=14)
+    if pot == "variant_s":
+        s.pot = W.potential_binary_variant_s()
+    K = 12
+    g = M.MxeSystem(s, "fp64")
+    assert g.pair_form() == (1, 1)
+    g.build_neighbors()
+    st, it, fm = g.relax(0.0, K)
+    assert st == M.ERR_NO_CONVERGE and it == K
+    sto, ito, fmo, qo, so = O.relax(s, 0.0, K)
+    assert sto == O.ERR_NO_CONVERGE and ito == K
+    np.testing.assert_allclose(g.q.cpu().numpy(), qo, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(g.sigma.cpu().numpy(), so, rtol=0, atol=1e-9)
+    assert abs(fm - fmo) <= 1e-8
+    g.close()
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_relax_converges_variant_s(prec):
     s = W.perturb(W.config_vacancy_lattice(pot=W.potential_variant_s(), x0=1.0), 0.05, 0.03)
