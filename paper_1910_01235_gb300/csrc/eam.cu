@@ -132,8 +132,10 @@ __device__ __forceinline__ void r_from_r2(float r2, float& r, float& rinv) {
   r = r2 * rinv;
 }
 __device__ __forceinline__ void r_from_r2(double r2, double& r, double& rinv) {
-  r = sqrt(r2);
-  rinv = 1.0 / r;
+  // one reciprocal square root (CUDA's rsqrt, 1 ulp) and a product: r and
+  // 1/r to about 2 ulps, against a square root and a division on the FP64 pipe
+  rinv = rsqrt(r2);
+  r = r2 * rinv;
 }
 
 __device__ __forceinline__ void r_from_r2(ff r2, ff& r, ff& rinv) {
