@@ -238,6 +238,11 @@ def roofline_of(shares, npairs, S, n_phi, n_f, with_traffic):
                     "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)"})
     out["traffic"] = ncu_traffic(dom) if with_traffic else None
     out["traffic_unit"] = "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)"
+    # HBM and L2 throughput of the dominant kernel: the captured bytes of one
+    # launch over its event-timed duration in this run
+    rec = ncu_record(dom) if with_traffic else None
+    out["hbm_gbs"] = (rec["dram_read"] + rec["dram_write"]) / avg_s / 1e9 if rec else None
+    out["l2_gbs"] = rec["l2_bytes"] / avg_s / 1e9 if rec else None
     return out
 
 
