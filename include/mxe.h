@@ -336,6 +336,14 @@ MXE_API mxe_status mxe_get_pass_shape(mxe_ctx *ctx, int32_t *lanes, int32_t *thr
  *    terms as products; 0: one exponential per term.                        */
 MXE_API mxe_status mxe_pair_form(mxe_ctx *ctx, int32_t *table_pattern, int32_t *power_form);
 
+/* The same decision for a potential alone, on the host (no context, no GPU):
+ * table_pattern and power_form as above; m, n (host arrays of 2, may be NULL)
+ * receive each species' integer powers of exp(-beta_s r) for the like pair
+ * term and the density term when power_form is 1 (0 otherwise).
+ * MXE_ERR_ARG for a potential mxe_create would reject.                      */
+MXE_API mxe_status mxe_potential_pair_form(const mxe_potential *pot, int32_t *table_pattern, int32_t *power_form,
+                                           int32_t *m, int32_t *n);
+
 /* Phase average of the embedding term (App. B.2).
  *  MXE_EMBED_TAYLOR (default): the Taylor form Eq. F_taylor_mxe,
  *    <F_k(rho_i)> ~ F_k(rho_bar_i) + F_k'(rho_bar_i)(<rho_i> - rho_bar_i).

@@ -2222,6 +2222,21 @@ mxe_status mxe_get_pass_shape(mxe_ctx* c, int32_t* lanes, int32_t* threads, int3
   return MXE_OK;
 }
 
+mxe_status mxe_potential_pair_form(const mxe_potential* pot, int32_t* table_pattern, int32_t* power_form, int32_t* m,
+                                   int32_t* n) {
+  if (!pot) return MXE_ERR_ARG;
+  DevPot d;
+  const mxe_status ms = make_devpot(*pot, d);
+  if (ms != MXE_OK) return ms;
+  if (table_pattern) *table_pattern = d.tab;
+  if (power_form) *power_form = d.pw_on;
+  for (int s = 0; s < 2; ++s) {
+    if (m) m[s] = d.pw_on ? d.pw_m[s] : 0;
+    if (n) n[s] = d.pw_on ? d.pw_n[s] : 0;
+  }
+  return MXE_OK;
+}
+
 mxe_status mxe_pair_form(mxe_ctx* c, int32_t* table_pattern, int32_t* power_form) {
   if (!c) return MXE_ERR_ARG;
   if (table_pattern) *table_pattern = c->dp.tab;

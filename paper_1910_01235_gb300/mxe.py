@@ -70,7 +70,8 @@ EXPORTS = ["mxe_status_string", "mxe_create", "mxe_create_batch", "mxe_destroy",
            "mxe_set_dt_scale", "mxe_run_staggered", "mxe_autotune", "mxe_set_pass_shape",
            "mxe_potential_terms", "mxe_tangent", "mxe_flux_vjp", "mxe_unrolled_grad", "mxe_transport_step",
            "mxe_set_embedding", "mxe_element_param_grad", "mxe_unrolled_grad_multi", "mxe_set_pair_block",
-           "mxe_get_pass_shape", "mxe_run_stats", "mxe_pair_form"]
+           "mxe_get_pass_shape", "mxe_run_stats", "mxe_pair_form",
+           "mxe_potential_pair_form"]
 EMBED_TAYLOR, EMBED_EXACT = 0, 1
 TIMING_NAME_LEN = 48
 NOALLOC_SCRATCH_DOUBLES = 1 << 19
@@ -108,6 +109,7 @@ def lib():
             L.mxe_set_pair_block.argtypes = [p, C.c_int32]
             L.mxe_get_pass_shape.argtypes = [p, p, p, p]
             L.mxe_pair_form.argtypes = [p, p, p]
+            L.mxe_potential_pair_form.argtypes = [p, p, p, p, p]
             L.mxe_run_stats.argtypes = [p, p, p]
             L.mxe_element_param_grad.argtypes = [p, p, p]
             L.mxe_unrolled_grad_multi.argtypes = [p, p, C.c_int32, d, d, d, d, C.c_int32, p, C.c_int32, C.c_int32,
@@ -324,6 +326,17 @@ def mxe_diffuse_step_noalloc(n, S, x_ptr, T_ptr, mu_ex_ptr, bond_off_ptr, bond_i
                                           C.c_void_p(mu_ex_ptr), C.c_void_p(bond_off_ptr),
                                           C.c_void_p(bond_idx_ptr), float(dt), float(nu0), float(Qm),
                                           C.c_void_p(stream))
+
+
+def potential_pair_form(pot):
+    """(table pattern, power form, m [2], n [2]) of a potential, decided on the
+    host as a context would (include/mxe.h, mxe_potential_pair_form)."""
+    P = make_potential(pot)
+    v = (C.c_int32 * 6)()
+    st = lib().mxe_potential_pair_form(C.byref(P), C.byref(v, 0), C.byref(v, 4), C.byref(v, 8), C.byref(v, 16))
+    if st != OK:
+        raise MxeError(st, "mxe_potential_pair_form")
+    return v[0], v[1], (v[2], v[3]), (v[4], v[5])
 
 
 # ------------------------------------------------------------------ helpers
