@@ -11,7 +11,9 @@
 //                   dt, alpha, n_pos;
 //   k_fire_update : v = (1 - alpha)(keep v + dt f) + alpha |v'| f / |f|,
 //                   y += dt v, sigma kept in [sigma_lo, sigma_hi] (velocity
-//                   zeroed at a bound), and the maxima the skin test needs.
+//                   zeroed at a bound), and the maxima the skin test needs;
+//                   the launch's last block then tests the rebuild criterion,
+//                   so a halted next evaluation returns at once.
 // The sigma force is projected on [sigma_lo, sigma_hi] (zero where a bound
 // blocks it) in the reduction and the update.
 // |v'|^2 = keep (|v|^2 + 2 dt f.v) + dt^2 |f|^2 is formed from the partial sums,
