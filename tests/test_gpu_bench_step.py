@@ -61,16 +61,17 @@ def oracle_step(s, r_list, r_bond, dt, K):
     return fe, xo, qo, so, fmo
 
 
-def test_bench_step_ff_256k_against_oracle():
-    """bench.py's timed step, float-float context, full size, with at least
-    one list rebuild inside the relaxation; then the forces at the GPU's final
-    state (half-list kernels on lists built mid-relaxation) against the
-    oracle's at that same state."""
+@pytest.mark.parametrize("prec", ["ff", "mixed"])
+def test_bench_step_256k_against_oracle(prec):
+    """bench.py's timed step, float-float and FP64-sum contexts, full size,
+    with at least one list rebuild inside the relaxation; then the forces at
+    the GPU's final state (half-list kernels on lists built mid-relaxation)
+    against the oracle's at that same state."""
     s = W.config_binary_alloy()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        g = M.MxeSystem(s, "ff", device=dev, stream=stream)
+        g = M.MxeSystem(s, prec, device=dev, stream=stream)
     g.build_neighbors()
     g.autotune()
     fire = M.make_fire(check_every=K_BENCH + 1)
@@ -99,7 +100,7 @@ def test_bench_step_ff_256k_against_oracle():
     ex = np.abs(x1 - xo).max()
     dq = np.abs(q1 - qo).max()
     ds = np.abs(s1 - so).max()
-    print(f"256k ff step: |dF/dq| err {eq:.2e}, |dF/dsigma| err {es:.2e} (scale {gscale:.2f}), "
+    print(f"256k {prec} step: |dF/dq| err {eq:.2e}, |dF/dsigma| err {es:.2e} (scale {gscale:.2f}), "
           f"x {ex:.2e}, q {dq:.2e} A, sigma {ds:.2e} A, fmax {fm:.6f} vs {fmo:.6f}")
     assert eq <= 1e-4 * gscale and es <= 1e-4 * gscale
     assert np.abs(xo - s.x).max() > 1e-6          # the Euler step moved mass (x_v = 1e-3)
